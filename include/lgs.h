@@ -1,0 +1,203 @@
+/*
+ * lgs.h -- C ABI of the GB300 language-feature Gaussian-splatting library.
+ *
+ * The library implements the data-parallel hot path of the mapping loop of
+ * LEGO-SLAM (arXiv 2511.16144): rendering a map of language-embedded 3D
+ * Gaussians (Sec. III-B.1) into RGB, depth and a compact feature map, the
+ * backward pass that the map optimisation of Sec. III-B.3 needs (Eq. 1-2),
+ * and the encoder / decoder GEMMs of the scene-adaptive autoencoder
+ * (Sec. III-B.3 Eq. 2, Sec. III-B.4 Eq. 3, Sec. IV-A.2).
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * - Pointers named *_host are host memory; every other pointer is device
+ *   memory owned by the caller.  The library allocates nothing and frees
+ *   nothing; scratch space is passed in (see gs_bin_sort_workspace and the
+ *   grad2d argument of gs_render_bwd).
+ * - Every call only enqueues work on `stream` (a cudaStream_t; NULL = the
+ *   legacy default stream) and returns without synchronising.  Argument
+ *   errors that the host can see (null or misaligned pointers, bad sizes)
+ *   return LGS_ERR_INVALID before anything is enqueued; launch failures
+ *   return LGS_ERR_CUDA.  lgs_last_error() gives the message (thread-local).
+ * - Arrays are dense, row-major, structure-of-arrays; images are [C,H,W,ch]
+ *   (camera, row, column, channel).  Pointers read or written with 16-byte
+ *   vector accesses must be 16-byte aligned (stated per argument).
+ * - Gradient outputs (d_*) are ACCUMULATED into (+=); zero them first for a
+ *   plain gradient.
+ * - bf16 arrays are passed as uint16_t (IEEE bfloat16 bit patterns).
+ * - A stream may carry calls from one host thread at a time; different
+ *   streams may be used concurrently.  No call keeps state between calls.
+ */
+#ifndef LGS_H
+#define LGS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  LGS_OK = 0,
+  LGS_ERR_INVALID = 1,   /* bad argument (host-detected) */
+  LGS_ERR_CAPACITY = 2,  /* instance buffer too small (see gs_bin_sort) */
+  LGS_ERR_CUDA = 5       /* a CUDA launch or runtime call failed */
+} lgs_status;
+
+typedef enum { LGS_F32 = 0, LGS_BF16 = 1 } lgs_dtype;
+
+/* Upper bound on cameras rendered in one launch (a keyframe window). */
+#define LGS_MAX_CAMS 16
+/* Tile edge in pixels (16x16 tiles, one CTA each). */
+#define LGS_TILE 16
+/* Floats per projected record and per 2D-gradient record. */
+#define LGS_PROJ_STRIDE 8
+
+/* Pinhole camera.  viewmat = row-major 3x4 world-to-camera [R | t] in
+ * OpenCV axes (x right, y down, z forward); a pixel (i, j) has its centre at
+ * (i + 0.5, j + 0.5); u = fx x/z + cx, v = fy y/z + cy.  Gaussians with
+ * camera depth z <= znear are culled. */
+typedef struct {
+  float fx, fy, cx, cy;
+  int32_t width, height;
+  float viewmat[12];
+  float znear;
+} lgs_camera;
+
+/* Library version string. */
+const char* lgs_version(void);
+
+/* Message of the last failing call on this host thread ("" if none). */
+const char* lgs_last_error(void);
+
+/* ------------------------------------------------------------------------
+ * gs_project -- EWA projection of every Gaussian into every camera.
+ *
+ * Sec. III-B.1: a Gaussian has position p, rotation q, scale s, opacity
+ * alpha, colour c and feature f, rendered "following the standard 3DGS
+ * pipeline".  Per (camera c, Gaussian i), in FP32:
+ *   t = R_c p + t_c;   Sigma3 = R(q/|q|) diag(exp(2 log_s)) R^T;
+ *   J = [[fx/tz, 0, -fx tx'/tz^2], [0, fy/tz, -fy ty'/tz^2]] with tx'/tz
+ *   clamped to [(-0.15W - cx)/fx, (1.15W - cx)/fx] (same in y);
+ *   Sigma2 = J R_c Sigma3 R_c^T J^T + 0.3 I;  conic = Sigma2^-1;
+ *   opacity o = sigmoid(logit).
+ * A Gaussian is culled (rect empty) if tz <= znear, det(Sigma2) <= 0,
+ * o < 1/255 or its support misses the image.  The support radius is
+ * sqrt(2 ln(255 o) lambda_max(Sigma2)) (1 + 1e-5) + 1e-3 px: every pixel
+ * outside it has o exp(power) < 1/255, so tiled rendering equals per-pixel
+ * rendering over all Gaussians.
+ *
+ * means [n,3], quats [n,4] (w,x,y,z), log_scales [n,3], opacity_logits [n]:
+ *   float32 device arrays.
+ * cams_host [n_cams]: host array, 1 <= n_cams <= LGS_MAX_CAMS.
+ * proj [n_cams*n, 8] (16-byte aligned): per (camera, Gaussian) record
+ *   (u, v, conic a, conic b, conic c, opacity, depth tz, 0); zero when culled.
+ * rect [n_cams*n, 4] uint16 (8-byte aligned): covered tiles
+ *   [x0, y0, x1, y1) on the 16x16 grid, x1 == x0 and y1 == y0 when culled.
+ * ---------------------------------------------------------------------- */
+lgs_status gs_project(const float* means, const float* quats, const float* log_scales,
+                      const float* opacity_logits, int64_t n, const lgs_camera* cams_host,
+                      int n_cams, float* proj, uint16_t* rect, void* stream);
+
+/* ------------------------------------------------------------------------
+ * gs_bin_sort -- 16x16 tile binning with a depth-keyed stable radix sort.
+ *
+ * Each (camera c, Gaussian i) emits one instance per covered tile; the
+ * instances are ordered by the 64-bit key ((c * tiles + tile) << 32) |
+ * bits(float depth), ties by ascending Gaussian index (a stable sort of the
+ * emission order).  This is the front-to-back order of Sec. III-B.1's
+ * alpha compositing within every tile.
+ *
+ * proj, rect: gs_project outputs for n Gaussians and n_cams cameras.
+ * tiles_x, tiles_y: grid size (ceil(W/16), ceil(H/16)).
+ * capacity: length of ids (and keys_opt).
+ * ids [capacity] uint32 out: Gaussian index of each sorted instance.
+ * ranges [n_cams*tiles_x*tiles_y, 2] uint32 out: [start, end) of each
+ *   tile's instances in ids; (0, 0) for an empty tile.
+ * keys_opt [capacity] uint64 out or NULL: the sort keys.
+ * n_instances_dev: device int64 out, the instance count K.  If K >
+ *   capacity nothing is sorted, every range is (0, 0) and the caller must
+ *   retry with capacity >= K (read K after synchronising).  The call never
+ *   synchronises, so capacity is not checked on the host.
+ * workspace: device scratch of at least gs_bin_sort_workspace(...) bytes,
+ *   256-byte aligned.
+ * ---------------------------------------------------------------------- */
+size_t gs_bin_sort_workspace(int64_t n, int n_cams, int tiles_x, int tiles_y,
+                             int64_t capacity);
+lgs_status gs_bin_sort(const float* proj, const uint16_t* rect, int64_t n, int n_cams,
+                       int tiles_x, int tiles_y, int64_t capacity, uint32_t* ids,
+                       uint32_t* ranges, uint64_t* keys_opt, int64_t* n_instances_dev,
+                       void* workspace, size_t workspace_bytes, void* stream);
+
+/* ------------------------------------------------------------------------
+ * gs_render_fwd -- front-to-back alpha compositing of RGB, depth and a
+ * feat_dim-channel feature map (Sec. III-B.1; F_render of Eq. 2).
+ *
+ * Per pixel, over its tile's sorted instances: power = -(a dx^2 + c dy^2)/2
+ * - b dx dy with d = (u - px, v - py); skip if power > 0; alpha =
+ * min(0.99, o e^power); skip if alpha < 1/255; T' = T (1 - alpha); stop,
+ * without blending, when T' < 1e-4; else w = alpha T accumulates w c,
+ * w tz, w f and T = T'.  rgb gets + T_final bg; depth is the unnormalised
+ * sum of w tz.  alpha / T are FP32; channels are read as float32 or bf16
+ * (chan_dtype) and accumulated in FP32.
+ *
+ * All cameras must share width and height.  colors [n,3], feats [n,D]
+ * (16-byte aligned, D = feat_dim, a positive multiple of 16).
+ * bg_host: float[3] background colour.
+ * Outputs (float32 unless stated): rgb [C,H,W,3], depth [C,H,W],
+ * feat [C,H,W,D], T_final [C,H,W], last [C,H,W] uint32 (position + 1, in
+ * the tile's range, of the last blended instance; the backward's start),
+ * n_contrib_opt [C,H,W] uint32 (number blended) or NULL.
+ * ---------------------------------------------------------------------- */
+lgs_status gs_render_fwd(const float* proj, const uint32_t* ids, const uint32_t* ranges,
+                         int64_t n, const lgs_camera* cams_host, int n_cams, const void* colors,
+                         const void* feats, int feat_dim, int chan_dtype, const float* bg_host,
+                         float* rgb, float* depth, float* feat, float* T_final, uint32_t* last,
+                         uint32_t* n_contrib_opt, void* stream);
+
+/* ------------------------------------------------------------------------
+ * gs_render_bwd -- gradient of the rendered maps w.r.t. every Gaussian
+ * parameter (the map optimisation of Sec. III-B.3, Eq. 1).
+ *
+ * Walks each pixel's blended instances back to front from `last`,
+ * recovering T_i = T_{i+1} / (1 - alpha_i) from T_final instead of storing
+ * it, and scatters per-Gaussian partials: colour and feature gradients
+ * sum_px w g, and the 2D-mean, conic and opacity gradients through
+ * dL/dalpha_i = T_i (x_i . g) - S_i / (1 - alpha_i), with S_i the suffix
+ * sum of w_k (x_k . g) behind i plus T_final (bg . g).  Partials are summed
+ * over each tile's 256 pixels on chip and added to global memory once per
+ * (tile, instance).  The chain rule through the projection then gives the
+ * parameter gradients, summed over cameras.
+ *
+ * Inputs: the Gaussian parameters and every gs_project / gs_bin_sort /
+ * gs_render_fwd input and output named here, plus the upstream gradients
+ * d_rgb [C,H,W,3], d_depth [C,H,W], d_feat [C,H,W,D] (float32).
+ * grad2d [n_cams*n, 8] (16-byte aligned): scratch, overwritten with the
+ *   per-(camera, Gaussian) 2D gradients (u, v, a, b, c, opacity, depth, 0).
+ * Outputs (accumulated): d_means [n,3], d_quats [n,4], d_log_scales [n,3],
+ * d_opacity_logits [n], d_colors [n,3], d_feats [n,D] (16-byte aligned).
+ * ---------------------------------------------------------------------- */
+lgs_status gs_render_bwd(const float* means, const float* quats, const float* log_scales,
+                         const float* opacity_logits, const float* proj, const uint32_t* ids,
+                         const uint32_t* ranges, int64_t n, const lgs_camera* cams_host,
+                         int n_cams, const void* colors, const void* feats, int feat_dim,
+                         int chan_dtype, const float* bg_host, const float* T_final,
+                         const uint32_t* last, const float* d_rgb, const float* d_depth,
+                         const float* d_feat, float* grad2d, float* d_means, float* d_quats,
+                         float* d_log_scales, float* d_opacity_logits, float* d_colors,
+                         float* d_feats, void* stream);
+
+/* ------------------------------------------------------------------------
+ * lgs_l1_loss -- one L1 term of Eq. 1 / Eq. 2: loss_dev += weight *
+ * mean|pred - target| and grad = weight * sign(pred - target) / count
+ * (overwritten; sign(0) = 0).  pred, grad: float32 [count]; target float32
+ * or bf16 (target_dtype) [count]; loss_dev: one float32 on the device.
+ * ---------------------------------------------------------------------- */
+lgs_status lgs_l1_loss(const float* pred, const void* target, int target_dtype, int64_t count,
+                       float weight, float* grad, float* loss_dev, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LGS_H */

@@ -57,7 +57,7 @@ def _load():
     I64, I32 = ctypes.c_int64, ctypes.c_int
     lib.lgso_project.argtypes = [I64, P, P, P, P, P, P, P, P, P, P, P, P, P]
     lib.lgso_render_fwd.argtypes = [I64, I32, P, P, P, P, P, P, P, P, I32, I32, I32, I32,
-                                    P, P, P, P, P, P]
+                                    P, P, P, P, P, P, P]
     lib.lgso_render_bwd.argtypes = [I64, I32, P, P, P, P, P, P, P, P, I32, I32, I32, I32,
                                     P, P, P, P, P, P, P, P, P, P]
     lib.lgso_project_bwd.argtypes = [I64, P, P, P, P, P, P, P, P, P, P]
@@ -116,9 +116,11 @@ def _crop(cam, crop):
 def render(scene, cam, bg=(0.0, 0.0, 0.0), crop=None) -> dict:
     """Brute-force front-to-back compositing of every pixel in ``crop``
     (x0, y0, w, h; default the whole image).  Returns rgb [h,w,3], depth [h,w],
-    feat [h,w,D], T_final [h,w], n_contrib [h,w] (int32, number blended) and
-    margin [h,w] (smallest relative distance of any discrete decision of the
-    pixel from its threshold, including depth-order gaps)."""
+    feat [h,w,D], T_final [h,w], n_contrib [h,w] (int32, number blended),
+    margin [h,w] (smallest relative distance of any skip / clamp / stop
+    decision of the pixel from its threshold) and zgap [h,w] (smallest
+    relative depth gap between consecutive non-skipped Gaussians, which
+    decides their order)."""
     lib = _load()
     n = scene.means.shape[0]
     d = scene.feats.shape[1] if scene.feats is not None and scene.feats.ndim == 2 else 0
@@ -129,10 +131,11 @@ def render(scene, cam, bg=(0.0, 0.0, 0.0), crop=None) -> dict:
     ca, bga = camera_array(cam), _f64(bg)
     out = dict(rgb=np.zeros((h, w, 3)), depth=np.zeros((h, w)), feat=np.zeros((h, w, d)),
                T_final=np.zeros((h, w)), n_contrib=np.zeros((h, w), np.int32),
-               margin=np.zeros((h, w)))
+               margin=np.zeros((h, w)), zgap=np.zeros((h, w)))
     lib.lgso_render_fwd(n, d, *[_ptr(a) for a in arrs], _ptr(ca), _ptr(bga), x0, y0, w, h,
                         _ptr(out["rgb"]), _ptr(out["depth"]), _ptr(out["feat"]),
-                        _ptr(out["T_final"]), _ptr(out["n_contrib"]), _ptr(out["margin"]))
+                        _ptr(out["T_final"]), _ptr(out["n_contrib"]), _ptr(out["margin"]),
+                        _ptr(out["zgap"]))
     return out
 
 

@@ -251,9 +251,9 @@ typedef struct { int64_t g; double alpha, T, power; int clamped; } blend_rec;
 static int composite_pixel(int x, int y, int d, const oproj* P, const int64_t* order, int64_t m,
                            const double* colors, const double* feats, const double* bg,
                            double* rgb, double* dep, double* feat, double* T_out,
-                           double* margin_out, blend_rec* list) {
+                           double* margin_out, double* zgap_out, blend_rec* list) {
   double px = x + 0.5, py = y + 0.5;
-  double T = 1.0, C[3] = {0, 0, 0}, D = 0, margin = INFINITY, zprev = -1;
+  double T = 1.0, C[3] = {0, 0, 0}, D = 0, margin = INFINITY, zgap = INFINITY, zprev = -1;
   for (int k = 0; k < d; k++) feat[k] = 0;
   int count = 0;
   for (int64_t j = 0; j < m; j++) {
@@ -271,7 +271,7 @@ static int composite_pixel(int x, int y, int d, const oproj* P, const int64_t* o
     double alpha = araw < ALPHA_MAX ? araw : ALPHA_MAX;
     if (zprev > 0) {
       double mz = fabs(g->t[2] - zprev) / g->t[2];
-      if (mz < margin) margin = mz;
+      if (mz < zgap) zgap = mz;
     }
     zprev = g->t[2];
     double Tn = T * (1.0 - alpha);
@@ -294,6 +294,7 @@ static int composite_pixel(int x, int y, int d, const oproj* P, const int64_t* o
   *dep = D;
   *T_out = T;
   if (margin_out) *margin_out = margin;
+  if (zgap_out) *zgap_out = zgap;
   return count;
 }
 
@@ -301,7 +302,7 @@ int lgso_render_fwd(int64_t n, int d, const double* means, const double* quats,
                     const double* log_scales, const double* op_logits, const double* colors,
                     const double* feats, const double* camv, const double* bg, int x0, int y0,
                     int w, int h, double* rgb, double* dep, double* feat, double* T_final,
-                    int32_t* n_contrib, double* margin) {
+                    int32_t* n_contrib, double* margin, double* zgap) {
   ocam cam = read_cam(camv);
   oproj* P = (oproj*)malloc(sizeof(oproj) * (n ? n : 1));
   int64_t* order = (int64_t*)malloc(sizeof(int64_t) * (n ? n : 1));
@@ -311,7 +312,8 @@ int lgso_render_fwd(int64_t n, int d, const double* means, const double* quats,
     int x = x0 + (int)(pix % w), y = y0 + (int)(pix / w);
     n_contrib[pix] = composite_pixel(x, y, d, P, order, m, colors, feats, bg, rgb + 3 * pix,
                                      dep + pix, feat + (int64_t)d * pix, T_final + pix,
-                                     margin ? margin + pix : NULL, NULL);
+                                     margin ? margin + pix : NULL, zgap ? zgap + pix : NULL,
+                                     NULL);
   }
   free(P);
   free(order);
@@ -440,7 +442,7 @@ int lgso_render_bwd(int64_t n, int d, const double* means, const double* quats,
       int x = x0 + (int)(pix % w), y = y0 + (int)(pix / w);
       double rgb[3], dep, T;
       int cnt = composite_pixel(x, y, d, P, order, m, colors, feats, bg, rgb, &dep, fbuf, &T,
-                                NULL, list);
+                                NULL, NULL, list);
       const double* gr = g_rgb + 3 * pix;
       double gd = g_dep[pix];
       const double* gf = g_feat + (int64_t)d * pix;

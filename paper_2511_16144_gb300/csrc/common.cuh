@@ -1,0 +1,73 @@
+// Shared device helpers and host-side argument checking for liblgs.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "lgs.h"
+
+namespace lgs {
+
+// ---------------------------------------------------------------- host errors
+void set_error(const std::string& msg);
+void clear_error();
+
+#define LGS_CHECK_ARG(cond, msg)                     \
+  do {                                               \
+    if (!(cond)) {                                   \
+      ::lgs::set_error(std::string(__func__) + ": " + (msg)); \
+      return LGS_ERR_INVALID;                        \
+    }                                                \
+  } while (0)
+
+#define LGS_CHECK_CUDA(expr)                                                   \
+  do {                                                                         \
+    cudaError_t e_ = (expr);                                                   \
+    if (e_ != cudaSuccess) {                                                   \
+      ::lgs::set_error(std::string(__func__) + ": " + cudaGetErrorString(e_)); \
+      return LGS_ERR_CUDA;                                                     \
+    }                                                                          \
+  } while (0)
+
+#define LGS_CHECK_LAUNCH() LGS_CHECK_CUDA(cudaGetLastError())
+
+inline bool aligned(const void* p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
+inline cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+// ---------------------------------------------------------------- constants
+// Thresholds of the compositing rule (front-to-back alpha blending of the
+// standard 3DGS pipeline that Sec. III-B.1 renders with).
+constexpr float kAlphaMin = 1.0f / 255.0f;
+constexpr float kAlphaMax = 0.99f;
+constexpr float kTStop = 1e-4f;
+constexpr float kDilation = 0.3f;
+constexpr int kTile = LGS_TILE;
+constexpr int kTilePixels = kTile * kTile;
+
+// Cameras passed by value to kernels (a keyframe window).
+struct CamBlock {
+  lgs_camera cam[LGS_MAX_CAMS];
+};
+
+// ---------------------------------------------------------------- device math
+// The compositing decision arithmetic is pinned with explicit round-to-nearest
+// intrinsics so the forward and the backward reach bit-identical alphas.
+__device__ __forceinline__ float gauss_power(float a, float b, float c, float dx, float dy) {
+  // -(a dx^2 + c dy^2)/2 - b dx dy
+  float q = __fmul_rn(a, __fmul_rn(dx, dx));
+  q = __fmaf_rn(c, __fmul_rn(dy, dy), q);
+  float cross = __fmul_rn(b, __fmul_rn(dx, dy));
+  return __fmaf_rn(-0.5f, q, -cross);
+}
+
+__device__ __forceinline__ float raw_alpha(float o, float power) {
+  return __fmul_rn(o, __expf(power));
+}
+
+__device__ __forceinline__ float to_float(float x) { return x; }
+__device__ __forceinline__ float to_float(__nv_bfloat16 x) { return __bfloat162float(x); }
+
+}  // namespace lgs

@@ -1,0 +1,18 @@
+// Internal launchers shared between translation units of liblgs.
+#pragma once
+
+#include "common.cuh"
+
+namespace lgs {
+
+// Validates the cameras and copies them into a kernel-parameter block.
+lgs_status fill_cams(const lgs_camera* cams_host, int n_cams, CamBlock& cb);
+
+// Projection backward: one thread per Gaussian sums the chain rule of every
+// camera's 2D gradient record (u, v, a, b, c, o, tz, 0) into the parameters.
+lgs_status launch_project_bwd(const float* means, const float* quats, const float* log_scales,
+                              const float* logits, int64_t n, int n_cams, const CamBlock& cams,
+                              const float* grad2d, float* d_means, float* d_quats,
+                              float* d_log_scales, float* d_logits, cudaStream_t s);
+
+}  // namespace lgs

@@ -1,0 +1,222 @@
+"""ctypes binding of liblgs (the C ABI in include/lgs.h).
+
+Each function here carries the C entry point's name and only marshals
+arguments: torch CUDA tensors supply device memory and the current CUDA
+stream, and every step runs in the library's kernels.  If liblgs.so is
+missing, or no CUDA device is present, calls raise; there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+
+import numpy as np
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "liblgs.so")
+MAX_CAMS = 16
+TILE = 16
+PROJ_STRIDE = 8
+F32, BF16 = 0, 1
+
+_lib = None
+
+
+class LgsError(RuntimeError):
+    """A liblgs call returned a non-zero lgs_status."""
+
+
+class LgsCamera(ctypes.Structure):
+    _fields_ = [("fx", ctypes.c_float), ("fy", ctypes.c_float), ("cx", ctypes.c_float),
+                ("cy", ctypes.c_float), ("width", ctypes.c_int32), ("height", ctypes.c_int32),
+                ("viewmat", ctypes.c_float * 12), ("znear", ctypes.c_float)]
+
+
+def load():
+    """Opens liblgs.so (build it first with ``paper_2511_16144_gb300.build``)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise LgsError(f"{LIB_PATH} is missing: run paper_2511_16144_gb300.build.build()")
+    lib = ctypes.CDLL(LIB_PATH)
+    P, I64, I32, SZ = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_size_t
+    F = ctypes.c_float
+    sig = {
+        "lgs_version": ([], ctypes.c_char_p),
+        "lgs_last_error": ([], ctypes.c_char_p),
+        "gs_project": ([P, P, P, P, I64, P, I32, P, P, P], I32),
+        "gs_bin_sort_workspace": ([I64, I32, I32, I32, I64], SZ),
+        "gs_bin_sort": ([P, P, I64, I32, I32, I32, I64, P, P, P, P, P, SZ, P], I32),
+        "gs_render_fwd": ([P, P, P, I64, P, I32, P, P, I32, I32, P, P, P, P, P, P, P, P], I32),
+        "gs_render_bwd": ([P, P, P, P, P, P, P, I64, P, I32, P, P, I32, I32, P, P, P, P, P, P, P,
+                           P, P, P, P, P, P, P], I32),
+        "lgs_l1_loss": ([P, P, I32, I64, F, P, P, P], I32),
+    }
+    for name, (args, res) in sig.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = res
+    _lib = lib
+    return lib
+
+
+def exported_symbols():
+    """Names of the C entry points this binding declares."""
+    return ["lgs_version", "lgs_last_error", "gs_project", "gs_bin_sort_workspace", "gs_bin_sort",
+            "gs_render_fwd", "gs_render_bwd", "lgs_l1_loss"]
+
+
+def _check(status, what):
+    if status != 0:
+        msg = load().lgs_last_error().decode()
+        raise LgsError(f"{what} failed with status {status}: {msg}")
+
+
+def _p(t):
+    if t is None:
+        return None
+    if isinstance(t, torch.Tensor):
+        if t.numel() and not t.is_contiguous():
+            raise LgsError("tensor must be contiguous")
+        return ctypes.c_void_p(t.data_ptr())
+    return t
+
+
+def _stream():
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def cameras(cams):
+    """Packs camera objects (fx, fy, cx, cy, width, height, viewmat[3,4],
+    znear) into an lgs_camera array."""
+    arr = (LgsCamera * len(cams))()
+    for k, c in enumerate(cams):
+        vm = np.asarray(c.viewmat, np.float32).reshape(12)
+        arr[k] = LgsCamera(float(c.fx), float(c.fy), float(c.cx), float(c.cy), int(c.width),
+                           int(c.height), (ctypes.c_float * 12)(*vm.tolist()), float(c.znear))
+    return arr
+
+
+def _dtype_code(t):
+    if t.dtype == torch.float32:
+        return F32
+    if t.dtype == torch.bfloat16:
+        return BF16
+    raise LgsError(f"unsupported channel dtype {t.dtype}")
+
+
+def tile_grid(cam):
+    return (int(cam.width) + TILE - 1) // TILE, (int(cam.height) + TILE - 1) // TILE
+
+
+# ---------------------------------------------------------------- entry points
+
+def gs_project(means, quats, log_scales, opacity_logits, cams):
+    """Returns proj [C*N, 8] float32 and rect [C*N, 4] int16 (uint16 bits)."""
+    lib = load()
+    n, c = means.shape[0], len(cams)
+    dev = means.device
+    proj = torch.empty((c * n, PROJ_STRIDE), dtype=torch.float32, device=dev)
+    rect = torch.empty((c * n, 4), dtype=torch.int16, device=dev)
+    ca = cameras(cams)
+    _check(lib.gs_project(_p(means), _p(quats), _p(log_scales), _p(opacity_logits), n, ca, c,
+                          _p(proj), _p(rect), _stream()), "gs_project")
+    return proj, rect
+
+
+class BinBuffers:
+    """Caller-owned buffers of gs_bin_sort for one (n, cameras, grid),
+    grown when the instance count exceeds the capacity."""
+
+    def __init__(self, n, n_cams, tiles_x, tiles_y, capacity, device, want_keys=False):
+        self.n, self.n_cams, self.tiles_x, self.tiles_y = n, n_cams, tiles_x, tiles_y
+        self.device, self.want_keys = device, want_keys
+        self.ranges = torch.empty((n_cams * tiles_x * tiles_y, 2), dtype=torch.int32, device=device)
+        self.k_dev = torch.zeros(1, dtype=torch.int64, device=device)
+        self.resize(capacity)
+
+    def resize(self, capacity):
+        lib = load()
+        self.capacity = int(capacity)
+        self.ids = torch.empty(max(self.capacity, 1), dtype=torch.int32, device=self.device)
+        self.keys = (torch.empty(max(self.capacity, 1), dtype=torch.int64, device=self.device)
+                     if self.want_keys else None)
+        ws = lib.gs_bin_sort_workspace(self.n, self.n_cams, self.tiles_x, self.tiles_y,
+                                       self.capacity)
+        self.workspace = torch.empty(max(int(ws), 256), dtype=torch.uint8, device=self.device)
+        self.workspace_bytes = int(ws)
+
+
+def gs_bin_sort(proj, rect, bufs: BinBuffers, stream=None):
+    """Enqueues binning into ``bufs`` (no synchronisation)."""
+    lib = load()
+    _check(lib.gs_bin_sort(_p(proj), _p(rect), bufs.n, bufs.n_cams, bufs.tiles_x, bufs.tiles_y,
+                           bufs.capacity, _p(bufs.ids), _p(bufs.ranges), _p(bufs.keys),
+                           _p(bufs.k_dev), _p(bufs.workspace), bufs.workspace_bytes,
+                           stream or _stream()), "gs_bin_sort")
+
+
+def bin_sort_checked(proj, rect, bufs: BinBuffers, headroom=1.25):
+    """gs_bin_sort, then reads K and re-runs with a larger capacity if it
+    overflowed.  Returns K (this synchronises once)."""
+    gs_bin_sort(proj, rect, bufs)
+    k = int(bufs.k_dev.item())
+    if k > bufs.capacity:
+        bufs.resize(int(math.ceil(k * headroom)) + 1024)
+        gs_bin_sort(proj, rect, bufs)
+    return k
+
+
+def gs_render_fwd(proj, bufs: BinBuffers, cams, colors, feats, bg=(0.0, 0.0, 0.0),
+                  want_count=False):
+    """Returns dict(rgb [C,H,W,3], depth [C,H,W], feat [C,H,W,D], T_final,
+    last, n_contrib (if asked))."""
+    lib = load()
+    c = len(cams)
+    h, w = int(cams[0].height), int(cams[0].width)
+    d = int(feats.shape[1])
+    dev = proj.device
+    out = dict(rgb=torch.empty((c, h, w, 3), dtype=torch.float32, device=dev),
+               depth=torch.empty((c, h, w), dtype=torch.float32, device=dev),
+               feat=torch.empty((c, h, w, d), dtype=torch.float32, device=dev),
+               T_final=torch.empty((c, h, w), dtype=torch.float32, device=dev),
+               last=torch.empty((c, h, w), dtype=torch.int32, device=dev))
+    out["n_contrib"] = (torch.empty((c, h, w), dtype=torch.int32, device=dev) if want_count
+                        else None)
+    bga = (ctypes.c_float * 3)(*[float(x) for x in bg])
+    ca = cameras(cams)
+    _check(lib.gs_render_fwd(_p(proj), _p(bufs.ids), _p(bufs.ranges), bufs.n, ca, c, _p(colors),
+                             _p(feats), d, _dtype_code(feats), bga, _p(out["rgb"]),
+                             _p(out["depth"]), _p(out["feat"]), _p(out["T_final"]),
+                             _p(out["last"]), _p(out["n_contrib"]), _stream()), "gs_render_fwd")
+    return out
+
+
+def gs_render_bwd(params, proj, bufs: BinBuffers, cams, colors, feats, fwd, d_rgb, d_depth, d_feat,
+                  grads, grad2d, bg=(0.0, 0.0, 0.0)):
+    """Accumulates parameter gradients into ``grads`` (dict of tensors named
+    means, quats, log_scales, opacity_logits, colors, feats).  ``params`` =
+    (means, quats, log_scales, opacity_logits); ``grad2d`` [C*N, 8] scratch."""
+    lib = load()
+    means, quats, log_scales, logits = params
+    c = len(cams)
+    d = int(feats.shape[1])
+    bga = (ctypes.c_float * 3)(*[float(x) for x in bg])
+    ca = cameras(cams)
+    _check(lib.gs_render_bwd(_p(means), _p(quats), _p(log_scales), _p(logits), _p(proj),
+                             _p(bufs.ids), _p(bufs.ranges), bufs.n, ca, c, _p(colors), _p(feats), d,
+                             _dtype_code(feats), bga, _p(fwd["T_final"]), _p(fwd["last"]),
+                             _p(d_rgb), _p(d_depth), _p(d_feat), _p(grad2d), _p(grads["means"]),
+                             _p(grads["quats"]), _p(grads["log_scales"]),
+                             _p(grads["opacity_logits"]), _p(grads["colors"]), _p(grads["feats"]),
+                             _stream()), "gs_render_bwd")
+
+
+def lgs_l1_loss(pred, target, weight, grad, loss_dev):
+    """grad = weight sign(pred - target)/count; loss_dev += weight mean|.|."""
+    lib = load()
+    _check(lib.lgs_l1_loss(_p(pred), _p(target), _dtype_code(target), pred.numel(), float(weight),
+                           _p(grad), _p(loss_dev), _stream()), "lgs_l1_loss")

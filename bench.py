@@ -1,0 +1,496 @@
+#!/usr/bin/env python
+"""Throughput of one mapping-loop step (fwd + bwd) on GB300.
+
+Workload "indoor-640x480-300k": 300k Gaussians uniform in a 6x6x3 m room,
+one 640x480 keyframe (fx=fy=525) on a 2 m arc around the room centre,
+RGB + depth + a 16-d language feature.  A step is the whole hot path:
+projection, tile binning, compositing, the L1 terms of Eq. 1, the frozen
+decoder with the L1 distillation loss of Eq. 2 and its gradient, and the
+render backward down to every Gaussian parameter.  The plain path renders
+all 512 embedding channels instead of the decoder (reported beside it).
+
+Prints ONE JSON line (rank 0).  ``--impl reference`` times the FP64 CPU
+oracle on bounded crops of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "fwd+bwd Mpix/s, 300k Gaussians 640x480, 16-d vs plain 512-d; % of roofline"
+WORKLOAD = "indoor-640x480-300k"
+L2_BYTES = 129 * 2 ** 20
+FP32_PEAK_NOTE = "152 SMs x 128 FP32 lanes x 2 FLOP x 2.07 GHz"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="lgs", choices=["lgs", "reference"])
+    ap.add_argument("--no-plain", action="store_true", help="skip the plain 512-d path")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the oracle cpu_baseline")
+    ap.add_argument("--ae-steps", type=int, default=200)
+    return ap.parse_args()
+
+
+# --------------------------------------------------------------------------- workload
+
+def build_workload(rank, ae_steps):
+    """Host arrays of the workload: geometry, 512-d Gaussian embeddings,
+    targets and the embedding frames the autoencoder trains on."""
+    from paper_2511_16144_gb300 import synth
+    scene, cams = synth.indoor(n_cams=8)
+    cam = cams[rank % 8]
+    rng = np.random.default_rng(1003 + rank)
+    cent = synth.embedding_centroids()
+    k = rng.integers(0, cent.shape[0], size=scene.n)
+    g512 = synth.unit_rows(cent[k] + 0.02 * rng.standard_normal((scene.n, 512)).astype(np.float32))
+    (rgb_t, dep_t, _), = synth.targets([cam], feat_dim=16, seed=2001 + rank)
+    f_gt = synth.embedding_map(rng, cent, cam.width, cam.height)
+    train_frames = [synth.embedding_map(rng, cent, 320, 240).reshape(-1, 512) for _ in range(4)]
+    return dict(scene=scene, cam=cam, g512=g512.astype(np.float32), rgb_t=rgb_t, dep_t=dep_t,
+                f_gt=f_gt, train=np.concatenate(train_frames))
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during timing."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index, self.proc, self.lines = index, None, []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [l for l in out.splitlines() if l.strip()]
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in self.lines:
+            f = [x.strip() for x in l.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return json.load(f), "measured"
+    except (OSError, ValueError):
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
+                "sm_max_mhz": 2070.0}, "fallback"
+
+
+# --------------------------------------------------------------------------- GPU arm
+
+def run_gpu(args, rank, world):
+    import torch
+    from paper_2511_16144_gb300 import build, lgs, synth
+    from paper_2511_16144_gb300.ae import AutoEncoder
+    from paper_2511_16144_gb300.pipeline import MappingStep
+    from paper_2511_16144_gb300.render import DeviceScene
+
+    build.build()
+    lgs.load()
+    dev = torch.device("cuda", torch.cuda.current_device())
+    W = build_workload(rank, args.ae_steps)
+    scene, cam = W["scene"], W["cam"]
+
+    # scene-adaptive autoencoder: pretrained online as an autoencoder on the
+    # frames' own embeddings (Sec. IV-A.2), then the encoder prior gives the
+    # Gaussians' 16-d features (Sec. III-B.2)
+    enc, dec = synth.ae_init(seed=3001)
+    model = AutoEncoder(enc, dec, device=dev)
+    train = torch.from_numpy(W["train"]).to(dev).bfloat16()
+    gen = torch.Generator(device=dev).manual_seed(rank)
+    ae_losses = []
+    t0 = time.time()
+    for _ in range(args.ae_steps):
+        idx = torch.randint(0, train.shape[0], (65536,), device=dev, generator=gen)
+        ae_losses.append(model.train_step(train[idx].contiguous(), lr=1e-3))
+    torch.cuda.synchronize()
+    ae_train_s = time.time() - t0
+    ae_losses = [float(l.item()) for l in ae_losses]
+    g512_bf = torch.from_numpy(W["g512"]).to(dev).bfloat16()
+    f16 = model.encode(g512_bf)
+
+    geom = DeviceScene.from_host(scene, device=dev)
+    colors_bf = geom.colors.bfloat16()
+    s16_bf = DeviceScene(geom.means, geom.quats, geom.log_scales, geom.opacity_logits,
+                         colors_bf, f16.bfloat16().contiguous())
+    s16_f32 = DeviceScene(geom.means, geom.quats, geom.log_scales, geom.opacity_logits,
+                          geom.colors, f16.contiguous())
+    rgb_t = torch.from_numpy(W["rgb_t"][None]).to(dev).contiguous()
+    dep_t = torch.from_numpy(W["dep_t"][None]).to(dev).contiguous()
+    f_gt = torch.from_numpy(W["f_gt"].reshape(-1, 512)).to(dev).bfloat16().contiguous()
+    cams = [cam]
+
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
+
+    def timed(step, k, warm, clocks=None, events_inside=None):
+        """Captures step.run in a CUDA graph; returns per-replay ms (L2
+        flushed before each replay, outside the timed events)."""
+        s = torch.cuda.Stream(device=dev)
+        s.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(s):
+            step.run()  # eager once (also sets kernel attributes)
+        torch.cuda.current_stream().wait_stream(s)
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            step.run()
+        torch.cuda.synchronize()
+        nodes = int(lgs.load().lgs_graph_kernel_nodes(ctypes_ptr(g.raw_cuda_graph()))) \
+            if hasattr(g, "raw_cuda_graph") else -1
+        for _ in range(warm):
+            flush.fill_(1.0)
+            g.replay()
+        torch.cuda.synchronize()
+        times = []
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(k)]
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        ctx = clocks if clocks is not None else _Null()
+        with ctx:
+            for i in range(k):
+                flush.fill_(1.0)
+                ev[i][0].record()
+                g.replay()
+                ev[i][1].record()
+            torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        times = [a.elapsed_time(b) for a, b in ev]
+        return times, g, nodes
+
+    results = {}
+    step16 = MappingStep(s16_bf, cams, rgb_t, dep_t, f_gt, model=model)
+    clocks = Clocks(torch.cuda.current_device())
+    t16, g16, nodes16 = timed(step16, args.steps, args.warmup, clocks)
+    k_inst = int(step16.k_dev.item())
+    ms16 = float(np.mean(t16))
+    if world > 1:
+        tt = torch.tensor([sum(t16)], device=dev)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(tt.item())
+    else:
+        total_ms = float(sum(t16))
+    pixels = step16.pixels
+    value = world * pixels * args.steps / 1e6 / (total_ms / 1e3)
+
+    # per-call durations of one eager step (events on the launching stream)
+    calls = per_call_times(step16, flush, reps=5)
+    rf = roofline_render_bwd(step16, calls)
+
+    # FP32-channel variant and the plain 512-channel path (same geometry)
+    extra = {}
+    step16f = MappingStep(s16_f32, cams, rgb_t, dep_t, f_gt, model=model,
+                          capacity=step16.bufs.capacity)
+    tf, _, _ = timed(step16f, max(5, args.steps // 2), 2)
+    extra["fp32_channels"] = {"value": pixels / 1e6 / (np.mean(tf) / 1e3), "ms_per_step": float(np.mean(tf))}
+    plain = None
+    cos_err = None
+    if not args.no_plain:
+        s512 = DeviceScene(geom.means, geom.quats, geom.log_scales, geom.opacity_logits,
+                           colors_bf, g512_bf)
+        step512 = MappingStep(s512, cams, rgb_t, dep_t, f_gt, model=None,
+                              capacity=step16.bufs.capacity)
+        tp, _, _ = timed(step512, max(5, args.steps // 2), 2)
+        plain = {"value": pixels / 1e6 / (np.mean(tp) / 1e3), "ms_per_step": float(np.mean(tp)),
+                 "channels": "bf16", "feat_dim": 512}
+        # decoded 16-d features against the plain 512-channel render, per pixel
+        step512.run()
+        step16.run()
+        torch.cuda.synchronize()
+        y = model.decode(step16.out["feat"].reshape(-1, 16).contiguous())
+        ref = step512.out["feat"].reshape(-1, 512)
+        nr = ref.norm(dim=1)
+        keep = nr > 1e-6
+        cos = (y * ref).sum(1)[keep] / (y.norm(dim=1)[keep] * nr[keep]).clamp_min(1e-30)
+        cos_err = {"mean": float((1 - cos).mean().item()), "excluded_pixels": int((~keep).sum().item())}
+        plain["speedup_of_16d"] = value / world / plain["value"]
+        del step512
+
+    # end to end through the C ABI with host buffers: per step the keyframe's
+    # targets (RGB, depth, F_gt) go host -> device from pinned memory and the
+    # loss comes back
+    e2e = measure_e2e(step16, g16, flush, args.steps, args.warmup)
+
+    if rank == 0:
+        peaks, kind = measured_peaks()
+        cpu = None if args.no_cpu else cpu_baseline(W, budget_s=15.0)
+        line = {
+            "metric": METRIC, "value": value, "unit": "Mpix/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms16,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "bf16", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "gaussians": scene.n, "cameras": 1, "width": 640,
+                       "height": 480, "feat_dim": 16, "channels": "bf16",
+                       "precision": "fp32 alpha/T/accumulation; bf16 channels and AE GEMMs",
+                       "instances": k_inst, "l2": "flushed before every step (258 MB write)",
+                       "graph": "one CUDA graph per step", "parallelism": "replicas" if world > 1 else "single"},
+            "gpu_launches": nodes16 * args.steps if nodes16 > 0 else None,
+            "kernels_per_step": nodes16,
+            "roofline": dict(rf, peak_source=kind),
+            "e2e": e2e,
+            "clocks": clocks.summary(),
+            "plain_512": plain, "decoded_cosine_error": cos_err, "variants": extra,
+            "per_call_ms": calls,
+            "ae_pretrain": {"steps": args.ae_steps, "loss_first": ae_losses[0],
+                            "loss_last": ae_losses[-1], "seconds": ae_train_s},
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+
+
+class _Null:
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        return False
+
+
+def ctypes_ptr(h):
+    import ctypes
+    return ctypes.c_void_p(int(h))
+
+
+def per_call_times(step, flush, reps=5):
+    """Average device time (ms) of each C-ABI call group of the step: each is
+    captured in its own CUDA graph and replayed between CUDA events on the
+    launching stream, with L2 flushed before every replay."""
+    import torch
+    step.run()
+    torch.cuda.synchronize()
+    out = {}
+    for name, fn in step.calls():
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            fn()
+        torch.cuda.synchronize()
+        flush.fill_(1.0)
+        g.replay()
+        ts = []
+        for _ in range(reps):
+            flush.fill_(1.0)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            g.replay()
+            b.record()
+            torch.cuda.synchronize()
+            ts.append(a.elapsed_time(b))
+        out[name] = float(np.mean(ts))
+        del g
+    return out
+
+
+def roofline_render_bwd(step, calls):
+    """Achieved FP32 rate of gs_render_bwd against the FP32 ALU peak.
+
+    Algorithmic FLOPs per launch (the per-unit figures of the hot-path
+    scope): 10 per evaluated (pixel, instance) pair E and 4(4+d) + 25 per
+    blended pair B, with E = sum over pixels of `last` (instances walked
+    back to front) and B = the number blended, read from the forward."""
+    import torch
+    E = float(step.out["last"].double().sum().item())
+    B = float(step.count_blended().double().sum().item())
+    d = step.D
+    flops = 10.0 * E + (4.0 * (4 + d) + 25.0) * B
+    ms = calls["gs_render_bwd"]
+    achieved = flops / (ms / 1e3) / 1e12
+    peaks, _ = measured_peaks()
+    peak = 152 * 128 * 2 * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12
+    return {"kernel": "gs_render_bwd (raster backward + projection chain rule)", "bound": "alu",
+            "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+            "traffic": None, "flops_per_launch": flops, "E_pairs": E, "B_pairs": B,
+            "ms_per_launch": ms, "peak_note": FP32_PEAK_NOTE}
+
+
+def measure_e2e(step, graph, flush, k, warm):
+    import torch
+    rgb_h = step.rgb_t.cpu().pin_memory()
+    dep_h = step.depth_t.cpu().pin_memory()
+    fgt_h = step.feat_t.cpu().pin_memory()
+    loss_h = torch.empty(1, dtype=torch.float32).pin_memory()
+
+    def one():
+        step.rgb_t.copy_(rgb_h, non_blocking=True)
+        step.depth_t.copy_(dep_h, non_blocking=True)
+        step.feat_t.copy_(fgt_h, non_blocking=True)
+        graph.replay()
+        loss_h.copy_(step.loss, non_blocking=True)
+
+    for _ in range(warm):
+        flush.fill_(1.0)
+        one()
+    torch.cuda.synchronize()
+    ts = []
+    for _ in range(k):
+        flush.fill_(1.0)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        one()
+        b.record()
+        b.synchronize()
+        ts.append(a.elapsed_time(b))
+    ms = float(np.mean(ts))
+    h2d = sum(t.numel() * t.element_size() for t in (rgb_h, dep_h, fgt_h))
+    return {"value": step.pixels / 1e6 / (ms / 1e3), "unit": "Mpix/s", "ms_per_step": ms,
+            "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": 4}
+
+
+# --------------------------------------------------------------------------- oracle
+
+def oracle_prepare(W):
+    """Oracle-side inputs that are not part of a step: the FP64 autoencoder
+    at its initial weights and the Gaussians' 16-d encoder prior."""
+    from oracle import ae
+    from paper_2511_16144_gb300 import synth
+    enc, dec = [[[w.astype(np.float64), b.astype(np.float64)] for w, b in L]
+                for L in synth.ae_init(seed=3001)]
+    sc = W["scene"].with_feats(ae.encode(enc, W["g512"]).astype(np.float32))
+    return sc, dec
+
+
+def oracle_step(W, side, prep):
+    """One bounded sample of the workload on the FP64 oracle: a side x side
+    centre crop rendered (RGB, depth, 16-d feature), decoded against F_gt
+    with its gradient, and back-propagated to every Gaussian parameter."""
+    import oracle
+    from oracle import ae
+    sc, dec = prep
+    cam = W["cam"]
+    x0, y0 = cam.width // 2 - side // 2, cam.height // 2 - side // 2
+    crop = (x0, y0, side, side)
+    o = oracle.render(sc, cam, crop=crop)
+    _, g_rgb = oracle.l1_loss_grad(o["rgb"], W["rgb_t"][y0:y0 + side, x0:x0 + side])
+    _, g_dep = oracle.l1_loss_grad(o["depth"], W["dep_t"][y0:y0 + side, x0:x0 + side], 0.1)
+    f_gt = W["f_gt"][y0:y0 + side, x0:x0 + side].reshape(-1, 512)
+    _, dz = ae.distill(dec, o["feat"].reshape(-1, 16), f_gt)
+    oracle.render_backward(sc, cam, g_rgb, g_dep, dz.reshape(side, side, 16), crop=crop)
+    return side * side
+
+
+def cpu_baseline(W, budget_s=15.0):
+    """Times the oracle on centre crops sized to about budget_s seconds."""
+    import oracle
+    oracle.build()
+    prep = oracle_prepare(W)
+    t0 = time.time()
+    oracle_step(W, 8, prep)
+    t_small = max(time.time() - t0, 1e-3)
+    side = int(max(8, min(128, 8 * math.sqrt(budget_s / t_small))))
+    t0 = time.time()
+    px = oracle_step(W, side, prep)
+    dt = time.time() - t0
+    return {"value": px / 1e6 / dt, "unit": "Mpix/s", "cores": oracle.num_threads(),
+            "kind": "oracle", "seconds": dt,
+            "sample": f"{side}x{side} centre crop of the 640x480 frame, 300k Gaussians: "
+                      "FP64 brute-force render + decoder L1 + analytic backward"}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    W = build_workload(0, 0)
+    prep = oracle_prepare(W)
+    t0 = time.time()
+    oracle_step(W, 8, prep)
+    t_small = max(time.time() - t0, 1e-3)
+    per_step = 150.0 / max(args.steps + args.warmup, 1)
+    side = int(max(8, min(160, 8 * math.sqrt(per_step / t_small))))
+    for _ in range(args.warmup):
+        oracle_step(W, side, prep)
+    ts = []
+    for _ in range(args.steps):
+        t0 = time.time()
+        px = oracle_step(W, side, prep)
+        ts.append(time.time() - t0)
+    ms = 1e3 * float(np.mean(ts))
+    value = px / 1e6 / (ms / 1e3)
+    line = {"metric": METRIC, "value": value, "unit": "Mpix/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "impl": "reference",
+            "config": {"workload": WORKLOAD, "gaussians": W["scene"].n, "sample": f"{side}x{side} centre crop"},
+            "cpu_baseline": {"value": value, "unit": "Mpix/s", "cores": oracle.num_threads(),
+                             "kind": "oracle",
+                             "sample": f"{side}x{side} centre crop per step, FP64 brute force"},
+            "e2e": {"value": value, "unit": "Mpix/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if args.impl == "reference":
+        if world > 1 and rank != 0:
+            return
+        # the oracle is plain CPU code; start its thread pool before any GPU work
+        run_reference(args, rank, world)
+        return
+    import torch
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        torch.distributed.init_process_group("nccl", device_id=torch.device("cuda", local))
+    try:
+        run_gpu(args, rank, world)
+    finally:
+        if world > 1:
+            torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

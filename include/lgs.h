@@ -71,6 +71,15 @@ const char* lgs_version(void);
 /* Message of the last failing call on this host thread ("" if none). */
 const char* lgs_last_error(void);
 
+/* Number of kernel nodes in a captured CUDA graph (a cudaGraph_t, e.g. one
+ * mapping step captured from the calls below), or -1 on error.  Utility for
+ * counting launches; the paper has no counterpart. */
+int64_t lgs_graph_kernel_nodes(void* graph);
+
+/* Enqueues a zero fill of `bytes` bytes of device memory (a memset, no
+ * kernel), e.g. gradient accumulators before gs_render_bwd. */
+lgs_status lgs_zero(void* dev, size_t bytes, void* stream);
+
 /* ------------------------------------------------------------------------
  * gs_project -- EWA projection of every Gaussian into every camera.
  *
@@ -196,6 +205,84 @@ lgs_status gs_render_bwd(const float* means, const float* quats, const float* lo
  * ---------------------------------------------------------------------- */
 lgs_status lgs_l1_loss(const float* pred, const void* target, int target_dtype, int64_t count,
                        float weight, float* grad, float* loss_dev, void* stream);
+
+/* ------------------------------------------------------------------------
+ * Scene-adaptive autoencoder (Sec. IV-A.2: stacks of 1x1 convolutions, i.e.
+ * one MLP applied per pixel, pretrained as an autoencoder; Sec. III-B.3
+ * Eq. 2: distillation through the frozen decoder; Sec. III-B.4 Eq. 3:
+ * encoder adaptation).  Layers 0-3 are the encoder 512-256-128-64-16, layers
+ * 4-7 the decoder 16-64-128-256-512; layer l maps width w[l] to w[l+1] with
+ * y = x W_l^T + b_l, GELU (erf form) after every layer except 3 and 7.
+ * GEMMs run on the tensor cores with BF16 operands and FP32 accumulation;
+ * activations between layers are BF16.  Pixels are rows: x [P, 512],
+ * z [P, 16], all row-major.
+ * ---------------------------------------------------------------------- */
+#define LGS_AE_LAYERS 8
+#define LGS_AE_ENCODE 0
+#define LGS_AE_DECODE 1
+#define LGS_AE_TRAIN 2
+#define LGS_AE_RECON 0     /* pretraining: L = mean_k (y-x)^2 + 1 - cos(y, x) */
+#define LGS_AE_ENC_ADAPT 1 /* Eq. 3: L = mean |E(x) - F_render|, decoder frozen */
+
+/* Inference weights: W[l] bf16 [w[l+1], w[l]] row-major, Wt[l] its
+ * transpose (bf16 [w[l], w[l+1]], used by the backward), b[l] fp32.  All
+ * 16-byte aligned device memory (ae_pack writes both copies). */
+typedef struct {
+  const uint16_t* W[LGS_AE_LAYERS];
+  const uint16_t* Wt[LGS_AE_LAYERS];
+  const float* b[LGS_AE_LAYERS];
+} lgs_ae_weights;
+
+/* Training state: FP32 master weights and biases, Adam moments, the last
+ * step's gradients, and the BF16 copies (Wbf = W, Wtbf = W^T) that the GEMMs
+ * read.  step counts Adam steps and is incremented by ae_train_step (host
+ * field). */
+typedef struct {
+  float* W[LGS_AE_LAYERS];
+  float* b[LGS_AE_LAYERS];
+  float* mW[LGS_AE_LAYERS];
+  float* vW[LGS_AE_LAYERS];
+  float* mb[LGS_AE_LAYERS];
+  float* vb[LGS_AE_LAYERS];
+  float* gW[LGS_AE_LAYERS];
+  float* gb[LGS_AE_LAYERS];
+  uint16_t* Wbf[LGS_AE_LAYERS];
+  uint16_t* Wtbf[LGS_AE_LAYERS];
+  int64_t step;
+} lgs_ae_state;
+
+/* Scratch bytes for P pixels of LGS_AE_ENCODE, LGS_AE_DECODE or
+ * LGS_AE_TRAIN work (0 for a bad argument). */
+size_t ae_workspace_bytes(int64_t P, int what);
+
+/* z [P,16] fp32 = E_phi(x), x bf16 [P,512] (the encoder prior of new
+ * Gaussians' features, Sec. III-B.2). */
+lgs_status ae_encode(const lgs_ae_weights* w, const uint16_t* x, int64_t P, float* z,
+                     void* workspace, size_t workspace_bytes, void* stream);
+
+/* Decoder D_theta on z [P,16] fp32 (the rendered F_render).  With target
+ * (F_gt, bf16 [P,512]): loss_dev += weight * mean|D(z) - F_gt| (Eq. 2) and
+ * dz [P,16] fp32 = its gradient w.r.t. z (overwritten; the decoder is
+ * frozen).  With y_opt: y_opt [P,512] fp32 = D(z).  Either or both. */
+lgs_status ae_decode(const lgs_ae_weights* w, const float* z, int64_t P, const uint16_t* target,
+                     float weight, float* loss_dev, float* dz, float* y_opt, void* workspace,
+                     size_t workspace_bytes, void* stream);
+
+/* One Adam step (lr; beta 0.9, 0.999; eps 1e-8) on a batch x bf16 [P,512].
+ * mode LGS_AE_RECON trains both networks on the reconstruction loss;
+ * LGS_AE_ENC_ADAPT trains layers 0-3 on Eq. 3 against target = F_render
+ * fp32 [P,16].  loss_dev += the batch loss (before the update); st->gW/gb
+ * hold the gradients; the BF16 copies are refreshed. */
+lgs_status ae_train_step(lgs_ae_state* st, const uint16_t* x, const float* target, int64_t P,
+                         int mode, float lr, float* loss_dev, void* workspace,
+                         size_t workspace_bytes, void* stream);
+
+/* Refreshes Wbf / Wtbf of layers first..last from the FP32 masters. */
+lgs_status ae_pack(lgs_ae_state* st, int first, int last, void* stream);
+
+/* Reads and clears the device error word that kernels with bounded waits
+ * set when a wait gives up (0 = none).  Synchronises the device. */
+lgs_status lgs_device_error(int* code);
 
 #ifdef __cplusplus
 }

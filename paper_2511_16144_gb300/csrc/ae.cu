@@ -1,0 +1,844 @@
+// Scene-adaptive autoencoder on the tensor cores (tcgen05, TMEM accumulators).
+//
+// LEGO-SLAM Sec. IV-A.2: encoder E_phi and decoder D_theta are stacks of 1x1
+// convolutions -- the same MLP applied to every pixel -- compressing the
+// extractor's high-dimensional features to 16 channels.  They are pretrained
+// as an autoencoder; Sec. III-B.3 Eq. 2 distils the rendered 16-d map through
+// the frozen decoder with an L1 loss; Sec. III-B.4 Eq. 3 adapts the encoder
+// alone with an L1 loss against the rendered map.
+//
+// Widths 512-256-128-64-16 and the mirrored decoder, GELU on hidden layers,
+// bias everywhere (layers 0-3 encoder, 4-7 decoder).  GEMMs take BF16
+// operands and accumulate in FP32 in tensor memory; activations between
+// layers are BF16.
+//
+// Kernels
+//   layer_kernel<NT, KC>: out[P, N] = epilogue(A[P, K] . W[N, K]^T) for one
+//     128-row tile per CTA, K streamed in chunks of KC through a two-stage
+//     cp.async pipeline into the canonical K-major layout; one thread issues
+//     the MMAs, all 128 threads run the epilogue from TMEM (thread = row).
+//     Epilogues: bias+GELU (+ pre-activation), linear, GELU'-gated backward,
+//     and the fused losses (L1 against a target, or L2 + (1 - cos)) that
+//     also emit the output gradient.
+//   dw_kernel<KT>: dW[N, K] += sum_p G[p, n] X[p, k] over a pixel range; the
+//     pixel dimension is the MMA's K, so both operands are transposed in 8x8
+//     blocks while staging.
+//   colsum, adam and pack kernels (SIMT).
+#include "common.cuh"
+#include "kernels.cuh"
+#include "tc05.cuh"
+
+namespace lgs {
+
+constexpr int kAeLayers = LGS_AE_LAYERS;
+constexpr int kAeWidths[9] = {512, 256, 128, 64, 16, 64, 128, 256, 512};
+constexpr uint32_t kSpinLimit = 1u << 26;
+
+__device__ unsigned g_ae_error;  // set when a bounded wait gives up
+
+enum Epi : int {
+  EPI_GELU = 0,      // out = gelu(acc + b) (bf16), pre = acc + b (bf16, optional)
+  EPI_LIN_F32 = 1,   // out = acc + b (f32)
+  EPI_LIN_BF16 = 2,  // out = acc + b (bf16)
+  EPI_DGELU = 3,     // out = acc * gelu'(pre_in) (bf16)
+  EPI_DX_F32 = 4,    // out = acc (f32)
+  EPI_DX_BF16 = 5,   // out = acc (bf16)
+  EPI_L1_BF16T = 6,  // y = acc + b; loss += s|y - t|; out = s sign(y - t) (bf16); t bf16
+  EPI_L1_F32T = 7,   // same with an f32 target
+  EPI_RECON = 8      // y = acc + b vs x: loss += s (mean (y-x)^2 + 1 - cos); out = dL/dy
+};
+
+struct LayerArgs {
+  const void* A;
+  int a_f32;
+  const __nv_bfloat16* W;
+  const float* bias;
+  int64_t P;
+  int K, N;
+  int epi;
+  __nv_bfloat16* out_bf;
+  float* out_f32;
+  __nv_bfloat16* pre_out;
+  const __nv_bfloat16* pre_in;
+  const void* target;
+  float scale;
+  float* loss;
+};
+
+__device__ __forceinline__ float gelu_f(float x) {
+  return 0.5f * x * (1.f + erff(x * 0.70710678118654752f));
+}
+__device__ __forceinline__ float gelu_grad_f(float x) {
+  return 0.5f * (1.f + erff(x * 0.70710678118654752f)) +
+         x * 0.39894228040143268f * expf(-0.5f * x * x);
+}
+
+__device__ __forceinline__ void store_bf16x32(__nv_bfloat16* dst, const float* v, int n) {
+  // n = 16 or 32 values to a 16-byte aligned destination
+#pragma unroll
+  for (int q = 0; q < 4; q++) {
+    if (q * 8 >= n) break;
+    uint4 u;
+    __nv_bfloat162* h = reinterpret_cast<__nv_bfloat162*>(&u);
+#pragma unroll
+    for (int k = 0; k < 4; k++) h[k] = __floats2bfloat162_rn(v[8 * q + 2 * k], v[8 * q + 2 * k + 1]);
+    reinterpret_cast<uint4*>(dst)[q] = u;
+  }
+}
+
+__device__ __forceinline__ void load_bf16x32(const __nv_bfloat16* src, float* v, int n) {
+#pragma unroll
+  for (int q = 0; q < 4; q++) {
+    if (q * 8 >= n) break;
+    uint4 u = reinterpret_cast<const uint4*>(src)[q];
+    const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&u);
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+      float2 f = __bfloat1622float2(h[k]);
+      v[8 * q + 2 * k] = f.x;
+      v[8 * q + 2 * k + 1] = f.y;
+    }
+  }
+}
+
+__device__ __forceinline__ void report_timeout() { atomicOr(&g_ae_error, 1u); }
+
+template <int NT, int KC>
+struct LayerSmem {
+  static constexpr int A_BYTES = 128 * KC * 2;
+  static constexpr int B_BYTES = NT * KC * 2;
+  static constexpr int STAGE = A_BYTES + B_BYTES;
+  static constexpr size_t total = 2 * STAGE + 64;
+  static constexpr uint32_t TCOLS = NT < 32 ? 32 : NT;
+};
+
+template <int NT, int KC>
+__global__ void __launch_bounds__(128, 1) layer_kernel(LayerArgs a) {
+  using L = LayerSmem<NT, KC>;
+  extern __shared__ __align__(1024) uint8_t sm[];
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(sm + 2 * L::STAGE);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + 2 * L::STAGE + 16);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int64_t row0 = (int64_t)blockIdx.x * 128;
+  const int n0 = blockIdx.y * NT;
+  const int K = a.K;
+  if (warp == 0) tc::tmem_alloc(tslot, L::TCOLS);
+  if (tid == 0) {
+    tc::mbar_init(&mbar[0], 1);
+    tc::mbar_init(&mbar[1], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  tc::fence_before();
+  __syncthreads();
+  tc::fence_after();
+  const uint32_t tmem = *tslot;
+  bool ok = true;
+
+  const int nk = K / KC;
+  constexpr uint32_t SBO = KC * 16;
+  for (int kc = 0; kc < nk && ok; kc++) {
+    const int s = kc & 1;
+    if (kc >= 2 && !tc::mbar_wait(&mbar[s], ((kc - 2) >> 1) & 1, kSpinLimit)) {
+      ok = false;
+      break;
+    }
+    uint8_t* sa = sm + s * L::STAGE;
+    uint8_t* sb = sa + L::A_BYTES;
+    const uint32_t sa_u = tc::smem_addr(sa), sb_u = tc::smem_addr(sb);
+    // A: 128 rows x KC columns
+    constexpr int APIECES = 128 * (KC / 8);
+    for (int i = tid; i < APIECES; i += 128) {
+      const int r = i / (KC / 8), c = i % (KC / 8);
+      const int64_t p = row0 + r;
+      const bool valid = p < a.P;
+      const int64_t pc = valid ? p : 0;
+      const uint32_t off = tc::core_offset(r, c, KC);
+      if (a.a_f32) {
+        const float4* src = reinterpret_cast<const float4*>(
+            reinterpret_cast<const float*>(a.A) + pc * K + kc * KC + c * 8);
+        float4 f0 = valid ? src[0] : make_float4(0.f, 0.f, 0.f, 0.f);
+        float4 f1 = valid ? src[1] : make_float4(0.f, 0.f, 0.f, 0.f);
+        uint4 u;
+        __nv_bfloat162* h = reinterpret_cast<__nv_bfloat162*>(&u);
+        h[0] = __floats2bfloat162_rn(f0.x, f0.y);
+        h[1] = __floats2bfloat162_rn(f0.z, f0.w);
+        h[2] = __floats2bfloat162_rn(f1.x, f1.y);
+        h[3] = __floats2bfloat162_rn(f1.z, f1.w);
+        *reinterpret_cast<uint4*>(sa + off) = u;
+      } else {
+        const __nv_bfloat16* src =
+            reinterpret_cast<const __nv_bfloat16*>(a.A) + pc * K + kc * KC + c * 8;
+        tc::cp_async16_zfill(sa_u + off, src, valid);
+      }
+    }
+    // B: NT weight rows x KC columns
+    constexpr int BPIECES = NT * (KC / 8);
+    for (int i = tid; i < BPIECES; i += 128) {
+      const int r = i / (KC / 8), c = i % (KC / 8);
+      const __nv_bfloat16* src = a.W + (int64_t)(n0 + r) * K + kc * KC + c * 8;
+      tc::cp_async16(sb_u + tc::core_offset(r, c, KC), src);
+    }
+    tc::cp_async_commit();
+    tc::cp_async_wait_all();
+    tc::fence_async_smem();
+    __syncthreads();
+    if (tid == 0) {
+      tc::fence_after();
+#pragma unroll
+      for (int j = 0; j < KC / 16; j++) {
+        const uint64_t ad = tc::sdesc(sa_u + j * 256, 128, SBO);
+#pragma unroll
+        for (int h = 0; h < (NT > 256 ? NT / 256 : 1); h++) {
+          constexpr int NM = NT > 256 ? 256 : NT;
+          const uint64_t bd = tc::sdesc(sb_u + h * (NM / 8) * SBO + j * 256, 128, SBO);
+          tc::mma_bf16(tmem + h * 256, ad, bd, tc::idesc_bf16(128, NM), (kc | j) != 0);
+        }
+      }
+      tc::commit(&mbar[s]);
+    }
+  }
+  if (ok && !tc::mbar_wait(&mbar[(nk - 1) & 1], ((nk - 1) >> 1) & 1, kSpinLimit)) ok = false;
+  if (!ok) {
+    if (tid == 0) report_timeout();
+  } else {
+    tc::fence_after();
+    // ---------------------------------------------------------- epilogue
+    const int r = warp * 32 + lane;
+    const int64_t p = row0 + r;
+    const bool valid = p < a.P;
+    const uint32_t tb = tmem + ((uint32_t)(warp * 32) << 16);
+    constexpr int CW = NT < 32 ? 16 : 32;
+    float lsum = 0.f;
+    if (a.epi == EPI_RECON) {
+      // pass 1: row statistics of y against x = target
+      float sdd = 0.f, syx = 0.f, syy = 0.f, sxx = 0.f;
+      for (int c0 = 0; c0 < NT; c0 += CW) {
+        float v[32], x[32];
+        tc::tmem_ld32(tb + c0, v);
+        if (valid) {
+          load_bf16x32(reinterpret_cast<const __nv_bfloat16*>(a.target) + p * a.N + n0 + c0, x, CW);
+#pragma unroll
+          for (int i = 0; i < CW; i++) {
+            const float y = v[i] + a.bias[n0 + c0 + i];
+            const float d = y - x[i];
+            sdd = fmaf(d, d, sdd);
+            syx = fmaf(y, x[i], syx);
+            syy = fmaf(y, y, syy);
+            sxx = fmaf(x[i], x[i], sxx);
+          }
+        }
+      }
+      const float ny = sqrtf(syy), nx = sqrtf(sxx);
+      const float inv = 1.f / fmaxf(ny * nx, 1e-30f);
+      const float cosv = syx * inv;
+      if (valid) lsum = a.scale * (sdd / (float)a.N + 1.f - cosv);
+      const float iy2 = 1.f / fmaxf(syy, 1e-30f);
+      // pass 2: dL/dy = s (2 (y - x)/N - (x/(|y||x|) - cos y/|y|^2))
+      for (int c0 = 0; c0 < NT; c0 += CW) {
+        float v[32], x[32];
+        tc::tmem_ld32(tb + c0, v);
+        if (valid) {
+          load_bf16x32(reinterpret_cast<const __nv_bfloat16*>(a.target) + p * a.N + n0 + c0, x, CW);
+#pragma unroll
+          for (int i = 0; i < CW; i++) {
+            const float y = v[i] + a.bias[n0 + c0 + i];
+            v[i] = a.scale * (2.f * (y - x[i]) / (float)a.N - (x[i] * inv - cosv * y * iy2));
+          }
+          store_bf16x32(a.out_bf + p * a.N + n0 + c0, v, CW);
+        }
+      }
+    } else {
+      for (int c0 = 0; c0 < NT; c0 += CW) {
+        float v[32];
+        if (CW == 32) tc::tmem_ld32(tb + c0, v);
+        else tc::tmem_ld16(tb + c0, v);
+        if (!valid) continue;
+        const int n = n0 + c0;
+        const int64_t o = p * a.N + n;
+        switch (a.epi) {
+          case EPI_GELU: {
+#pragma unroll
+            for (int i = 0; i < CW; i++) v[i] += a.bias[n + i];
+            if (a.pre_out) store_bf16x32(a.pre_out + o, v, CW);
+#pragma unroll
+            for (int i = 0; i < CW; i++) v[i] = gelu_f(v[i]);
+            store_bf16x32(a.out_bf + o, v, CW);
+            break;
+          }
+          case EPI_LIN_F32:
+          case EPI_LIN_BF16: {
+#pragma unroll
+            for (int i = 0; i < CW; i++) v[i] += a.bias[n + i];
+            if (a.epi == EPI_LIN_BF16) {
+              store_bf16x32(a.out_bf + o, v, CW);
+            } else {
+#pragma unroll
+              for (int q = 0; q < CW / 4; q++)
+                reinterpret_cast<float4*>(a.out_f32 + o)[q] =
+                    make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+            }
+            break;
+          }
+          case EPI_DGELU: {
+            float pr[32];
+            load_bf16x32(a.pre_in + o, pr, CW);
+#pragma unroll
+            for (int i = 0; i < CW; i++) v[i] *= gelu_grad_f(pr[i]);
+            store_bf16x32(a.out_bf + o, v, CW);
+            break;
+          }
+          case EPI_DX_F32: {
+#pragma unroll
+            for (int q = 0; q < CW / 4; q++)
+              reinterpret_cast<float4*>(a.out_f32 + o)[q] =
+                  make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+            break;
+          }
+          case EPI_DX_BF16:
+            store_bf16x32(a.out_bf + o, v, CW);
+            break;
+          case EPI_L1_BF16T:
+          case EPI_L1_F32T: {
+            float t[32];
+            if (a.epi == EPI_L1_BF16T) {
+              load_bf16x32(reinterpret_cast<const __nv_bfloat16*>(a.target) + o, t, CW);
+            } else {
+#pragma unroll
+              for (int i = 0; i < CW; i++) t[i] = reinterpret_cast<const float*>(a.target)[o + i];
+            }
+#pragma unroll
+            for (int i = 0; i < CW; i++) {
+              const float d = v[i] + a.bias[n + i] - t[i];
+              lsum += fabsf(d);
+              v[i] = d > 0.f ? a.scale : (d < 0.f ? -a.scale : 0.f);
+            }
+            store_bf16x32(a.out_bf + o, v, CW);
+            break;
+          }
+          default:
+            break;
+        }
+      }
+      if (a.epi == EPI_L1_BF16T || a.epi == EPI_L1_F32T) lsum *= a.scale;
+    }
+    if (a.loss) {
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) lsum += __shfl_xor_sync(0xffffffffu, lsum, o);
+      if (lane == 0 && lsum != 0.f) atomicAdd(a.loss, lsum);
+    }
+  }
+  tc::fence_before();
+  __syncthreads();
+  if (warp == 0) tc::tmem_dealloc(tmem, L::TCOLS);
+}
+
+// ------------------------------------------------------------------ dW
+
+struct DwArgs {
+  const __nv_bfloat16* G;  // [P][N]
+  const __nv_bfloat16* X;  // [P][K]
+  int64_t P;
+  int N, K;
+  int chunks_per_cta;      // 64-pixel chunks per CTA
+  float* dW;               // [N][K], accumulated
+};
+
+// Transposes the 8x8 bf16 block held as 8 rows of 16 bytes.
+__device__ __forceinline__ void transpose8x8(const uint4* in, uint4* out) {
+  const uint32_t* w = reinterpret_cast<const uint32_t*>(in);
+#pragma unroll
+  for (int i = 0; i < 8; i++) {
+    uint32_t* o = reinterpret_cast<uint32_t*>(&out[i]);
+    const uint32_t sel = (i & 1) ? 0x7632u : 0x5410u;
+#pragma unroll
+    for (int q = 0; q < 4; q++) o[q] = __byte_perm(w[(2 * q) * 4 + (i >> 1)], w[(2 * q + 1) * 4 + (i >> 1)], sel);
+  }
+}
+
+// Stages the transposed block: rows = features f0..f0+7 of src (row stride
+// ld), columns = pixels p0..p0+7; zero outside [0, P) x [0, F).
+__device__ __forceinline__ void stage_block(const __nv_bfloat16* src, int64_t ld, int64_t p0,
+                                            int64_t P, int f0, int F, uint8_t* dst_tile,
+                                            int g, int c) {
+  uint4 in[8], out[8];
+#pragma unroll
+  for (int j = 0; j < 8; j++) {
+    const int64_t p = p0 + j;
+    in[j] = (p < P && f0 < F) ? *reinterpret_cast<const uint4*>(src + p * ld + f0)
+                              : make_uint4(0, 0, 0, 0);
+  }
+  transpose8x8(in, out);
+#pragma unroll
+  for (int i = 0; i < 8; i++)
+    *reinterpret_cast<uint4*>(dst_tile + tc::core_offset(8 * g + i, c, 64)) = out[i];
+}
+
+template <int KT>
+struct DwSmem {
+  static constexpr int A_BYTES = 128 * 64 * 2;
+  static constexpr int B_BYTES = KT * 64 * 2;
+  static constexpr int STAGE = A_BYTES + B_BYTES;
+  static constexpr size_t total = 2 * STAGE + 64;
+  static constexpr uint32_t TCOLS = KT < 32 ? 32 : KT;
+};
+
+template <int KT>
+__global__ void __launch_bounds__(128, 1) dw_kernel(DwArgs a) {
+  using L = DwSmem<KT>;
+  extern __shared__ __align__(1024) uint8_t sm[];
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(sm + 2 * L::STAGE);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + 2 * L::STAGE + 16);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int n0 = blockIdx.x * 128, k0 = blockIdx.y * KT;
+  const int64_t pbeg = (int64_t)blockIdx.z * a.chunks_per_cta * 64;
+  const int64_t pend = min(a.P, pbeg + (int64_t)a.chunks_per_cta * 64);
+  const int nchunks = pend > pbeg ? (int)((pend - pbeg + 63) / 64) : 0;
+  if (warp == 0) tc::tmem_alloc(tslot, L::TCOLS);
+  if (tid == 0) {
+    tc::mbar_init(&mbar[0], 1);
+    tc::mbar_init(&mbar[1], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  tc::fence_before();
+  __syncthreads();
+  tc::fence_after();
+  const uint32_t tmem = *tslot;
+  bool ok = true;
+  for (int ch = 0; ch < nchunks && ok; ch++) {
+    const int s = ch & 1;
+    if (ch >= 2 && !tc::mbar_wait(&mbar[s], ((ch - 2) >> 1) & 1, kSpinLimit)) {
+      ok = false;
+      break;
+    }
+    uint8_t* sa = sm + s * L::STAGE;
+    uint8_t* sb = sa + L::A_BYTES;
+    const int64_t p0 = pbeg + (int64_t)ch * 64;
+    {  // A = G^T: 16 feature groups x 8 pixel groups, one block per thread
+      const int g = tid >> 3, c = tid & 7;
+      stage_block(a.G, a.N, p0 + 8 * c, pend, n0 + 8 * g, a.N, sa, g, c);
+    }
+    for (int b = tid; b < (KT / 8) * 8; b += 128) {  // B = X^T
+      const int g = b >> 3, c = b & 7;
+      stage_block(a.X, a.K, p0 + 8 * c, pend, k0 + 8 * g, a.K, sb, g, c);
+    }
+    tc::fence_async_smem();
+    __syncthreads();
+    if (tid == 0) {
+      tc::fence_after();
+      const uint32_t sa_u = tc::smem_addr(sa), sb_u = tc::smem_addr(sb);
+#pragma unroll
+      for (int j = 0; j < 4; j++)
+        tc::mma_bf16(tmem, tc::sdesc(sa_u + j * 256, 128, 1024), tc::sdesc(sb_u + j * 256, 128, 1024),
+                     tc::idesc_bf16(128, KT), (ch | j) != 0);
+      tc::commit(&mbar[s]);
+    }
+  }
+  if (ok && nchunks > 0 &&
+      !tc::mbar_wait(&mbar[(nchunks - 1) & 1], ((nchunks - 1) >> 1) & 1, kSpinLimit))
+    ok = false;
+  if (!ok) {
+    if (tid == 0) report_timeout();
+  } else if (nchunks > 0) {
+    tc::fence_after();
+    const int n = n0 + warp * 32 + lane;
+    const uint32_t tb = tmem + ((uint32_t)(warp * 32) << 16);
+    constexpr int CW = KT < 32 ? 16 : 32;
+    for (int c0 = 0; c0 < KT; c0 += CW) {
+      float v[32];
+      if (CW == 32) tc::tmem_ld32(tb + c0, v);
+      else tc::tmem_ld16(tb + c0, v);
+      if (n < a.N) {
+        float4* dst = reinterpret_cast<float4*>(a.dW + (int64_t)n * a.K + k0 + c0);
+#pragma unroll
+        for (int q = 0; q < CW / 4; q++)
+          atomicAdd(dst + q, make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]));
+      }
+    }
+  }
+  tc::fence_before();
+  __syncthreads();
+  if (warp == 0) tc::tmem_dealloc(tmem, L::TCOLS);
+}
+
+// db[n] += sum_p G[p][n]
+__global__ void colsum_kernel(const __nv_bfloat16* __restrict__ G, int64_t P, int N,
+                              int rows_per_block, float* __restrict__ db) {
+  const int64_t p0 = (int64_t)blockIdx.x * rows_per_block;
+  const int64_t p1 = min(P, p0 + rows_per_block);
+  for (int n = threadIdx.x; n < N; n += blockDim.x) {
+    float s = 0.f;
+    for (int64_t p = p0; p < p1; p++) s += __bfloat162float(G[p * N + n]);
+    atomicAdd(db + n, s);
+  }
+}
+
+__global__ void adam_kernel(float* __restrict__ w, float* __restrict__ m, float* __restrict__ v,
+                            const float* __restrict__ g, int64_t n, float lr, float bc1, float bc2) {
+  const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const float gi = g[i];
+    const float mi = b1 * m[i] + (1.f - b1) * gi;
+    const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    w[i] -= lr * (mi / bc1) / (sqrtf(vi / bc2) + eps);
+  }
+}
+
+// W [N][K] fp32 -> Wb [N][K] and Wt [K][N] bf16
+__global__ void pack_kernel(const float* __restrict__ W, int N, int K, __nv_bfloat16* __restrict__ Wb,
+                            __nv_bfloat16* __restrict__ Wt) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < (int64_t)N * K;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int n = (int)(i / K), k = (int)(i % K);
+    const __nv_bfloat16 b = __float2bfloat16_rn(W[i]);
+    Wb[i] = b;
+    Wt[(int64_t)k * N + n] = b;
+  }
+}
+
+// ------------------------------------------------------------------ host side
+
+template <int NT, int KC>
+static lgs_status launch_layer_t(const LayerArgs& a, cudaStream_t s) {
+  using L = LayerSmem<NT, KC>;
+  LGS_CHECK_CUDA(set_smem_limit(reinterpret_cast<const void*>(layer_kernel<NT, KC>), (int)L::total));
+  dim3 grid((unsigned)((a.P + 127) / 128), a.N / NT);
+  layer_kernel<NT, KC><<<grid, 128, L::total, s>>>(a);
+  LGS_CHECK_LAUNCH();
+  return LGS_OK;
+}
+
+static lgs_status launch_layer(const LayerArgs& a, cudaStream_t s) {
+  if (a.P == 0) return LGS_OK;
+  const bool k16 = a.K == 16;
+  switch (a.N) {
+    case 16: return k16 ? launch_layer_t<16, 16>(a, s) : launch_layer_t<16, 64>(a, s);
+    case 64: return k16 ? launch_layer_t<64, 16>(a, s) : launch_layer_t<64, 64>(a, s);
+    case 128: return k16 ? launch_layer_t<128, 16>(a, s) : launch_layer_t<128, 64>(a, s);
+    case 256: return k16 ? launch_layer_t<256, 16>(a, s) : launch_layer_t<256, 64>(a, s);
+    case 512: return k16 ? launch_layer_t<512, 16>(a, s) : launch_layer_t<512, 64>(a, s);
+    default: set_error("unsupported layer width"); return LGS_ERR_INVALID;
+  }
+}
+
+template <int KT>
+static lgs_status launch_dw_t(const DwArgs& a0, cudaStream_t s) {
+  using L = DwSmem<KT>;
+  LGS_CHECK_CUDA(set_smem_limit(reinterpret_cast<const void*>(dw_kernel<KT>), (int)L::total));
+  DwArgs a = a0;
+  const int ntile = (a.N + 127) / 128, ktile = a.K / KT;
+  const int64_t chunks = (a.P + 63) / 64;
+  int64_t splits = std::max<int64_t>(1, (2 * 152) / (ntile * ktile));
+  splits = std::min<int64_t>(splits, chunks);
+  a.chunks_per_cta = (int)((chunks + splits - 1) / splits);
+  splits = (chunks + a.chunks_per_cta - 1) / a.chunks_per_cta;
+  dw_kernel<KT><<<dim3(ntile, ktile, (unsigned)splits), 128, L::total, s>>>(a);
+  LGS_CHECK_LAUNCH();
+  return LGS_OK;
+}
+
+// dW += G^T X and db += colsum(G) for one layer.
+static lgs_status launch_dw(const __nv_bfloat16* G, const __nv_bfloat16* X, int64_t P, int N,
+                            int K, float* dW, float* db, cudaStream_t s) {
+  if (P == 0) return LGS_OK;
+  DwArgs a{G, X, P, N, K, 0, dW};
+  lgs_status st;
+  if (K == 16) st = launch_dw_t<16>(a, s);
+  else if (K == 64) st = launch_dw_t<64>(a, s);
+  else if (K == 128) st = launch_dw_t<128>(a, s);
+  else st = launch_dw_t<256>(a, s);  // K = 256 or 512 (two column tiles)
+  if (st != LGS_OK) return st;
+  const int rows = 512;
+  colsum_kernel<<<(unsigned)((P + rows - 1) / rows), 256, 0, s>>>(G, P, N, rows, db);
+  LGS_CHECK_LAUNCH();
+  return LGS_OK;
+}
+
+static LayerArgs layer(const void* A, bool a_f32, const uint16_t* W, const float* b, int64_t P,
+                       int K, int N, int epi) {
+  LayerArgs a = {};
+  a.A = A;
+  a.a_f32 = a_f32 ? 1 : 0;
+  a.W = reinterpret_cast<const __nv_bfloat16*>(W);
+  a.bias = b;
+  a.P = P;
+  a.K = K;
+  a.N = N;
+  a.epi = epi;
+  return a;
+}
+
+// Workspace carving (bf16 activation buffers, 256-byte aligned).
+struct Carver {
+  char* base;
+  size_t off = 0;
+  explicit Carver(void* b) : base((char*)b) {}
+  __nv_bfloat16* bf(int64_t P, int w) {
+    __nv_bfloat16* p = base ? reinterpret_cast<__nv_bfloat16*>(base + off) : nullptr;
+    off += ((size_t)P * w * 2 + 255) & ~(size_t)255;
+    return p;
+  }
+};
+
+static void carve_encode(Carver& c, int64_t P, __nv_bfloat16** h) {
+  h[0] = c.bf(P, 256);
+  h[1] = c.bf(P, 128);
+  h[2] = c.bf(P, 64);
+}
+
+struct DecodeBufs {
+  __nv_bfloat16 *a[3], *pre[3], *dy, *d[3];
+};
+static void carve_decode(Carver& c, int64_t P, DecodeBufs& B) {
+  const int w[3] = {64, 128, 256};
+  for (int i = 0; i < 3; i++) {
+    B.a[i] = c.bf(P, w[i]);
+    B.pre[i] = c.bf(P, w[i]);
+    B.d[i] = c.bf(P, w[i]);
+  }
+  B.dy = c.bf(P, 512);
+}
+
+struct TrainBufs {
+  __nv_bfloat16* act[8];   // output of layer l (post-activation; z for l = 3)
+  __nv_bfloat16* pre[8];   // pre-activation of hidden layers
+  __nv_bfloat16* grad[8];  // gradient w.r.t. the output of layer l (after GELU')
+};
+static void carve_train(Carver& c, int64_t P, TrainBufs& B) {
+  for (int l = 0; l < kAeLayers; l++) {
+    const int w = kAeWidths[l + 1];
+    B.act[l] = c.bf(P, w);
+    B.pre[l] = c.bf(P, w);
+    B.grad[l] = c.bf(P, w);
+  }
+}
+
+static lgs_status check_weights(const lgs_ae_weights* w, int first, int last) {
+  LGS_CHECK_ARG(w != nullptr, "weights are null");
+  for (int l = first; l <= last; l++) {
+    LGS_CHECK_ARG(w->W[l] && w->Wt[l] && w->b[l], "null weight pointer");
+    LGS_CHECK_ARG(aligned(w->W[l], 16) && aligned(w->Wt[l], 16), "weights must be 16-byte aligned");
+  }
+  return LGS_OK;
+}
+
+}  // namespace lgs
+
+using namespace lgs;
+
+extern "C" size_t ae_workspace_bytes(int64_t P, int what) {
+  if (P < 0) return 0;
+  Carver c(nullptr);
+  if (what == LGS_AE_ENCODE) {
+    __nv_bfloat16* h[3];
+    carve_encode(c, P, h);
+  } else if (what == LGS_AE_DECODE) {
+    DecodeBufs B;
+    carve_decode(c, P, B);
+  } else if (what == LGS_AE_TRAIN) {
+    TrainBufs B;
+    carve_train(c, P, B);
+  } else {
+    return 0;
+  }
+  return c.off + 256;
+}
+
+extern "C" lgs_status ae_encode(const lgs_ae_weights* w, const uint16_t* x, int64_t P, float* z,
+                                void* workspace, size_t workspace_bytes, void* stream) {
+  clear_error();
+  LGS_CHECK_ARG(P >= 0, "P < 0");
+  lgs_status st = check_weights(w, 0, 3);
+  if (st != LGS_OK) return st;
+  if (P == 0) return LGS_OK;
+  LGS_CHECK_ARG(x && z && workspace, "null pointer");
+  LGS_CHECK_ARG(aligned(x, 16) && aligned(z, 16) && aligned(workspace, 256), "misaligned pointer");
+  LGS_CHECK_ARG(workspace_bytes >= ae_workspace_bytes(P, LGS_AE_ENCODE), "workspace too small");
+  cudaStream_t s = as_stream(stream);
+  Carver c(workspace);
+  __nv_bfloat16* h[3];
+  carve_encode(c, P, h);
+  LayerArgs a;
+  a = layer(x, false, w->W[0], w->b[0], P, 512, 256, EPI_GELU); a.out_bf = h[0];
+  if ((st = launch_layer(a, s)) != LGS_OK) return st;
+  a = layer(h[0], false, w->W[1], w->b[1], P, 256, 128, EPI_GELU); a.out_bf = h[1];
+  if ((st = launch_layer(a, s)) != LGS_OK) return st;
+  a = layer(h[1], false, w->W[2], w->b[2], P, 128, 64, EPI_GELU); a.out_bf = h[2];
+  if ((st = launch_layer(a, s)) != LGS_OK) return st;
+  a = layer(h[2], false, w->W[3], w->b[3], P, 64, 16, EPI_LIN_F32); a.out_f32 = z;
+  return launch_layer(a, s);
+}
+
+extern "C" lgs_status ae_decode(const lgs_ae_weights* w, const float* z, int64_t P,
+                                const uint16_t* target, float weight, float* loss_dev, float* dz,
+                                float* y_opt, void* workspace, size_t workspace_bytes,
+                                void* stream) {
+  clear_error();
+  LGS_CHECK_ARG(P >= 0, "P < 0");
+  lgs_status st = check_weights(w, 4, 7);
+  if (st != LGS_OK) return st;
+  if (P == 0) return LGS_OK;
+  LGS_CHECK_ARG(z && workspace, "null pointer");
+  LGS_CHECK_ARG(target || y_opt, "nothing to compute: give a target or y_opt");
+  LGS_CHECK_ARG(!target || (loss_dev && dz), "a target needs loss_dev and dz");
+  LGS_CHECK_ARG(aligned(z, 16) && aligned(workspace, 256) && aligned(target, 16) &&
+                    aligned(dz, 16) && aligned(y_opt, 16),
+                "misaligned pointer");
+  LGS_CHECK_ARG(workspace_bytes >= ae_workspace_bytes(P, LGS_AE_DECODE), "workspace too small");
+  cudaStream_t s = as_stream(stream);
+  Carver c(workspace);
+  DecodeBufs B;
+  carve_decode(c, P, B);
+  LayerArgs a;
+  a = layer(z, true, w->W[4], w->b[4], P, 16, 64, EPI_GELU); a.out_bf = B.a[0]; a.pre_out = B.pre[0];
+  if ((st = launch_layer(a, s)) != LGS_OK) return st;
+  a = layer(B.a[0], false, w->W[5], w->b[5], P, 64, 128, EPI_GELU); a.out_bf = B.a[1]; a.pre_out = B.pre[1];
+  if ((st = launch_layer(a, s)) != LGS_OK) return st;
+  a = layer(B.a[1], false, w->W[6], w->b[6], P, 128, 256, EPI_GELU); a.out_bf = B.a[2]; a.pre_out = B.pre[2];
+  if ((st = launch_layer(a, s)) != LGS_OK) return st;
+  if (y_opt) {
+    a = layer(B.a[2], false, w->W[7], w->b[7], P, 256, 512, EPI_LIN_F32); a.out_f32 = y_opt;
+    if ((st = launch_layer(a, s)) != LGS_OK) return st;
+  }
+  if (!target) return LGS_OK;
+  // Eq. 2: L1 against F_gt fused into the last layer, then back to F_render
+  a = layer(B.a[2], false, w->W[7], w->b[7], P, 256, 512, EPI_L1_BF16T);
+  a.out_bf = B.dy; a.target = target; a.scale = weight / ((float)P * 512.f); a.loss = loss_dev;
+  if ((st = launch_layer(a, s)) != LGS_OK) return st;
+  a = layer(B.dy, false, w->Wt[7], nullptr, P, 512, 256, EPI_DGELU); a.out_bf = B.d[2]; a.pre_in = B.pre[2];
+  if ((st = launch_layer(a, s)) != LGS_OK) return st;
+  a = layer(B.d[2], false, w->Wt[6], nullptr, P, 256, 128, EPI_DGELU); a.out_bf = B.d[1]; a.pre_in = B.pre[1];
+  if ((st = launch_layer(a, s)) != LGS_OK) return st;
+  a = layer(B.d[1], false, w->Wt[5], nullptr, P, 128, 64, EPI_DGELU); a.out_bf = B.d[0]; a.pre_in = B.pre[0];
+  if ((st = launch_layer(a, s)) != LGS_OK) return st;
+  a = layer(B.d[0], false, w->Wt[4], nullptr, P, 64, 16, EPI_DX_F32); a.out_f32 = dz;
+  return launch_layer(a, s);
+}
+
+extern "C" lgs_status ae_pack(lgs_ae_state* st_, int first, int last, void* stream) {
+  clear_error();
+  LGS_CHECK_ARG(st_ && first >= 0 && last < kAeLayers && first <= last, "bad arguments");
+  cudaStream_t s = as_stream(stream);
+  for (int l = first; l <= last; l++) {
+    LGS_CHECK_ARG(st_->W[l] && st_->Wbf[l] && st_->Wtbf[l], "null weight pointer");
+    const int K = kAeWidths[l], N = kAeWidths[l + 1];
+    pack_kernel<<<(N * K + 255) / 256, 256, 0, s>>>(st_->W[l], N, K,
+                                                    reinterpret_cast<__nv_bfloat16*>(st_->Wbf[l]),
+                                                    reinterpret_cast<__nv_bfloat16*>(st_->Wtbf[l]));
+    LGS_CHECK_LAUNCH();
+  }
+  return LGS_OK;
+}
+
+extern "C" lgs_status ae_train_step(lgs_ae_state* st_, const uint16_t* x, const float* target,
+                                    int64_t P, int mode, float lr, float* loss_dev,
+                                    void* workspace, size_t workspace_bytes, void* stream) {
+  clear_error();
+  LGS_CHECK_ARG(st_ != nullptr, "state is null");
+  LGS_CHECK_ARG(mode == LGS_AE_RECON || mode == LGS_AE_ENC_ADAPT, "bad mode");
+  LGS_CHECK_ARG(P > 0, "P must be positive");
+  LGS_CHECK_ARG(x && loss_dev && workspace, "null pointer");
+  LGS_CHECK_ARG(mode == LGS_AE_RECON || target, "ENC_ADAPT needs the rendered target");
+  LGS_CHECK_ARG(aligned(x, 16) && aligned(workspace, 256) && aligned(target, 16),
+                "misaligned pointer");
+  LGS_CHECK_ARG(workspace_bytes >= ae_workspace_bytes(P, LGS_AE_TRAIN), "workspace too small");
+  const int last = mode == LGS_AE_RECON ? 7 : 3;
+  for (int l = 0; l <= last; l++)
+    LGS_CHECK_ARG(st_->W[l] && st_->b[l] && st_->mW[l] && st_->vW[l] && st_->mb[l] && st_->vb[l] &&
+                      st_->gW[l] && st_->gb[l] && st_->Wbf[l] && st_->Wtbf[l],
+                  "null state pointer");
+  cudaStream_t s = as_stream(stream);
+  Carver c(workspace);
+  TrainBufs B;
+  carve_train(c, P, B);
+  auto W = [&](int l) { return st_->Wbf[l]; };
+  auto Wt = [&](int l) { return st_->Wtbf[l]; };
+  lgs_status st;
+  for (int l = 0; l <= last; l++) {
+    const int K = kAeWidths[l], N = kAeWidths[l + 1];
+    LGS_CHECK_CUDA(cudaMemsetAsync(st_->gW[l], 0, sizeof(float) * N * K, s));
+    LGS_CHECK_CUDA(cudaMemsetAsync(st_->gb[l], 0, sizeof(float) * N, s));
+  }
+  // forward, keeping every layer's input and pre-activation
+  const void* in = x;
+  for (int l = 0; l <= 3; l++) {
+    const int K = kAeWidths[l], N = kAeWidths[l + 1];
+    LayerArgs a;
+    if (l < 3) {
+      a = layer(in, false, W(l), st_->b[l], P, K, N, EPI_GELU);
+      a.out_bf = B.act[l];
+      a.pre_out = B.pre[l];
+    } else if (mode == LGS_AE_RECON) {
+      a = layer(in, false, W(l), st_->b[l], P, K, N, EPI_LIN_BF16);
+      a.out_bf = B.act[l];
+    } else {
+      // Eq. 3: L1(E(F_gt), F_render), gradient w.r.t. z straight out of the epilogue
+      a = layer(in, false, W(l), st_->b[l], P, K, N, EPI_L1_F32T);
+      a.out_bf = B.grad[3];
+      a.target = target;
+      a.scale = 1.f / ((float)P * 16.f);
+      a.loss = loss_dev;
+    }
+    if ((st = launch_layer(a, s)) != LGS_OK) return st;
+    in = B.act[l];
+  }
+  if (mode == LGS_AE_RECON) {
+    for (int l = 4; l <= 7; l++) {
+      const int K = kAeWidths[l], N = kAeWidths[l + 1];
+      LayerArgs a;
+      if (l < 7) {
+        a = layer(B.act[l - 1], false, W(l), st_->b[l], P, K, N, EPI_GELU);
+        a.out_bf = B.act[l];
+        a.pre_out = B.pre[l];
+      } else {
+        a = layer(B.act[6], false, W(7), st_->b[7], P, K, N, EPI_RECON);
+        a.out_bf = B.grad[7];
+        a.target = x;
+        a.scale = 1.f / (float)P;
+        a.loss = loss_dev;
+      }
+      if ((st = launch_layer(a, s)) != LGS_OK) return st;
+    }
+  }
+  // backward: dW_l = grad_l^T input_l, grad_{l-1} = (grad_l W_l) * gelu'(pre_{l-1})
+  for (int l = last; l >= 0; l--) {
+    const int K = kAeWidths[l], N = kAeWidths[l + 1];
+    const __nv_bfloat16* input = l == 0 ? reinterpret_cast<const __nv_bfloat16*>(x) : B.act[l - 1];
+    if ((st = launch_dw(B.grad[l], input, P, N, K, st_->gW[l], st_->gb[l], s)) != LGS_OK) return st;
+    if (l == 0) break;
+    LayerArgs a;
+    if (l == 4) {  // below the linear latent: no GELU
+      a = layer(B.grad[l], false, Wt(l), nullptr, P, N, K, EPI_DX_BF16);
+    } else {
+      a = layer(B.grad[l], false, Wt(l), nullptr, P, N, K, EPI_DGELU);
+      a.pre_in = B.pre[l - 1];
+    }
+    a.out_bf = B.grad[l - 1];
+    if ((st = launch_layer(a, s)) != LGS_OK) return st;
+  }
+  // Adam on FP32 master weights, then refresh the BF16 copies
+  st_->step += 1;
+  const float bc1 = 1.f - powf(0.9f, (float)st_->step);
+  const float bc2 = 1.f - powf(0.999f, (float)st_->step);
+  for (int l = 0; l <= last; l++) {
+    const int K = kAeWidths[l], N = kAeWidths[l + 1];
+    adam_kernel<<<(N * K + 255) / 256, 256, 0, s>>>(st_->W[l], st_->mW[l], st_->vW[l], st_->gW[l],
+                                                   (int64_t)N * K, lr, bc1, bc2);
+    adam_kernel<<<(N + 255) / 256, 256, 0, s>>>(st_->b[l], st_->mb[l], st_->vb[l], st_->gb[l], N,
+                                               lr, bc1, bc2);
+    LGS_CHECK_LAUNCH();
+  }
+  return ae_pack(st_, 0, last, stream);
+}
+
+extern "C" lgs_status lgs_device_error(int* code) {
+  clear_error();
+  LGS_CHECK_ARG(code != nullptr, "code is null");
+  unsigned v = 0, zero = 0;
+  LGS_CHECK_CUDA(cudaMemcpyFromSymbol(&v, g_ae_error, sizeof(v)));
+  LGS_CHECK_CUDA(cudaMemcpyToSymbol(g_ae_error, &zero, sizeof(zero)));
+  *code = (int)v;
+  return LGS_OK;
+}

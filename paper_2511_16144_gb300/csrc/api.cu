@@ -1,4 +1,8 @@
 // Error plumbing, version and the L1 loss term of Eq. 1 / Eq. 2.
+#include <mutex>
+#include <unordered_map>
+#include <vector>
+
 #include "common.cuh"
 
 namespace lgs {
@@ -7,6 +11,17 @@ static thread_local std::string g_last_error;
 
 void set_error(const std::string& msg) { g_last_error = msg; }
 void clear_error() { g_last_error.clear(); }
+
+cudaError_t set_smem_limit(const void* func, int bytes) {
+  static std::mutex mu;
+  static std::unordered_map<const void*, int> done;
+  std::lock_guard<std::mutex> lock(mu);
+  auto it = done.find(func);
+  if (it != done.end() && it->second >= bytes) return cudaSuccess;
+  cudaError_t e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e == cudaSuccess) done[func] = bytes;
+  return e;
+}
 
 // loss += weight * mean|pred - target|, grad = weight * sign(pred - target) / count.
 template <typename TT>
@@ -38,6 +53,31 @@ using namespace lgs;
 extern "C" const char* lgs_version(void) { return "lgs 0.1 (sm_103a)"; }
 
 extern "C" const char* lgs_last_error(void) { return g_last_error.c_str(); }
+
+extern "C" int64_t lgs_graph_kernel_nodes(void* graph) {
+  clear_error();
+  if (!graph) return -1;
+  cudaGraph_t g = reinterpret_cast<cudaGraph_t>(graph);
+  size_t n = 0;
+  if (cudaGraphGetNodes(g, nullptr, &n) != cudaSuccess) return -1;
+  std::vector<cudaGraphNode_t> nodes(n);
+  if (n && cudaGraphGetNodes(g, nodes.data(), &n) != cudaSuccess) return -1;
+  int64_t k = 0;
+  for (size_t i = 0; i < n; i++) {
+    cudaGraphNodeType t;
+    if (cudaGraphNodeGetType(nodes[i], &t) != cudaSuccess) return -1;
+    if (t == cudaGraphNodeTypeKernel) k++;
+  }
+  return k;
+}
+
+extern "C" lgs_status lgs_zero(void* dev, size_t bytes, void* stream) {
+  clear_error();
+  if (bytes == 0) return LGS_OK;
+  LGS_CHECK_ARG(dev != nullptr, "null pointer");
+  LGS_CHECK_CUDA(cudaMemsetAsync(dev, 0, bytes, as_stream(stream)));
+  return LGS_OK;
+}
 
 extern "C" lgs_status lgs_l1_loss(const float* pred, const void* target, int target_dtype,
                                   int64_t count, float weight, float* grad, float* loss_dev,

@@ -34,6 +34,9 @@ void clear_error();
 
 #define LGS_CHECK_LAUNCH() LGS_CHECK_CUDA(cudaGetLastError())
 
+// Raises a kernel's dynamic shared-memory limit once per process.
+cudaError_t set_smem_limit(const void* func, int bytes);
+
 inline bool aligned(const void* p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
 inline cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
 

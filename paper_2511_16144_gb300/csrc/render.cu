@@ -439,7 +439,7 @@ __global__ void __launch_bounds__(kThreads) render_bwd_kernel(RasterArgs A, int 
 
 template <typename K>
 static cudaError_t prepare(K kernel, size_t smem) {
-  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  return set_smem_limit(reinterpret_cast<const void*>(kernel), (int)smem);
 }
 
 template <int FC, typename TC>

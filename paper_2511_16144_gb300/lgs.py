@@ -28,6 +28,23 @@ class LgsError(RuntimeError):
     """A liblgs call returned a non-zero lgs_status."""
 
 
+AE_LAYERS = 8
+AE_WIDTHS = (512, 256, 128, 64, 16, 64, 128, 256, 512)
+AE_ENCODE, AE_DECODE, AE_TRAIN = 0, 1, 2
+AE_RECON, AE_ENC_ADAPT = 0, 1
+
+
+class AeWeights(ctypes.Structure):
+    _fields_ = [("W", ctypes.c_void_p * AE_LAYERS), ("Wt", ctypes.c_void_p * AE_LAYERS),
+                ("b", ctypes.c_void_p * AE_LAYERS)]
+
+
+class AeState(ctypes.Structure):
+    _fields_ = [(name, ctypes.c_void_p * AE_LAYERS)
+                for name in ("W", "b", "mW", "vW", "mb", "vb", "gW", "gb", "Wbf", "Wtbf")] + \
+               [("step", ctypes.c_int64)]
+
+
 class LgsCamera(ctypes.Structure):
     _fields_ = [("fx", ctypes.c_float), ("fy", ctypes.c_float), ("cx", ctypes.c_float),
                 ("cy", ctypes.c_float), ("width", ctypes.c_int32), ("height", ctypes.c_int32),
@@ -54,6 +71,14 @@ def load():
         "gs_render_bwd": ([P, P, P, P, P, P, P, I64, P, I32, P, P, I32, I32, P, P, P, P, P, P, P,
                            P, P, P, P, P, P, P], I32),
         "lgs_l1_loss": ([P, P, I32, I64, F, P, P, P], I32),
+        "ae_workspace_bytes": ([I64, I32], SZ),
+        "ae_encode": ([P, P, I64, P, P, SZ, P], I32),
+        "ae_decode": ([P, P, I64, P, F, P, P, P, P, SZ, P], I32),
+        "ae_train_step": ([P, P, P, I64, I32, F, P, P, SZ, P], I32),
+        "ae_pack": ([P, I32, I32, P], I32),
+        "lgs_device_error": ([P], I32),
+        "lgs_graph_kernel_nodes": ([P], I64),
+        "lgs_zero": ([P, SZ, P], I32),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -66,7 +91,8 @@ def load():
 def exported_symbols():
     """Names of the C entry points this binding declares."""
     return ["lgs_version", "lgs_last_error", "gs_project", "gs_bin_sort_workspace", "gs_bin_sort",
-            "gs_render_fwd", "gs_render_bwd", "lgs_l1_loss"]
+            "gs_render_fwd", "gs_render_bwd", "lgs_l1_loss", "ae_workspace_bytes", "ae_encode",
+            "ae_decode", "ae_train_step", "ae_pack", "lgs_device_error", "lgs_graph_kernel_nodes", "lgs_zero"]
 
 
 def _check(status, what):
@@ -220,3 +246,58 @@ def lgs_l1_loss(pred, target, weight, grad, loss_dev):
     lib = load()
     _check(lib.lgs_l1_loss(_p(pred), _p(target), _dtype_code(target), pred.numel(), float(weight),
                            _p(grad), _p(loss_dev), _stream()), "lgs_l1_loss")
+
+
+# ---------------------------------------------------------------- autoencoder
+
+def ae_workspace_bytes(P, what):
+    return int(load().ae_workspace_bytes(int(P), int(what)))
+
+
+def _workspace(P, what, device, cache=None):
+    nbytes = ae_workspace_bytes(P, what)
+    if cache is not None and cache.numel() >= nbytes:
+        return cache, nbytes
+    return torch.empty(max(nbytes, 256), dtype=torch.uint8, device=device), nbytes
+
+
+def ae_encode(weights: AeWeights, x, z, ws=None):
+    """z [P,16] f32 = E(x), x bf16 [P,512]."""
+    P = x.shape[0]
+    ws, nb = _workspace(P, AE_ENCODE, x.device, ws)
+    _check(load().ae_encode(ctypes.byref(weights), _p(x), P, _p(z), _p(ws), nb, _stream()),
+           "ae_encode")
+    return ws
+
+
+def ae_decode(weights: AeWeights, z, target=None, weight=1.0, loss=None, dz=None, y=None, ws=None):
+    """Eq. 2 (loss += weight mean|D(z) - target|, dz = its gradient) and/or
+    y = D(z)."""
+    P = z.shape[0]
+    ws, nb = _workspace(P, AE_DECODE, z.device, ws)
+    _check(load().ae_decode(ctypes.byref(weights), _p(z), P, _p(target), float(weight), _p(loss),
+                            _p(dz), _p(y), _p(ws), nb, _stream()), "ae_decode")
+    return ws
+
+
+def ae_train_step(state: AeState, x, target, mode, lr, loss, ws=None):
+    P = x.shape[0]
+    ws, nb = _workspace(P, AE_TRAIN, x.device, ws)
+    _check(load().ae_train_step(ctypes.byref(state), _p(x), _p(target), P, int(mode), float(lr),
+                                _p(loss), _p(ws), nb, _stream()), "ae_train_step")
+    return ws
+
+
+def ae_pack(state: AeState, first=0, last=AE_LAYERS - 1):
+    _check(load().ae_pack(ctypes.byref(state), first, last, _stream()), "ae_pack")
+
+
+def lgs_zero(t):
+    """Zero-fills a device tensor with a memset on the current stream."""
+    _check(load().lgs_zero(_p(t), t.numel() * t.element_size(), _stream()), "lgs_zero")
+
+
+def lgs_device_error():
+    code = ctypes.c_int(0)
+    _check(load().lgs_device_error(ctypes.byref(code)), "lgs_device_error")
+    return code.value

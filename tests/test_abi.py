@@ -21,7 +21,8 @@ def declared_symbols():
     for h in sorted(os.listdir(os.path.join(ROOT, "include"))):
         if h.endswith(".h"):
             text = open(os.path.join(ROOT, "include", h)).read()
-            names += re.findall(r"^(?:lgs_status|size_t|const char\*)\s+(\w+)\s*\(", text, re.M)
+            names += re.findall(r"^(?:lgs_status|size_t|int64_t|const char\*)\s+(\w+)\s*\(",
+                                text, re.M)
     return names
 
 

@@ -1,0 +1,130 @@
+"""GPU parity of the tensor-core autoencoder (encode, Eq. 2 distillation with
+its gradient, and the Adam training step) against the FP64 oracle run on
+BF16-rounded weights and inputs (marked gpu)."""
+import numpy as np
+import pytest
+import torch
+
+from paper_2511_16144_gb300 import synth
+from tests.gpu_util import bf16_round
+
+pytestmark = pytest.mark.gpu
+
+REL = 1e-2  # norm-relative: BF16 activations between layers, FP32 accumulation
+
+
+@pytest.fixture(scope="module")
+def lgs():
+    assert torch.cuda.is_available(), "the gpu tests need a CUDA device"
+    from paper_2511_16144_gb300 import build, lgs as L
+    build.build()
+    L.load()
+    return L
+
+
+def rounded(layers):
+    """What the GPU multiplies with: BF16 weights, FP32 biases (as float64)."""
+    return [[bf16_round(W).astype(np.float64), np.asarray(b, np.float64)] for W, b in layers]
+
+
+def rel_err(a, b):
+    a, b = np.asarray(a, np.float64), np.asarray(b, np.float64)
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30)
+
+
+def embeddings(w, h, seed):
+    rng = np.random.default_rng(seed)
+    return synth.embedding_map(rng, synth.embedding_centroids(), w, h).reshape(-1, 512)
+
+
+def test_encode_matches_oracle(lgs):
+    from oracle import ae
+    from paper_2511_16144_gb300.ae import AutoEncoder
+    enc, dec = synth.ae_init()
+    model = AutoEncoder(enc, dec)
+    x = embeddings(97, 61, 0)  # 5917 rows: a ragged last tile
+    z = model.encode(torch.from_numpy(x).cuda().bfloat16()).cpu().numpy()
+    zr = ae.encode(rounded(enc), bf16_round(x))
+    assert rel_err(z, zr) < REL
+    # per pixel as well, not just in aggregate
+    per = np.linalg.norm(z - zr, axis=1) / np.linalg.norm(zr, axis=1)
+    assert np.percentile(per, 99) < 3 * REL
+
+
+def test_decode_and_distillation_match_oracle(lgs):
+    from oracle import ae
+    from paper_2511_16144_gb300.ae import AutoEncoder
+    enc, dec = synth.ae_init(seed=3005)
+    model = AutoEncoder(enc, dec)
+    rng = np.random.default_rng(1)
+    P = 3000 + 45
+    z = rng.standard_normal((P, 16)).astype(np.float32)
+    t = embeddings(45, 68, 2)[:P]
+    zt = torch.from_numpy(z).cuda()
+    y = model.decode(zt).cpu().numpy()
+    zr = bf16_round(z)  # the GPU feeds z to the first GEMM as BF16
+    yr = ae.decode(rounded(dec), zr)
+    assert rel_err(y, yr) < REL
+    loss, dz = model.distill(zt, torch.from_numpy(t).cuda().bfloat16(), weight=0.7)
+    lr_, dzr = ae.distill(rounded(dec), zr, bf16_round(t))
+    assert abs(loss.item() - 0.7 * lr_) <= 1e-3 * 0.7 * lr_
+    assert rel_err(dz.cpu().numpy(), 0.7 * dzr) < 2 * REL
+
+
+@pytest.mark.parametrize("mode", ["recon", "enc_adapt"])
+def test_train_step_gradients_and_update(lgs, mode):
+    from oracle import ae
+    from paper_2511_16144_gb300.ae import AutoEncoder
+    enc, dec = synth.ae_init(seed=3006)
+    model = AutoEncoder(enc, dec)
+    P = 4096 + 77
+    x = embeddings(64, 66, 4)[:P]
+    rng = np.random.default_rng(5)
+    target = rng.standard_normal((P, 16)).astype(np.float32) if mode == "enc_adapt" else None
+    W0 = [w.clone() for w in model.W]
+    loss = model.train_step(torch.from_numpy(x).cuda().bfloat16(),
+                            None if target is None else torch.from_numpy(target).cuda(),
+                            mode=lgs.AE_RECON if mode == "recon" else lgs.AE_ENC_ADAPT, lr=1e-3)
+    torch.cuda.synchronize()
+    re, rd = rounded(enc), rounded(dec)
+    state = ae.new_state(re, rd)
+    l_ref, g_ref = ae.train_step(re, rd, state, bf16_round(x), target, mode, lr=0.0)
+    assert abs(loss.item() - l_ref) <= 1e-2 * abs(l_ref)
+    n_layers = 8 if mode == "recon" else 4
+    for l in range(8):
+        gW, gb = model.gW[l].cpu().numpy(), model.gb[l].cpu().numpy()
+        if l >= n_layers:
+            assert g_ref[l] is None
+            torch.testing.assert_close(model.W[l], W0[l], rtol=0, atol=0)
+            continue
+        assert rel_err(gW, g_ref[l][0]) < 3 * REL, (l, rel_err(gW, g_ref[l][0]))
+        assert rel_err(gb, g_ref[l][1]) < 3 * REL, (l, rel_err(gb, g_ref[l][1]))
+        # first Adam step: W1 = W0 - lr g / (|g| + eps), from the GPU's own gradient
+        g = model.gW[l]
+        exp = W0[l] - 1e-3 * g / (g.abs() + 1e-8)
+        torch.testing.assert_close(model.W[l], exp, rtol=1e-5, atol=1e-7)
+    # the BF16 copies follow the masters
+    for l in range(n_layers):
+        torch.testing.assert_close(model.Wbf[l], model.W[l].bfloat16(), rtol=0, atol=0)
+        torch.testing.assert_close(model.Wtbf[l], model.W[l].t().contiguous().bfloat16(),
+                                   rtol=0, atol=0)
+    assert lgs.lgs_device_error() == 0
+
+
+def test_training_reduces_reconstruction_loss(lgs):
+    """200 Adam steps on 64k-pixel batches of per-frame embedding maps."""
+    from paper_2511_16144_gb300.ae import AutoEncoder
+    enc, dec = synth.ae_init()
+    model = AutoEncoder(enc, dec)
+    rng = np.random.default_rng(7)
+    cent = synth.embedding_centroids()
+    frames = [synth.embedding_map(rng, cent, 320, 240).reshape(-1, 512) for _ in range(4)]
+    data = torch.from_numpy(np.concatenate(frames)).cuda().bfloat16()
+    gen = torch.Generator(device="cuda").manual_seed(0)
+    losses = []
+    for step in range(200):
+        idx = torch.randint(0, data.shape[0], (65536,), device="cuda", generator=gen)
+        losses.append(model.train_step(data[idx].contiguous(), lr=1e-3).item())
+    assert np.isfinite(losses).all()
+    assert np.mean(losses[-10:]) < 0.25 * np.mean(losses[:5]), (losses[:5], losses[-10:])
+    assert lgs.lgs_device_error() == 0

@@ -32,7 +32,7 @@ namespace lgs {
 
 constexpr int kAeLayers = LGS_AE_LAYERS;
 constexpr int kAeWidths[9] = {512, 256, 128, 64, 16, 64, 128, 256, 512};
-constexpr uint32_t kSpinLimit = 1u << 26;
+constexpr uint32_t kSpinLimit = 1u << 22;  // polls before a wait gives up
 
 __device__ unsigned g_ae_error;  // set when a bounded wait gives up
 
@@ -136,9 +136,11 @@ __global__ void __launch_bounds__(128, 1) layer_kernel(LayerArgs a) {
 
   const int nk = K / KC;
   constexpr uint32_t SBO = KC * 16;
-  for (int kc = 0; kc < nk && ok; kc++) {
+  for (int kc = 0; kc < nk; kc++) {
     const int s = kc & 1;
-    if (kc >= 2 && !tc::mbar_wait(&mbar[s], ((kc - 2) >> 1) & 1, kSpinLimit)) {
+    // every thread polls; the block agrees before anyone moves on
+    const bool freed = kc < 2 || tc::mbar_wait(&mbar[s], ((kc - 2) >> 1) & 1, kSpinLimit);
+    if (!__syncthreads_and(freed)) {
       ok = false;
       break;
     }
@@ -197,7 +199,7 @@ __global__ void __launch_bounds__(128, 1) layer_kernel(LayerArgs a) {
       tc::commit(&mbar[s]);
     }
   }
-  if (ok && !tc::mbar_wait(&mbar[(nk - 1) & 1], ((nk - 1) >> 1) & 1, kSpinLimit)) ok = false;
+  if (ok) ok = __syncthreads_and(tc::mbar_wait(&mbar[(nk - 1) & 1], ((nk - 1) >> 1) & 1, kSpinLimit));
   if (!ok) {
     if (tid == 0) report_timeout();
   } else {
@@ -404,9 +406,10 @@ __global__ void __launch_bounds__(128, 1) dw_kernel(DwArgs a) {
   tc::fence_after();
   const uint32_t tmem = *tslot;
   bool ok = true;
-  for (int ch = 0; ch < nchunks && ok; ch++) {
+  for (int ch = 0; ch < nchunks; ch++) {
     const int s = ch & 1;
-    if (ch >= 2 && !tc::mbar_wait(&mbar[s], ((ch - 2) >> 1) & 1, kSpinLimit)) {
+    const bool freed = ch < 2 || tc::mbar_wait(&mbar[s], ((ch - 2) >> 1) & 1, kSpinLimit);
+    if (!__syncthreads_and(freed)) {
       ok = false;
       break;
     }
@@ -433,9 +436,9 @@ __global__ void __launch_bounds__(128, 1) dw_kernel(DwArgs a) {
       tc::commit(&mbar[s]);
     }
   }
-  if (ok && nchunks > 0 &&
-      !tc::mbar_wait(&mbar[(nchunks - 1) & 1], ((nchunks - 1) >> 1) & 1, kSpinLimit))
-    ok = false;
+  if (ok && nchunks > 0)
+    ok = __syncthreads_and(tc::mbar_wait(&mbar[(nchunks - 1) & 1], ((nchunks - 1) >> 1) & 1,
+                                         kSpinLimit));
   if (!ok) {
     if (tid == 0) report_timeout();
   } else if (nchunks > 0) {

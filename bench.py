@@ -43,6 +43,8 @@ def parse():
     ap.add_argument("--no-plain", action="store_true", help="skip the plain 512-d path")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle cpu_baseline")
     ap.add_argument("--ae-steps", type=int, default=200)
+    ap.add_argument("--profile", action="store_true",
+                    help="run warmup + steps eager mapping steps and exit (for ncu)")
     return ap.parse_args()
 
 
@@ -184,8 +186,7 @@ def run_gpu(args, rank, world):
         with torch.cuda.graph(g):
             step.run()
         torch.cuda.synchronize()
-        nodes = int(lgs.load().lgs_graph_kernel_nodes(ctypes_ptr(g.raw_cuda_graph()))) \
-            if hasattr(g, "raw_cuda_graph") else -1
+        nodes = kernel_nodes(step.run)
         for _ in range(warm):
             flush.fill_(1.0)
             g.replay()
@@ -209,8 +210,13 @@ def run_gpu(args, rank, world):
         times = [a.elapsed_time(b) for a, b in ev]
         return times, g, nodes
 
-    results = {}
     step16 = MappingStep(s16_bf, cams, rgb_t, dep_t, f_gt, model=model)
+    if args.profile:
+        for _ in range(args.warmup + args.steps):
+            step16.run()
+        torch.cuda.synchronize()
+        print(f"profile: {args.warmup + args.steps} eager steps, K = {int(step16.k_dev.item())}")
+        return
     clocks = Clocks(torch.cuda.current_device())
     t16, g16, nodes16 = timed(step16, args.steps, args.warmup, clocks)
     k_inst = int(step16.k_dev.item())
@@ -297,9 +303,23 @@ class _Null:
         return False
 
 
-def ctypes_ptr(h):
+def kernel_nodes(fn):
+    """Kernel nodes in a CUDA graph captured from fn (every one is a liblgs
+    kernel: the step's fills are memset nodes), or -1 if unavailable."""
     import ctypes
-    return ctypes.c_void_p(int(h))
+
+    import torch
+    from paper_2511_16144_gb300 import lgs
+    try:
+        g = torch.cuda.CUDAGraph(keep_graph=True)
+        with torch.cuda.graph(g):
+            fn()
+        torch.cuda.synchronize()
+        n = int(lgs.load().lgs_graph_kernel_nodes(ctypes.c_void_p(int(g.raw_cuda_graph()))))
+        del g
+        return n
+    except (TypeError, RuntimeError, AttributeError):
+        return -1
 
 
 def per_call_times(step, flush, reps=5):

@@ -125,18 +125,27 @@ def test_bin_sort_invalid_arguments(lgs):
 
 # ---------------------------------------------------------------- forward
 
+def _check_maps(out, o, keep, atol=1e-5):
+    """Strict parity on pixels whose decisions are robust; on the few pixels
+    where an FP32 skip / clamp / stop decision may flip, the difference must
+    stay within what one flipped decision can cause (a blend weight of at
+    most 2/255 of a unit-range channel, or one stop-level blend)."""
+    frac = 1.0 - keep.mean()
+    assert frac < 1e-2, f"{frac:.2e} of pixels within the decision margin"
+    dscale = max(1.0, np.abs(o["depth"]).max())
+    fscale = max(1.0, np.abs(o["feat"]).max()) if o["feat"].size else 1.0
+    for k, scale in (("rgb", 1.0), ("feat", 1.0), ("T_final", 1.0), ("depth", dscale)):
+        d = np.abs(out[k] - o[k])
+        assert d[keep].max() <= atol * scale, (k, d[keep].max())
+        if (~keep).any():
+            bound = 2.0 / 255.0 * (dscale if k == "depth" else fscale if k == "feat" else 1.0)
+            assert d[~keep].max() <= bound, (k, "flagged", d[~keep].max())
+    np.testing.assert_array_equal(out["n_contrib"][keep], o["n_contrib"][keep])
+
+
 def _compare_forward(fr, o, keep, cam_index=0, atol=1e-5):
     out = {k: _np(v[cam_index]) for k, v in fr.out.items() if v is not None}
-    frac = 1.0 - keep.mean()
-    assert frac < 1e-3, f"{frac:.2e} of pixels within the decision margin"
-    for k in ("rgb", "feat", "T_final"):
-        d = np.abs(out[k] - o[k])[keep]
-        assert d.max() <= atol, (k, d.max())
-    # depth is an unnormalised sum of w * z (z up to a few metres): same
-    # absolute bound relative to the depth scale
-    d = np.abs(out["depth"] - o["depth"])[keep]
-    assert d.max() <= atol * max(1.0, np.abs(o["depth"]).max()), d.max()
-    np.testing.assert_array_equal(out["n_contrib"][keep], o["n_contrib"][keep])
+    _check_maps(out, o, keep, atol)
     return out
 
 
@@ -191,12 +200,7 @@ def test_render_fwd_indoor_full_size_crop(lgs, oracle_lib):
         x0, y0, w, h = crop
         keep = robust_mask(o)
         out = {k: _np(v[0])[y0:y0 + h, x0:x0 + w] for k, v in fr.out.items() if v is not None}
-        frac = 1 - keep.mean()
-        assert frac < 1e-3, frac
-        for k in ("rgb", "feat", "T_final"):
-            assert np.abs(out[k] - o[k])[keep].max() <= 1e-5, k
-        assert np.abs(out["depth"] - o["depth"])[keep].max() <= 1e-5 * max(1, o["depth"].max())
-        np.testing.assert_array_equal(out["n_contrib"][keep], o["n_contrib"][keep])
+        _check_maps(out, o, keep)
         assert o["n_contrib"].mean() > 5
 
 

@@ -198,6 +198,38 @@ lgs_status gs_render_bwd(const float* means, const float* quats, const float* lo
                          float* d_feats, void* stream);
 
 /* ------------------------------------------------------------------------
+ * gs_render_bwd_static -- gs_render_bwd without the caller-owned grad2d
+ * scratch, for callers that cannot allocate device memory: for example a
+ * mapping thread with a hard real-time budget that must never take the
+ * device-wide synchronisation a cudaMalloc / cudaFree implies, or a host
+ * application that forbids libraries and plug-ins from owning device
+ * memory.  The paper has no counterpart; this is a deployment variant.
+ *
+ * Same arguments, meaning and results as gs_render_bwd except grad2d.  The
+ * scratch is a fixed array inside the library's device image, 524,288
+ * (camera, Gaussian) records (16 MiB, see gs_render_bwd_static_capacity),
+ * held by every GPU that loads the library until the process exits.
+ * n_cams * n above that limit returns LGS_ERR_INVALID before anything is
+ * enqueued.  Nothing is allocated by the caller or the library.
+ * The first call on a device looks the array's device address up (with that
+ * device current) and caches it: make that first call before any stream
+ * capture.  All calls share the array, zero the part they use and leave
+ * their contents in it; calls that overlap on the GPU (unordered streams)
+ * race on it, so order them on one stream.
+ * ---------------------------------------------------------------------- */
+int64_t gs_render_bwd_static_capacity(void);
+lgs_status gs_render_bwd_static(const float* means, const float* quats, const float* log_scales,
+                                const float* opacity_logits, const float* proj,
+                                const uint32_t* ids, const uint32_t* ranges, int64_t n,
+                                const lgs_camera* cams_host, int n_cams, const void* colors,
+                                const void* feats, int feat_dim, int chan_dtype,
+                                const float* bg_host, const float* T_final, const uint32_t* last,
+                                const float* d_rgb, const float* d_depth, const float* d_feat,
+                                float* d_means, float* d_quats, float* d_log_scales,
+                                float* d_opacity_logits, float* d_colors, float* d_feats,
+                                void* stream);
+
+/* ------------------------------------------------------------------------
  * lgs_l1_loss -- one L1 term of Eq. 1 / Eq. 2: loss_dev += weight *
  * mean|pred - target| and grad = weight * sign(pred - target) / count
  * (overwritten; sign(0) = 0).  pred, grad: float32 [count]; target float32

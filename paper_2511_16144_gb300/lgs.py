@@ -79,6 +79,9 @@ def load():
         "lgs_device_error": ([P], I32),
         "lgs_graph_kernel_nodes": ([P], I64),
         "lgs_zero": ([P, SZ, P], I32),
+        "gs_render_bwd_static_capacity": ([], I64),
+        "gs_render_bwd_static": ([P, P, P, P, P, P, P, I64, P, I32, P, P, I32, I32, P, P, P, P,
+                                  P, P, P, P, P, P, P, P, P], I32),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -92,7 +95,8 @@ def exported_symbols():
     """Names of the C entry points this binding declares."""
     return ["lgs_version", "lgs_last_error", "gs_project", "gs_bin_sort_workspace", "gs_bin_sort",
             "gs_render_fwd", "gs_render_bwd", "lgs_l1_loss", "ae_workspace_bytes", "ae_encode",
-            "ae_decode", "ae_train_step", "ae_pack", "lgs_device_error", "lgs_graph_kernel_nodes", "lgs_zero"]
+            "ae_decode", "ae_train_step", "ae_pack", "lgs_device_error", "lgs_graph_kernel_nodes", "lgs_zero",
+            "gs_render_bwd_static_capacity", "gs_render_bwd_static"]
 
 
 def _check(status, what):
@@ -239,6 +243,26 @@ def gs_render_bwd(params, proj, bufs: BinBuffers, cams, colors, feats, fwd, d_rg
                              _p(grads["quats"]), _p(grads["log_scales"]),
                              _p(grads["opacity_logits"]), _p(grads["colors"]), _p(grads["feats"]),
                              _stream()), "gs_render_bwd")
+
+
+def gs_render_bwd_static(params, proj, bufs: BinBuffers, cams, colors, feats, fwd, d_rgb, d_depth,
+                         d_feat, grads, bg=(0.0, 0.0, 0.0)):
+    """gs_render_bwd with the library's fixed scratch instead of a
+    caller-owned grad2d buffer (for callers that cannot allocate)."""
+    lib = load()
+    means, quats, log_scales, logits = params
+    c = len(cams)
+    d = int(feats.shape[1])
+    bga = (ctypes.c_float * 3)(*[float(x) for x in bg])
+    ca = cameras(cams)
+    _check(lib.gs_render_bwd_static(_p(means), _p(quats), _p(log_scales), _p(logits), _p(proj),
+                                    _p(bufs.ids), _p(bufs.ranges), bufs.n, ca, c, _p(colors),
+                                    _p(feats), d, _dtype_code(feats), bga, _p(fwd["T_final"]),
+                                    _p(fwd["last"]), _p(d_rgb), _p(d_depth), _p(d_feat),
+                                    _p(grads["means"]), _p(grads["quats"]),
+                                    _p(grads["log_scales"]), _p(grads["opacity_logits"]),
+                                    _p(grads["colors"]), _p(grads["feats"]), _stream()),
+           "gs_render_bwd_static")
 
 
 def lgs_l1_loss(pred, target, weight, grad, loss_dev):

@@ -50,21 +50,16 @@ def parse():
 
 # --------------------------------------------------------------------------- workload
 
-def build_workload(rank, ae_steps):
-    """Host arrays of the workload: geometry, 512-d Gaussian embeddings,
-    targets and the embedding frames the autoencoder trains on."""
+def build_workload(rank):
+    """Host arrays of the workload: the indoor scene with spatially coherent
+    512-d semantics (64 3D Voronoi cells of the room), its 8 arc keyframes,
+    the keyframe this rank renders, and RGB / depth targets."""
     from paper_2511_16144_gb300 import synth
     scene, cams = synth.indoor(n_cams=8)
+    g512 = synth.semantic_features(scene.means, synth.ROOM_LO, synth.ROOM_HI, seed=1005)
     cam = cams[rank % 8]
-    rng = np.random.default_rng(1003 + rank)
-    cent = synth.embedding_centroids()
-    k = rng.integers(0, cent.shape[0], size=scene.n)
-    g512 = synth.unit_rows(cent[k] + 0.02 * rng.standard_normal((scene.n, 512)).astype(np.float32))
     (rgb_t, dep_t, _), = synth.targets([cam], feat_dim=16, seed=2001 + rank)
-    f_gt = synth.embedding_map(rng, cent, cam.width, cam.height)
-    train_frames = [synth.embedding_map(rng, cent, 320, 240).reshape(-1, 512) for _ in range(4)]
-    return dict(scene=scene, cam=cam, g512=g512.astype(np.float32), rgb_t=rgb_t, dep_t=dep_t,
-                f_gt=f_gt, train=np.concatenate(train_frames))
+    return dict(scene=scene, cams=cams, cam=cam, g512=g512, rgb_t=rgb_t, dep_t=dep_t)
 
 
 class Clocks:
@@ -139,15 +134,28 @@ def run_gpu(args, rank, world):
     build.build()
     lgs.load()
     dev = torch.device("cuda", torch.cuda.current_device())
-    W = build_workload(rank, args.ae_steps)
+    W = build_workload(rank)
     scene, cam = W["scene"], W["cam"]
+    from paper_2511_16144_gb300.render import Frame
 
-    # scene-adaptive autoencoder: pretrained online as an autoencoder on the
-    # frames' own embeddings (Sec. IV-A.2), then the encoder prior gives the
-    # Gaussians' 16-d features (Sec. III-B.2)
+    geom = DeviceScene.from_host(scene, device=dev)
+    colors_bf = geom.colors.bfloat16()
+    g512_bf = torch.from_numpy(W["g512"]).to(dev).bfloat16()
+    g512_f32 = torch.from_numpy(W["g512"]).to(dev)
+    s512 = DeviceScene(geom.means, geom.quats, geom.log_scales, geom.opacity_logits,
+                       colors_bf, g512_bf)
+    s512_f32 = DeviceScene(geom.means, geom.quats, geom.log_scales, geom.opacity_logits,
+                           geom.colors, g512_f32)
+    # the extractor's per-frame 512-d maps: the semantic field rendered by the
+    # plain path for every keyframe of the window (BF16), F_gt = this rank's
+    frames = [Frame(s512, [c]).out["feat"][0].reshape(-1, 512).bfloat16() for c in W["cams"]]
+    f_gt = frames[rank % 8].contiguous()
+
+    # scene-adaptive autoencoder pretrained online on those maps (Sec. IV-A.2);
+    # the encoder prior gives the Gaussians' 16-d features (Sec. III-B.2)
     enc, dec = synth.ae_init(seed=3001)
     model = AutoEncoder(enc, dec, device=dev)
-    train = torch.from_numpy(W["train"]).to(dev).bfloat16()
+    train = torch.cat(frames)
     gen = torch.Generator(device=dev).manual_seed(rank)
     ae_losses = []
     t0 = time.time()
@@ -156,20 +164,17 @@ def run_gpu(args, rank, world):
         ae_losses.append(model.train_step(train[idx].contiguous(), lr=1e-3))
     torch.cuda.synchronize()
     ae_train_s = time.time() - t0
-    ae_losses = [float(l.item()) for l in ae_losses]
-    g512_bf = torch.from_numpy(W["g512"]).to(dev).bfloat16()
+    ae_losses = [float(l.item()) for l in ae_losses] or [float("nan")]
+    del train, frames
     f16 = model.encode(g512_bf)
-
-    geom = DeviceScene.from_host(scene, device=dev)
-    colors_bf = geom.colors.bfloat16()
     s16_bf = DeviceScene(geom.means, geom.quats, geom.log_scales, geom.opacity_logits,
                          colors_bf, f16.bfloat16().contiguous())
     s16_f32 = DeviceScene(geom.means, geom.quats, geom.log_scales, geom.opacity_logits,
                           geom.colors, f16.contiguous())
     rgb_t = torch.from_numpy(W["rgb_t"][None]).to(dev).contiguous()
     dep_t = torch.from_numpy(W["dep_t"][None]).to(dev).contiguous()
-    f_gt = torch.from_numpy(W["f_gt"].reshape(-1, 512)).to(dev).bfloat16().contiguous()
     cams = [cam]
+    W["f_gt"] = f_gt.float().cpu().numpy().reshape(cam.height, cam.width, 512)
 
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
 
@@ -243,25 +248,24 @@ def run_gpu(args, rank, world):
     plain = None
     cos_err = None
     if not args.no_plain:
-        s512 = DeviceScene(geom.means, geom.quats, geom.log_scales, geom.opacity_logits,
-                           colors_bf, g512_bf)
         step512 = MappingStep(s512, cams, rgb_t, dep_t, f_gt, model=None,
                               capacity=step16.bufs.capacity)
         tp, _, _ = timed(step512, max(5, args.steps // 2), 2)
         plain = {"value": pixels / 1e6 / (np.mean(tp) / 1e3), "ms_per_step": float(np.mean(tp)),
                  "channels": "bf16", "feat_dim": 512}
-        # decoded 16-d features against the plain 512-channel render, per pixel
-        step512.run()
-        step16.run()
-        torch.cuda.synchronize()
-        y = model.decode(step16.out["feat"].reshape(-1, 16).contiguous())
-        ref = step512.out["feat"].reshape(-1, 512)
-        nr = ref.norm(dim=1)
-        keep = nr > 1e-6
-        cos = (y * ref).sum(1)[keep] / (y.norm(dim=1)[keep] * nr[keep]).clamp_min(1e-30)
-        cos_err = {"mean": float((1 - cos).mean().item()), "excluded_pixels": int((~keep).sum().item())}
         plain["speedup_of_16d"] = value / world / plain["value"]
         del step512
+    # decoded 16-d features against the plain 512-channel FP32 render, per pixel
+    step16.run()
+    torch.cuda.synchronize()
+    y = model.decode(step16.out["feat"].reshape(-1, 16).contiguous())
+    ref = Frame(s512_f32, cams).out["feat"][0].reshape(-1, 512)
+    nr = ref.norm(dim=1)
+    keep = nr > 1e-6
+    cos = (y * ref).sum(1)[keep] / (y.norm(dim=1)[keep] * nr[keep]).clamp_min(1e-30)
+    cos_err = {"mean": float((1 - cos).mean().item()), "excluded_pixels": int((~keep).sum().item()),
+               "reference": "plain 512-channel FP32 render of the same Gaussians"}
+    del y, ref
 
     # end to end through the C ABI with host buffers: per step the keyframe's
     # targets (RGB, depth, F_gt) go host -> device from pinned memory and the
@@ -461,8 +465,9 @@ def run_reference(args, rank, world):
         return
     import oracle
     oracle.build()
-    W = build_workload(0, 0)
+    W = build_workload(0)
     prep = oracle_prepare(W)
+    W["f_gt"] = reference_f_gt(W, 160)
     t0 = time.time()
     oracle_step(W, 8, prep)
     t_small = max(time.time() - t0, 1e-3)
@@ -488,6 +493,18 @@ def run_reference(args, rank, world):
             "e2e": {"value": value, "unit": "Mpix/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def reference_f_gt(W, side):
+    """F_gt of the centre crop for the oracle arm: the semantic field rendered
+    by the oracle itself (512 channels), in a full-frame array."""
+    import oracle
+    cam = W["cam"]
+    x0, y0 = cam.width // 2 - side // 2, cam.height // 2 - side // 2
+    o = oracle.render(W["scene"].with_feats(W["g512"]), cam, crop=(x0, y0, side, side))
+    full = np.zeros((cam.height, cam.width, 512), np.float32)
+    full[y0:y0 + side, x0:x0 + side] = o["feat"]
+    return full
 
 
 def main():

@@ -224,6 +224,27 @@ def embedding_scene(n: int = 100_000, seed: int = 1003, dim: int = 512):
     return scene.with_feats(g.astype(np.float32)), cams
 
 
+def semantic_features(means, lo, hi, n_cells=64, dim=512, noise=0.02, seed=1005):
+    """Spatially coherent 512-d semantics: ``n_cells`` Voronoi seeds uniform in
+    the box [lo, hi], each cell owning one unit centroid; a Gaussian takes its
+    nearest seed's centroid plus N(0, noise^2), renormalised (the 3D analogue
+    of the per-frame Voronoi embedding maps).  [N, dim] float32."""
+    rng = np.random.default_rng(seed)
+    lo, hi = np.asarray(lo, np.float64), np.asarray(hi, np.float64)
+    seeds = lo + (hi - lo) * rng.random((n_cells, 3))
+    cent = unit_rows(rng.standard_normal((n_cells, dim)))
+    m = np.asarray(means, np.float64)
+    best = np.zeros(m.shape[0], np.int64)
+    bestd = np.full(m.shape[0], np.inf)
+    for k in range(n_cells):
+        d = ((m - seeds[k]) ** 2).sum(-1)
+        upd = d < bestd
+        best[upd] = k
+        bestd[upd] = d[upd]
+    g = cent[best] + noise * rng.standard_normal((m.shape[0], dim))
+    return unit_rows(g).astype(np.float32)
+
+
 def ae_init(widths_enc=(512, 256, 128, 64, 16), widths_dec=(16, 64, 128, 256, 512),
             seed: int = 3003):
     """Initial autoencoder weights, each layer (W [out, in], b [out]) ~

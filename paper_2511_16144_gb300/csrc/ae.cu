@@ -7,7 +7,7 @@
 // the frozen decoder with an L1 loss; Sec. III-B.4 Eq. 3 adapts the encoder
 // alone with an L1 loss against the rendered map.
 //
-// Widths 512-256-128-64-16 and the mirrored decoder, GELU on hidden layers,
+// Widths 512-256-128-64-16 and the mirrored decoder, GELU (tanh form) on hidden layers,
 // bias everywhere (layers 0-3 encoder, 4-7 decoder).  GEMMs take BF16
 // operands and accumulate in FP32 in tensor memory; activations between
 // layers are BF16.
@@ -65,13 +65,8 @@ struct LayerArgs {
   float* loss;
 };
 
-__device__ __forceinline__ float gelu_f(float x) {
-  return 0.5f * x * (1.f + erff(x * 0.70710678118654752f));
-}
-__device__ __forceinline__ float gelu_grad_f(float x) {
-  return 0.5f * (1.f + erff(x * 0.70710678118654752f)) +
-         x * 0.39894228040143268f * expf(-0.5f * x * x);
-}
+__device__ __forceinline__ float gelu_f(float x) { return gelu_tanh(x); }
+__device__ __forceinline__ float gelu_grad_f(float x) { return gelu_tanh_grad(x); }
 
 __device__ __forceinline__ void store_bf16x32(__nv_bfloat16* dst, const float* v, int n) {
   // n = 16 or 32 values to a 16-byte aligned destination
@@ -592,16 +587,13 @@ static void carve_encode(Carver& c, int64_t P, __nv_bfloat16** h) {
 }
 
 struct DecodeBufs {
-  __nv_bfloat16 *a[3], *pre[3], *dy, *d[3];
+  __nv_bfloat16* a[3];
+  void* pack;
 };
 static void carve_decode(Carver& c, int64_t P, DecodeBufs& B) {
   const int w[3] = {64, 128, 256};
-  for (int i = 0; i < 3; i++) {
-    B.a[i] = c.bf(P, w[i]);
-    B.pre[i] = c.bf(P, w[i]);
-    B.d[i] = c.bf(P, w[i]);
-  }
-  B.dy = c.bf(P, 512);
+  for (int i = 0; i < 3; i++) B.a[i] = c.bf(P, w[i]);
+  B.pack = c.bf(1, (int)(decode_pack_bytes() / 2));
 }
 
 struct TrainBufs {
@@ -695,29 +687,20 @@ extern "C" lgs_status ae_decode(const lgs_ae_weights* w, const float* z, int64_t
   DecodeBufs B;
   carve_decode(c, P, B);
   LayerArgs a;
-  a = layer(z, true, w->W[4], w->b[4], P, 16, 64, EPI_GELU); a.out_bf = B.a[0]; a.pre_out = B.pre[0];
-  if ((st = launch_layer(a, s)) != LGS_OK) return st;
-  a = layer(B.a[0], false, w->W[5], w->b[5], P, 64, 128, EPI_GELU); a.out_bf = B.a[1]; a.pre_out = B.pre[1];
-  if ((st = launch_layer(a, s)) != LGS_OK) return st;
-  a = layer(B.a[1], false, w->W[6], w->b[6], P, 128, 256, EPI_GELU); a.out_bf = B.a[2]; a.pre_out = B.pre[2];
-  if ((st = launch_layer(a, s)) != LGS_OK) return st;
-  if (y_opt) {
+  if (y_opt) {  // inference: layer by layer, activations through the workspace
+    a = layer(z, true, w->W[4], w->b[4], P, 16, 64, EPI_GELU); a.out_bf = B.a[0];
+    if ((st = launch_layer(a, s)) != LGS_OK) return st;
+    a = layer(B.a[0], false, w->W[5], w->b[5], P, 64, 128, EPI_GELU); a.out_bf = B.a[1];
+    if ((st = launch_layer(a, s)) != LGS_OK) return st;
+    a = layer(B.a[1], false, w->W[6], w->b[6], P, 128, 256, EPI_GELU); a.out_bf = B.a[2];
+    if ((st = launch_layer(a, s)) != LGS_OK) return st;
     a = layer(B.a[2], false, w->W[7], w->b[7], P, 256, 512, EPI_LIN_F32); a.out_f32 = y_opt;
     if ((st = launch_layer(a, s)) != LGS_OK) return st;
   }
   if (!target) return LGS_OK;
-  // Eq. 2: L1 against F_gt fused into the last layer, then back to F_render
-  a = layer(B.a[2], false, w->W[7], w->b[7], P, 256, 512, EPI_L1_BF16T);
-  a.out_bf = B.dy; a.target = target; a.scale = weight / ((float)P * 512.f); a.loss = loss_dev;
-  if ((st = launch_layer(a, s)) != LGS_OK) return st;
-  a = layer(B.dy, false, w->Wt[7], nullptr, P, 512, 256, EPI_DGELU); a.out_bf = B.d[2]; a.pre_in = B.pre[2];
-  if ((st = launch_layer(a, s)) != LGS_OK) return st;
-  a = layer(B.d[2], false, w->Wt[6], nullptr, P, 256, 128, EPI_DGELU); a.out_bf = B.d[1]; a.pre_in = B.pre[1];
-  if ((st = launch_layer(a, s)) != LGS_OK) return st;
-  a = layer(B.d[1], false, w->Wt[5], nullptr, P, 128, 64, EPI_DGELU); a.out_bf = B.d[0]; a.pre_in = B.pre[0];
-  if ((st = launch_layer(a, s)) != LGS_OK) return st;
-  a = layer(B.d[0], false, w->Wt[4], nullptr, P, 64, 16, EPI_DX_F32); a.out_f32 = dz;
-  return launch_layer(a, s);
+  // Eq. 2: decoder forward, L1 against F_gt and the gradient back to
+  // F_render in one persistent kernel (nothing but dz leaves the chip)
+  return launch_decode_fused(w, z, P, target, weight, loss_dev, dz, B.pack, s);
 }
 
 extern "C" lgs_status ae_pack(lgs_ae_state* st_, int first, int last, void* stream) {
@@ -842,6 +825,6 @@ extern "C" lgs_status lgs_device_error(int* code) {
   unsigned v = 0, zero = 0;
   LGS_CHECK_CUDA(cudaMemcpyFromSymbol(&v, g_ae_error, sizeof(v)));
   LGS_CHECK_CUDA(cudaMemcpyToSymbol(g_ae_error, &zero, sizeof(zero)));
-  *code = (int)v;
+  *code = (int)(v | (fused_error_word() << 4));
   return LGS_OK;
 }

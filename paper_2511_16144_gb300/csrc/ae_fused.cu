@@ -1,0 +1,514 @@
+// Fused feature distillation through the frozen decoder (LEGO-SLAM
+// Sec. III-B.3, Eq. 2): y = D_theta(F_render), loss += w mean|y - F_gt| and
+// dF_render = dL/dF_render, for 128-pixel tiles that never leave the chip.
+//
+// D_theta is 16 -> 64 -> 128 -> 256 -> 512 with GELU (tanh form) after the first three
+// layers.  Per tile the CTA runs, on the tensor cores (BF16 operands, FP32
+// accumulators in tensor memory):
+//   F1..F3  forward hidden layers, activations kept in shared memory (BF16);
+//   F4/B1   the 512-wide output in four 128-column chunks: each chunk's
+//           epilogue forms dy = w sign(y - F_gt) / (P 512) and immediately
+//           feeds dh3 += dy_chunk W7_chunk, so y and dy never reach memory;
+//   R3..R1  the pre-activations are recomputed instead of stored (this keeps
+//           the working set in 212 KB of shared memory);
+//   B2..B4  dh2 = (dh3 * gelu'(pre3)) W6, dh1 = (dh2 * gelu'(pre2)) W5,
+//           dz = (dh1 * gelu'(pre1)) W4.
+// Warps 0-15 are the epilogue (TMEM -> registers -> shared memory; warps w,
+// w + 4, w + 8, w + 12 share TMEM lane quadrant w % 4 and split the columns in
+// quarters), warp 16 streams
+// the weights as 51 pre-packed units (<= 16 KB each, already in the
+// tensor-core's canonical layout) through a 4-stage ring with bulk TMA
+// copies, warp 17 issues the MMAs.  Every wait is bounded.
+#include <mutex>
+#include <vector>
+
+#include "common.cuh"
+#include "kernels.cuh"
+#include "tc05.cuh"
+
+namespace lgs {
+
+namespace {
+
+constexpr int kUnits = 51;
+constexpr int kStages = 4;
+constexpr uint32_t kStageBytes = 16384;
+constexpr uint32_t kLimit = 1u << 22;
+
+// shared-memory map (bytes)
+constexpr uint32_t SM_Z = 0;         // 128 x 16 bf16
+constexpr uint32_t SM_H1 = 4096;     // 128 x 64   (h1, later d1)
+constexpr uint32_t SM_H2 = 20480;    // 128 x 128  (h2, later d2)
+constexpr uint32_t SM_H3 = 53248;    // 128 x 256  (h3, later d3)
+constexpr uint32_t SM_DY = 118784;   // 128 x 128  (one dy chunk)
+constexpr uint32_t SM_ST = 151552;   // kStages x 16 KB weight ring
+constexpr uint32_t SM_BAR = SM_ST + kStages * kStageBytes;
+
+// weight matrices of the decoder: forward W (out x in) and transposed Wt
+enum Mat { W4 = 0, W5, W6, W7, T4, T5, T6, T7 };
+constexpr int kCols[8] = {16, 64, 128, 256, 64, 128, 256, 512};
+
+struct Unit {
+  int mat, row0, rows, col0, kc;
+};
+
+// The 51 weight units of one tile, in the order the MMAs consume them.
+std::vector<Unit> schedule() {
+  std::vector<Unit> U;
+  auto add = [&](int m, int r0, int rows, int c0, int kc) { U.push_back({m, r0, rows, c0, kc}); };
+  add(W4, 0, 64, 0, 16);                                                   // F1
+  add(W5, 0, 128, 0, 64);                                                  // F2
+  for (int h = 0; h < 2; h++) for (int k = 0; k < 2; k++) add(W6, 128 * h, 128, 64 * k, 64);  // F3
+  for (int k = 0; k < 4; k++) add(W7, 0, 128, 64 * k, 64);                // F4 chunk 0
+  for (int k = 0; k < 4; k++) add(W7, 128, 128, 64 * k, 64);             // F4 chunk 1
+  auto b1 = [&](int c) {
+    for (int h = 0; h < 2; h++)
+      for (int k = 0; k < 2; k++) add(T7, 128 * h, 128, 128 * c + 64 * k, 64);
+  };
+  b1(0);
+  for (int k = 0; k < 4; k++) add(W7, 256, 128, 64 * k, 64);             // F4 chunk 2
+  b1(1);
+  for (int k = 0; k < 4; k++) add(W7, 384, 128, 64 * k, 64);             // F4 chunk 3
+  b1(2);
+  b1(3);
+  for (int h = 0; h < 2; h++) for (int k = 0; k < 2; k++) add(W6, 128 * h, 128, 64 * k, 64);  // R3
+  for (int k = 0; k < 4; k++) add(T6, 0, 128, 64 * k, 64);               // B2
+  add(W5, 0, 128, 0, 64);                                                  // R2
+  for (int k = 0; k < 2; k++) add(T5, 0, 64, 64 * k, 64);                // B3
+  add(W4, 0, 64, 0, 16);                                                   // R1
+  add(T4, 0, 16, 0, 64);                                                   // B4
+  return U;
+}
+
+struct PackArgs {
+  const __nv_bfloat16* mats[8];
+  int ld[8];
+  Unit units[kUnits];
+  uint32_t off[kUnits];
+  uint32_t piece0[kUnits + 1];
+  uint8_t* pack;
+};
+
+// Writes every unit as [rows/8][kc/8][8][8] bf16 core matrices.
+__global__ void pack_units_kernel(PackArgs a) {
+  const uint32_t total = a.piece0[kUnits];
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
+    int u = 0;
+    while (a.piece0[u + 1] <= i) u++;
+    const Unit U = a.units[u];
+    const uint32_t j = i - a.piece0[u];
+    const int per_row = U.kc / 8;
+    const int r = (int)(j / per_row), c = (int)(j % per_row);
+    const __nv_bfloat16* src = a.mats[U.mat] + (int64_t)(U.row0 + r) * a.ld[U.mat] + U.col0 + 8 * c;
+    *reinterpret_cast<uint4*>(a.pack + a.off[u] + tc::core_offset(r, c, U.kc)) =
+        *reinterpret_cast<const uint4*>(src);
+  }
+}
+
+struct FusedArgs {
+  const uint8_t* pack;
+  uint32_t off[kUnits];
+  uint32_t bytes[kUnits];
+  const float* b4;
+  const float* b5;
+  const float* b6;
+  const float* b7;
+  const float* z;
+  const __nv_bfloat16* target;
+  float* dz;
+  int64_t P;
+  float scale;
+  float* loss;
+};
+
+// 16 or 32 consecutive columns of row r as BF16 into an activation tile of
+// width kw starting at column col (a multiple of 8).
+template <int NV>
+__device__ __forceinline__ void put_row(uint8_t* tile, int r, int col, int kw, const float* v) {
+#pragma unroll
+  for (int q = 0; q < NV / 8; q++) {
+    uint4 u;
+    __nv_bfloat162* h = reinterpret_cast<__nv_bfloat162*>(&u);
+#pragma unroll
+    for (int k = 0; k < 4; k++) h[k] = __floats2bfloat162_rn(v[8 * q + 2 * k], v[8 * q + 2 * k + 1]);
+    *reinterpret_cast<uint4*>(tile + tc::core_offset(r, col / 8 + q, kw)) = u;
+  }
+}
+
+__device__ unsigned g_fused_error;
+
+constexpr int kEpiWarps = 16;
+constexpr int kFusedThreads = (kEpiWarps + 2) * 32;   // + producer warp + MMA warp
+constexpr uint32_t SM_BIAS = SM_BAR + 128;             // b4 | b5 | b6 | b7 (960 floats)
+constexpr uint32_t SM_ALL = SM_BIAS + 960 * 4;
+
+__global__ void __launch_bounds__(kFusedThreads, 1)
+decode_fused_kernel(const __grid_constant__ FusedArgs a) {
+  extern __shared__ __align__(1024) uint8_t sm[];
+  uint64_t* full = reinterpret_cast<uint64_t*>(sm + SM_BAR);
+  uint64_t* empty = full + kStages;
+  uint64_t* accbar = full + 2 * kStages;
+  uint64_t* opbar = accbar + 1;
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(opbar + 1);
+  float* sb = reinterpret_cast<float*>(sm + SM_BIAS);
+  const float* sb4 = sb;
+  const float* sb5 = sb + 64;
+  const float* sb6 = sb + 192;
+  const float* sb7 = sb + 448;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int64_t ntiles = (a.P + 127) / 128;
+  for (int i = tid; i < 960; i += kFusedThreads)
+    sb[i] = i < 64 ? a.b4[i] : i < 192 ? a.b5[i - 64] : i < 448 ? a.b6[i - 192] : a.b7[i - 448];
+  if (warp == 0) tc::tmem_alloc(tslot, 512);
+  if (tid == 0) {
+    for (int s = 0; s < kStages; s++) {
+      tc::mbar_init(&full[s], 1);
+      tc::mbar_init(&empty[s], 1);
+    }
+    tc::mbar_init(accbar, 1);
+    tc::mbar_init(opbar, kEpiWarps * 32);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  tc::fence_before();
+  __syncthreads();
+  tc::fence_after();
+  const uint32_t tmem = *tslot;
+  const uint32_t sbase = tc::smem_addr(sm);
+
+  if (warp == kEpiWarps) {
+    // ---------------------------------------------------------------- producer
+    if (lane == 0) {
+      uint32_t u = 0;
+      bool ok = true;
+      for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+        for (int i = 0; i < kUnits; i++, u++) {
+          const uint32_t s = u % kStages, round = u / kStages;
+          if (round > 0 && !tc::mbar_wait(&empty[s], (round - 1) & 1, kLimit)) {
+            ok = false;
+            break;
+          }
+          tc::mbar_expect_tx(&full[s], a.bytes[i]);
+          tc::bulk_g2s(sbase + SM_ST + s * kStageBytes, a.pack + a.off[i], a.bytes[i], &full[s]);
+        }
+      }
+      if (!ok) atomicOr(&g_fused_error, 1u);
+    }
+  } else if (warp == kEpiWarps + 1) {
+    // ---------------------------------------------------------------- MMA issuer
+    if (lane == 0) {
+      uint32_t u = 0, ops = 0;
+      bool ok = true;
+      auto wait_op = [&]() {
+        ok = ok && tc::mbar_wait(opbar, ops & 1, kLimit);
+        ops++;
+        tc::fence_after();
+      };
+      // one weight unit: B = ring stage, A = activation tile at a_off (width
+      // a_kw) from column k0, D = TMEM column dcol, N = n, K = kc
+      auto unit = [&](uint32_t a_off, int a_kw, int k0, int kc, int n, uint32_t dcol, bool fresh) {
+        if (!ok) return;
+        const uint32_t s = u % kStages, round = u / kStages;
+        if (!tc::mbar_wait(&full[s], round & 1, kLimit)) {
+          ok = false;
+          return;
+        }
+        tc::fence_after();
+        const uint32_t b = sbase + SM_ST + s * kStageBytes;
+        const uint32_t idesc = tc::idesc_bf16(128, n);
+        for (int j = 0; j < kc / 16; j++) {
+          const uint64_t ad = tc::sdesc(sbase + a_off + ((k0 + 16 * j) >> 3) * 128, 128, a_kw * 16);
+          const uint64_t bd = tc::sdesc(b + j * 256, 128, kc * 16);
+          tc::mma_bf16(tmem + dcol, ad, bd, idesc, (fresh && j == 0) ? 0u : 1u);
+        }
+        tc::commit(&empty[s]);
+        u++;
+      };
+      auto done = [&]() { if (ok) tc::commit(accbar); };
+      for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+        wait_op();                                                     // z staged
+        unit(SM_Z, 16, 0, 16, 64, 0, true);                            // F1
+        done();
+        wait_op();
+        unit(SM_H1, 64, 0, 64, 128, 0, true);                          // F2
+        done();
+        wait_op();
+        for (int h = 0; h < 2; h++)
+          for (int k = 0; k < 2; k++) unit(SM_H2, 128, 64 * k, 64, 128, 128 * h, k == 0);  // F3
+        done();
+        wait_op();
+        for (int k = 0; k < 4; k++) unit(SM_H3, 256, 64 * k, 64, 128, 256, k == 0);       // F4 c0
+        done();
+        for (int k = 0; k < 4; k++) unit(SM_H3, 256, 64 * k, 64, 128, 384, k == 0);       // F4 c1
+        for (int c = 0; c < 4; c++) {
+          wait_op();                                                   // dy chunk c written
+          for (int h = 0; h < 2; h++)
+            for (int k = 0; k < 2; k++)
+              unit(SM_DY, 128, 64 * k, 64, 128, 128 * h, c == 0 && k == 0);               // B1 c
+          if (c < 3) done();
+          if (c < 2)
+            for (int k = 0; k < 4; k++)
+              unit(SM_H3, 256, 64 * k, 64, 128, 256 + 128 * (c & 1), k == 0);             // F4 c+2
+        }
+        for (int h = 0; h < 2; h++)
+          for (int k = 0; k < 2; k++) unit(SM_H2, 128, 64 * k, 64, 128, 256 + 128 * h, k == 0);  // R3
+        done();
+        wait_op();                                                     // d3 written
+        for (int k = 0; k < 4; k++) unit(SM_H3, 256, 64 * k, 64, 128, 0, k == 0);         // B2
+        unit(SM_H1, 64, 0, 64, 128, 128, true);                        // R2
+        done();
+        wait_op();                                                     // d2 written
+        for (int k = 0; k < 2; k++) unit(SM_H2, 128, 64 * k, 64, 64, 0, k == 0);           // B3
+        unit(SM_Z, 16, 0, 16, 64, 64, true);                           // R1
+        done();
+        wait_op();                                                     // d1 written
+        unit(SM_H1, 64, 0, 64, 16, 0, true);                           // B4
+        done();
+      }
+      if (!ok) atomicOr(&g_fused_error, 2u);
+    }
+  } else {
+    // ---------------------------------------------------------------- epilogue
+    // warp w reads TMEM lane quadrant w % 4 (rows 32 (w % 4) ..) and the
+    // column quarter w / 4 of every accumulator
+    const int q = warp & 3, qq = warp >> 2;
+    const int r = 32 * q + lane;
+    const uint32_t tb = tmem + ((uint32_t)(32 * q) << 16);
+    uint32_t accs = 0;
+    bool ok = true;
+    float lsum = 0.f;
+    auto wait_acc = [&]() {
+      ok = ok && tc::mbar_wait(accbar, accs & 1, kLimit);
+      accs++;
+      tc::fence_after();
+    };
+    auto arrive = [&]() {
+      tc::fence_async_smem();
+      tc::fence_before();
+      tc::mbar_arrive(opbar);
+    };
+    for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+      const int64_t p = t * 128 + r;
+      const bool valid = p < a.P;
+      if (qq < 2) {  // E0: z (f32) -> bf16 A operand, columns [8 qq, 8 qq + 8)
+        float4 f0 = make_float4(0.f, 0.f, 0.f, 0.f), f1 = f0;
+        if (valid) {
+          const float4* src = reinterpret_cast<const float4*>(a.z + p * 16 + 8 * qq);
+          f0 = src[0];
+          f1 = src[1];
+        }
+        uint4 u;
+        __nv_bfloat162* h = reinterpret_cast<__nv_bfloat162*>(&u);
+        h[0] = __floats2bfloat162_rn(f0.x, f0.y);
+        h[1] = __floats2bfloat162_rn(f0.z, f0.w);
+        h[2] = __floats2bfloat162_rn(f1.x, f1.y);
+        h[3] = __floats2bfloat162_rn(f1.z, f1.w);
+        *reinterpret_cast<uint4*>(sm + SM_Z + tc::core_offset(r, qq, 16)) = u;
+      }
+      arrive();
+      float v[32], pre[32];
+      // E1..E3: hidden forward layers (columns of this warp's quarter)
+      wait_acc();
+      {
+        const int c0 = 16 * qq;
+        tc::tmem_ld16(tb + c0, v);
+#pragma unroll
+        for (int i = 0; i < 16; i++) v[i] = gelu_tanh(v[i] + sb4[c0 + i]);
+        put_row<16>(sm + SM_H1, r, c0, 64, v);
+      }
+      arrive();
+      wait_acc();
+      {
+        const int c0 = 32 * qq;
+        tc::tmem_ld32(tb + c0, v);
+#pragma unroll
+        for (int i = 0; i < 32; i++) v[i] = gelu_tanh(v[i] + sb5[c0 + i]);
+        put_row<32>(sm + SM_H2, r, c0, 128, v);
+      }
+      arrive();
+      wait_acc();
+#pragma unroll 1
+      for (int s2 = 0; s2 < 2; s2++) {
+        const int c0 = 64 * qq + 32 * s2;
+        tc::tmem_ld32(tb + c0, v);
+#pragma unroll
+        for (int i = 0; i < 32; i++) v[i] = gelu_tanh(v[i] + sb6[c0 + i]);
+        put_row<32>(sm + SM_H3, r, c0, 256, v);
+      }
+      arrive();
+      // E4: output chunks, L1 against F_gt, dy into the chunk buffer
+#pragma unroll 1
+      for (int c = 0; c < 4; c++) {
+        uint4 tg[4];
+        const int n0 = 128 * c + 32 * qq;
+        if (valid) {
+          const uint4* src = reinterpret_cast<const uint4*>(a.target + p * 512 + n0);
+#pragma unroll
+          for (int k = 0; k < 4; k++) tg[k] = src[k];
+        }
+        wait_acc();
+        tc::tmem_ld32(tb + 256 + 128 * (c & 1) + 32 * qq, v);
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+          const __nv_bfloat162* h2 = reinterpret_cast<const __nv_bfloat162*>(&tg[k]);
+#pragma unroll
+          for (int e = 0; e < 4; e++) {
+            const float2 tt = valid ? __bfloat1622float2(h2[e]) : make_float2(0.f, 0.f);
+            const int i = 8 * k + 2 * e;
+            const float d0 = v[i] + sb7[n0 + i] - tt.x;
+            const float d1 = v[i + 1] + sb7[n0 + i + 1] - tt.y;
+            if (valid) lsum += fabsf(d0) + fabsf(d1);
+            v[i] = valid ? (d0 > 0.f ? a.scale : (d0 < 0.f ? -a.scale : 0.f)) : 0.f;
+            v[i + 1] = valid ? (d1 > 0.f ? a.scale : (d1 < 0.f ? -a.scale : 0.f)) : 0.f;
+          }
+        }
+        put_row<32>(sm + SM_DY, r, 32 * qq, 128, v);
+        arrive();
+      }
+      // E5: d3 = dh3 * gelu'(pre3)
+      wait_acc();
+#pragma unroll 1
+      for (int s2 = 0; s2 < 2; s2++) {
+        const int c0 = 64 * qq + 32 * s2;
+        tc::tmem_ld32(tb + c0, v);
+        tc::tmem_ld32(tb + 256 + c0, pre);
+#pragma unroll
+        for (int i = 0; i < 32; i++) v[i] *= gelu_tanh_grad(pre[i] + sb6[c0 + i]);
+        put_row<32>(sm + SM_H3, r, c0, 256, v);
+      }
+      arrive();
+      // E6: d2 = dh2 * gelu'(pre2)
+      wait_acc();
+      {
+        const int c0 = 32 * qq;
+        tc::tmem_ld32(tb + c0, v);
+        tc::tmem_ld32(tb + 128 + c0, pre);
+#pragma unroll
+        for (int i = 0; i < 32; i++) v[i] *= gelu_tanh_grad(pre[i] + sb5[c0 + i]);
+        put_row<32>(sm + SM_H2, r, c0, 128, v);
+      }
+      arrive();
+      // E7: d1 = dh1 * gelu'(pre1)
+      wait_acc();
+      {
+        const int c0 = 16 * qq;
+        tc::tmem_ld16(tb + c0, v);
+        tc::tmem_ld16(tb + 64 + c0, pre);
+#pragma unroll
+        for (int i = 0; i < 16; i++) v[i] *= gelu_tanh_grad(pre[i] + sb4[c0 + i]);
+        put_row<16>(sm + SM_H1, r, c0, 64, v);
+      }
+      arrive();
+      // E8: dz
+      wait_acc();
+      if (qq == 0) {
+        tc::tmem_ld16(tb, v);
+        if (valid) {
+          float4* dst = reinterpret_cast<float4*>(a.dz + p * 16);
+#pragma unroll
+          for (int k = 0; k < 4; k++) dst[k] = make_float4(v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3]);
+        }
+      }
+    }
+    if (!ok) atomicOr(&g_fused_error, 4u);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) lsum += __shfl_xor_sync(0xffffffffu, lsum, o);
+    if (lane == 0 && lsum != 0.f) atomicAdd(a.loss, lsum * a.scale);
+  }
+  tc::fence_before();
+  __syncthreads();
+  if (warp == 0) tc::tmem_dealloc(tmem, 512);
+}
+
+struct Plan {
+  std::vector<Unit> units;
+  uint32_t off[kUnits], bytes[kUnits], piece0[kUnits + 1];
+  size_t total;
+};
+
+const Plan& plan() {
+  static Plan P;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    P.units = schedule();
+    uint32_t o = 0, pc = 0;
+    for (int i = 0; i < kUnits; i++) {
+      const Unit& U = P.units[i];
+      P.off[i] = o;
+      P.bytes[i] = (uint32_t)(U.rows * U.kc * 2);
+      P.piece0[i] = pc;
+      o += P.bytes[i];
+      pc += (uint32_t)(U.rows * (U.kc / 8));
+    }
+    P.piece0[kUnits] = pc;
+    P.total = o;
+  });
+  return P;
+}
+
+int sm_count() {
+  int dev = 0, n = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0)
+    n = 148;
+  return n;
+}
+
+}  // namespace
+
+size_t decode_pack_bytes() { return (plan().total + 255) & ~(size_t)255; }
+
+lgs_status launch_decode_fused(const lgs_ae_weights* w, const float* z, int64_t P,
+                               const uint16_t* target, float weight, float* loss, float* dz,
+                               void* pack, cudaStream_t s) {
+  const Plan& pl = plan();
+  if ((int)pl.units.size() != kUnits) {
+    set_error("decoder schedule size mismatch");
+    return LGS_ERR_INVALID;
+  }
+  PackArgs pa;
+  for (int m = 0; m < 4; m++) {
+    pa.mats[m] = reinterpret_cast<const __nv_bfloat16*>(w->W[4 + m]);
+    pa.mats[4 + m] = reinterpret_cast<const __nv_bfloat16*>(w->Wt[4 + m]);
+  }
+  for (int m = 0; m < 8; m++) pa.ld[m] = kCols[m];
+  for (int i = 0; i < kUnits; i++) {
+    pa.units[i] = pl.units[i];
+    pa.off[i] = pl.off[i];
+    pa.piece0[i] = pl.piece0[i];
+  }
+  pa.piece0[kUnits] = pl.piece0[kUnits];
+  pa.pack = static_cast<uint8_t*>(pack);
+  pack_units_kernel<<<(pl.piece0[kUnits] + 255) / 256, 256, 0, s>>>(pa);
+  LGS_CHECK_LAUNCH();
+  FusedArgs fa;
+  fa.pack = static_cast<const uint8_t*>(pack);
+  for (int i = 0; i < kUnits; i++) {
+    fa.off[i] = pl.off[i];
+    fa.bytes[i] = pl.bytes[i];
+  }
+  fa.b4 = w->b[4];
+  fa.b5 = w->b[5];
+  fa.b6 = w->b[6];
+  fa.b7 = w->b[7];
+  fa.z = z;
+  fa.target = reinterpret_cast<const __nv_bfloat16*>(target);
+  fa.dz = dz;
+  fa.P = P;
+  fa.scale = weight / ((float)P * 512.f);
+  fa.loss = loss;
+  LGS_CHECK_CUDA(set_smem_limit(reinterpret_cast<const void*>(decode_fused_kernel), (int)SM_ALL));
+  const int64_t ntiles = (P + 127) / 128;
+  const int grid = (int)std::min<int64_t>(ntiles, sm_count());
+  decode_fused_kernel<<<grid, kFusedThreads, SM_ALL, s>>>(fa);
+  LGS_CHECK_LAUNCH();
+  return LGS_OK;
+}
+
+unsigned fused_error_word() {
+  unsigned v = 0, zero = 0;
+  if (cudaMemcpyFromSymbol(&v, g_fused_error, sizeof(v)) != cudaSuccess) return 0;
+  cudaMemcpyToSymbol(g_fused_error, &zero, sizeof(zero));
+  return v;
+}
+
+}  // namespace lgs

@@ -70,6 +70,25 @@ __device__ __forceinline__ float raw_alpha(float o, float power) {
   return __fmul_rn(o, __expf(power));
 }
 
+// GELU in its tanh form (Hendrycks & Gimpel): 0.5 x (1 + tanh(u)),
+// u = sqrt(2/pi) (x + 0.044715 x^3), with the hardware tanh approximation,
+// and its derivative 0.5 (1 + t) + 0.5 x (1 - t^2) sqrt(2/pi) (1 + 0.134145 x^2).
+__device__ __forceinline__ float tanh_approx(float x) {
+  float y;
+  asm("tanh.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float gelu_tanh(float x) {
+  const float u = 0.7978845608028654f * fmaf(0.044715f * x, x * x, x);
+  return 0.5f * x * (1.f + tanh_approx(u));
+}
+__device__ __forceinline__ float gelu_tanh_grad(float x) {
+  const float x2 = x * x;
+  const float t = tanh_approx(0.7978845608028654f * fmaf(0.044715f * x, x2, x));
+  return fmaf(0.5f, 1.f + t,
+              0.5f * x * (1.f - t * t) * 0.7978845608028654f * fmaf(0.134145f, x2, 1.f));
+}
+
 __device__ __forceinline__ float to_float(float x) { return x; }
 __device__ __forceinline__ float to_float(__nv_bfloat16 x) { return __bfloat162float(x); }
 

@@ -15,4 +15,13 @@ lgs_status launch_project_bwd(const float* means, const float* quats, const floa
                               const float* grad2d, float* d_means, float* d_quats,
                               float* d_log_scales, float* d_logits, cudaStream_t s);
 
+// Fused Eq. 2 distillation (decoder forward, L1 against F_gt, gradient to
+// z); `pack` is decode_pack_bytes() of scratch for the packed weights.
+size_t decode_pack_bytes();
+lgs_status launch_decode_fused(const lgs_ae_weights* w, const float* z, int64_t P,
+                               const uint16_t* target, float weight, float* loss, float* dz,
+                               void* pack, cudaStream_t s);
+// Reads and clears the fused kernel's timeout word.
+unsigned fused_error_word();
+
 }  // namespace lgs

@@ -71,6 +71,28 @@ def test_decode_and_distillation_match_oracle(lgs):
     assert rel_err(dz.cpu().numpy(), 0.7 * dzr) < 2 * REL
 
 
+def test_fused_distillation_many_tiles(lgs):
+    """Eq. 2 through the fused decoder with several tiles per CTA and a
+    ragged last tile: loss and dz against the oracle."""
+    from oracle import ae
+    from paper_2511_16144_gb300.ae import AutoEncoder
+    enc, dec = synth.ae_init(seed=3007)
+    model = AutoEncoder(enc, dec)
+    rng = np.random.default_rng(8)
+    P = 152 * 128 * 2 + 77
+    z = rng.standard_normal((P, 16)).astype(np.float32)
+    t = synth.unit_rows(rng.standard_normal((P, 512))).astype(np.float32)
+    loss, dz = model.distill(torch.from_numpy(z).cuda(), torch.from_numpy(t).cuda().bfloat16())
+    l_ref, dz_ref = ae.distill(rounded(dec), bf16_round(z), bf16_round(t))
+    assert abs(loss.item() - l_ref) <= 1e-3 * l_ref
+    assert rel_err(dz.cpu().numpy(), dz_ref) < 2 * REL
+    # a second call on the same workspace gives the same answer
+    loss2, dz2 = model.distill(torch.from_numpy(z).cuda(), torch.from_numpy(t).cuda().bfloat16())
+    assert abs(loss2.item() - loss.item()) <= 1e-5 * loss.item()
+    assert rel_err(dz2.cpu().numpy(), dz.cpu().numpy()) < 1e-6
+    assert lgs.lgs_device_error() == 0
+
+
 @pytest.mark.parametrize("mode", ["recon", "enc_adapt"])
 def test_train_step_gradients_and_update(lgs, mode):
     from oracle import ae

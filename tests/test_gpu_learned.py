@@ -1,10 +1,10 @@
 """What the trained autoencoder gains (marked gpu).
 
-Setup (the learned-compression workload): 100k Gaussians in the 6x6x3 m room
-with spatially coherent 512-d semantics (64 3D Voronoi cells); the plain path
+Setup (the benchmark's frame): 300k Gaussians in the 6x6x3 m room with
+spatially coherent 512-d semantics (64 3D Voronoi cells); the plain path
 renders all 512 channels for 8 keyframes at 640x480, and those rendered maps
 are the autoencoder's online training data (200 Adam steps of 64k pixels,
-L2 + (1 - cos)).  The Gaussians' 16-d features are the encoder prior
+lr 3e-3, L2 + (1 - cos)).  The Gaussians' 16-d features are the encoder prior
 E(g_i) (Sec. III-B.2); the 16-d render is decoded by D and compared with the
 plain 512-channel render pixel by pixel (1 - cos over pixels with a
 non-zero reference).
@@ -12,6 +12,10 @@ non-zero reference).
 Baselines: the untrained autoencoder, a random linear 512 -> 16 projection
 with its pseudo-inverse as decoder, and an autoencoder trained on a different
 scene (a frozen, non-adapted encoder).
+
+The per-Gaussian N(0, 0.02) embedding noise sets a floor: a 16-d code cannot
+carry it, and the plain render keeps what survives alpha blending (about
+0.01-0.02 of cosine at this density, more for sparser maps).
 """
 import numpy as np
 import pytest
@@ -29,9 +33,9 @@ def cosine_error(y, ref):
     return float((1 - cos).mean().item()), int((~keep).sum().item())
 
 
-def semantic_scene(n, seed):
+def semantic_scene(n, seed, sem_seed):
     scene, cams = synth.indoor(n=n, n_cams=8, seed=seed)
-    g = synth.semantic_features(scene.means, synth.ROOM_LO, synth.ROOM_HI, seed=seed + 4)
+    g = synth.semantic_features(scene.means, synth.ROOM_LO, synth.ROOM_HI, seed=sem_seed)
     return scene.with_feats(g), cams
 
 
@@ -49,7 +53,7 @@ def train_ae(frames, seed, steps=200):
     gen = torch.Generator(device="cuda").manual_seed(seed)
     for _ in range(steps):
         idx = torch.randint(0, data.shape[0], (65536,), device="cuda", generator=gen)
-        model.train_step(data[idx].contiguous(), lr=1e-3)
+        model.train_step(data[idx].contiguous(), lr=3e-3)
     return model
 
 
@@ -69,7 +73,7 @@ def test_trained_autoencoder_gain():
     from paper_2511_16144_gb300.render import DeviceScene
     build.build()
     lgs.load()
-    scene, cams = semantic_scene(100_000, 1003)
+    scene, cams = semantic_scene(300_000, 1001, 1005)
     ds = DeviceScene.from_host(scene)
     frames = [render_feat(ds, c) for c in cams]
     model = train_ae(frames, 3003)
@@ -91,12 +95,12 @@ def test_trained_autoencoder_gain():
                   (ds.feats @ Pm).contiguous())
         lin.append(cosine_error(render_feat(ds16, c) @ Pinv, ref)[0])
     linear = float(np.mean(lin))
-    other_scene, other_cams = semantic_scene(100_000, 1013)
+    other_scene, other_cams = semantic_scene(300_000, 1011, 1015)
     ods = DeviceScene.from_host(other_scene)
     other = train_ae([render_feat(ods, c) for c in other_cams], 3013)
     frozen = np.mean([decoded_error(other, ds, ds, c, ref)[0]
                       for c, ref in zip(cams[::3], frames[::3])])
-    print(f"decoded cosine error: trained {trained:.4f}, untrained {untrained:.4f}, "
+    print(f"decoded cosine error: trained {trained:.4f}; untrained {untrained:.4f}, "
           f"linear+pinv {linear:.4f}, other-scene encoder {frozen:.4f}")
     assert trained <= 0.02, trained
-    assert trained < 0.5 * min(untrained, linear, frozen)
+    assert trained < 0.1 * min(untrained, linear, frozen)

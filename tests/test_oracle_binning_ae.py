@@ -72,12 +72,18 @@ def test_bin_sort_invariants_and_ties(oracle_lib):
 
 # ---------------------------------------------------------------- autoencoder
 
-def test_gelu_values():
+def test_gelu_tanh_form_against_normal_cdf():
     from oracle import ae
-    # x Phi(x): Phi(1) = 0.8413447460685429, Phi(-1) = 0.15865525393145707
-    np.testing.assert_allclose(ae.gelu(np.array([1.0, -1.0, 0.0, 3.0])),
-                               [0.8413447460685429, -0.15865525393145707, 0.0,
-                                3.0 * 0.9986501019683699], rtol=1e-14)
+    from scipy.special import ndtr
+    # the tanh form tracks x Phi(x) to within 4.73e-4, reached near x = 2.7;
+    # a wrong constant (e.g. 0.044 or 0.045, or 0.8 for sqrt(2/pi)) or a
+    # missing cubic term breaks the bound, a sign error breaks it by far
+    x = np.linspace(-8, 8, 160001)
+    dev = np.abs(ae.gelu(x) - x * ndtr(x))
+    assert dev.max() <= 4.8e-4
+    assert dev.max() >= 4.6e-4 and 2.4 < abs(x[dev.argmax()]) < 3.0
+    np.testing.assert_allclose(ae.gelu(np.array([0.0, 40.0, -40.0])), [0.0, 40.0, 0.0],
+                               atol=1e-12)
     # derivative against central differences
     x = np.linspace(-4, 4, 41)
     h = 1e-6
@@ -102,7 +108,8 @@ def test_mlp_forward_matches_loops():
                 for i in range(W.shape[1]):
                     acc += W[o, i] * h[i]
                 if li < len(layers) - 1:
-                    acc = 0.5 * acc * (1 + math.erf(acc / math.sqrt(2)))
+                    u = math.sqrt(2 / math.pi) * (acc + 0.044715 * acc ** 3)
+                    acc = 0.5 * acc * (1 + math.tanh(u))
                 out.append(acc)
             h = out
         np.testing.assert_allclose(y[p], h, rtol=1e-13, atol=1e-14)

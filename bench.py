@@ -270,7 +270,12 @@ def run_gpu(args, rank, world):
     # end to end through the C ABI with host buffers: per step the keyframe's
     # targets (RGB, depth, F_gt) go host -> device from pinned memory and the
     # loss comes back
-    e2e = measure_e2e(step16, g16, flush, args.steps, args.warmup)
+    rgb_b, dep_b, fgt_b = rgb_t.clone(), dep_t.clone(), f_gt.clone()
+    step16b = MappingStep(s16_bf, cams, rgb_b, dep_b, fgt_b, model=model,
+                          capacity=step16.bufs.capacity)
+    _, g16b, _ = timed(step16b, 1, 1)
+    e2e = measure_e2e([step16, step16b], [g16, g16b], args.steps, args.warmup)
+    del step16b
 
     if rank == 0:
         peaks, kind = measured_peaks()
@@ -377,37 +382,54 @@ def roofline_render_bwd(step, calls):
             "ms_per_launch": ms, "peak_note": FP32_PEAK_NOTE}
 
 
-def measure_e2e(step, graph, flush, k, warm):
+def measure_e2e(steps, graphs, k, warm):
+    """End to end through the C ABI with host buffers: every step uploads its
+    keyframe's targets (RGB, depth, F_gt) from pinned host memory and reads
+    the loss back.  Uploads run on a copy stream into one of two target sets
+    while the other set's step computes (keyframe k+1 arrives while the map
+    is optimised on keyframe k); all copies stay inside the timed region."""
     import torch
-    rgb_h = step.rgb_t.cpu().pin_memory()
-    dep_h = step.depth_t.cpu().pin_memory()
-    fgt_h = step.feat_t.cpu().pin_memory()
-    loss_h = torch.empty(1, dtype=torch.float32).pin_memory()
+    host = [(st.rgb_t.cpu().pin_memory(), st.depth_t.cpu().pin_memory(),
+             st.feat_t.cpu().pin_memory()) for st in steps]
+    loss_h = [torch.empty(1, dtype=torch.float32).pin_memory() for _ in steps]
+    copy = torch.cuda.Stream()
+    comp = torch.cuda.current_stream()
+    copied = [torch.cuda.Event() for _ in steps]
+    freed = [torch.cuda.Event() for _ in steps]
+    for e in freed:
+        e.record(comp)
 
-    def one():
-        step.rgb_t.copy_(rgb_h, non_blocking=True)
-        step.depth_t.copy_(dep_h, non_blocking=True)
-        step.feat_t.copy_(fgt_h, non_blocking=True)
-        graph.replay()
-        loss_h.copy_(step.loss, non_blocking=True)
+    def run(n):
+        for i in range(n):
+            j = i % 2
+            st = steps[j]
+            with torch.cuda.stream(copy):
+                copy.wait_event(freed[j])
+                st.rgb_t.copy_(host[j][0], non_blocking=True)
+                st.depth_t.copy_(host[j][1], non_blocking=True)
+                st.feat_t.copy_(host[j][2], non_blocking=True)
+                copied[j].record(copy)
+            comp.wait_event(copied[j])
+            graphs[j].replay()
+            loss_h[j].copy_(st.loss, non_blocking=True)
+            freed[j].record(comp)
 
-    for _ in range(warm):
-        flush.fill_(1.0)
-        one()
+    run(warm)
     torch.cuda.synchronize()
-    ts = []
-    for _ in range(k):
-        flush.fill_(1.0)
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record()
-        one()
-        b.record()
-        b.synchronize()
-        ts.append(a.elapsed_time(b))
-    ms = float(np.mean(ts))
-    h2d = sum(t.numel() * t.element_size() for t in (rgb_h, dep_h, fgt_h))
-    return {"value": step.pixels / 1e6 / (ms / 1e3), "unit": "Mpix/s", "ms_per_step": ms,
-            "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": 4}
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(comp)
+    copy.wait_event(a)
+    run(k)
+    copy_done = torch.cuda.Event()
+    copy_done.record(copy)
+    comp.wait_event(copy_done)
+    b.record(comp)
+    b.synchronize()
+    ms = a.elapsed_time(b) / k
+    h2d = sum(t.numel() * t.element_size() for t in host[0])
+    return {"value": steps[0].pixels / 1e6 / (ms / 1e3), "unit": "Mpix/s", "ms_per_step": ms,
+            "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": 4,
+            "overlap": "targets double-buffered on a copy stream"}
 
 
 # --------------------------------------------------------------------------- oracle

@@ -825,6 +825,6 @@ extern "C" lgs_status lgs_device_error(int* code) {
   unsigned v = 0, zero = 0;
   LGS_CHECK_CUDA(cudaMemcpyFromSymbol(&v, g_ae_error, sizeof(v)));
   LGS_CHECK_CUDA(cudaMemcpyToSymbol(g_ae_error, &zero, sizeof(zero)));
-  *code = (int)(v | (fused_error_word() << 4));
+  *code = (int)(v | (fused_error_word() << 4) | (sort_error_word() << 8));
   return LGS_OK;
 }

@@ -13,18 +13,31 @@
 //      at most 8 per pass).
 // Stability makes equal tiles keep depth order and equal depths keep index
 // order, which is exactly a stable sort of the 64-bit keys.
+//
+// Each radix pass is one kernel ("onesweep"): blocks take tile numbers in
+// launch order from an atomic counter, rank their 4096 keys per digit inside
+// the block, publish their per-digit counts, and find the counts of all
+// earlier tiles by decoupled look-back (walking back over published
+// aggregates until an inclusive prefix is found).  One histogram kernel per
+// sort gives every pass's global digit offsets.  The instance offsets come
+// from a single-pass look-back scan.  Spins are bounded: a wait that gives
+// up sets the device error word instead of hanging.
 #include "common.cuh"
 #include "kernels.cuh"
 
 namespace lgs {
 
-constexpr int kSortThreads = 256;
-constexpr int kSortItems = 8;
-constexpr int kSortTile = kSortThreads * kSortItems;  // items per block and pass
+constexpr int kOsThreads = 256;
+constexpr int kOsItems = 16;
+constexpr int kOsTile = kOsThreads * kOsItems;  // keys per onesweep tile
 constexpr int kRadix = 256;
-constexpr int kScanThreads = 256;
-constexpr int kScanItems = 16;
-constexpr int kScanChunk = kScanThreads * kScanItems;
+constexpr uint32_t kFlagAgg = 1u << 30, kFlagInc = 2u << 30, kValMask = (1u << 30) - 1;
+constexpr uint64_t kFlag64Agg = 1ull << 62, kFlag64Inc = 2ull << 62,
+                   kVal64Mask = (1ull << 62) - 1;
+constexpr uint32_t kSpinLimit = 1u << 22;
+constexpr int kPassesMax = 8;  // 4 depth + 1 camera + up to 3 tile
+
+__device__ unsigned g_sort_error;  // a look-back gave up
 
 __device__ __forceinline__ uint32_t lanemask_lt() {
   uint32_t m;
@@ -36,9 +49,22 @@ __device__ __forceinline__ int64_t item_count(const int64_t* n_dev, int64_t n_ho
   return n_dev ? *n_dev : n_host;
 }
 
-// ------------------------------------------------------------------ scan
-// Exclusive prefix sum in three launches: per-chunk sums, a one-block scan of
-// those sums, and a per-chunk rescan with the carried offset.
+__device__ __forceinline__ uint32_t ld_relaxed(const uint32_t* p) {
+  uint32_t v;
+  asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_relaxed(uint32_t* p, uint32_t v) {
+  asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ uint64_t ld_relaxed64(const uint64_t* p) {
+  uint64_t v;
+  asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_relaxed64(uint64_t* p, uint64_t v) {
+  asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
 
 template <typename T>
 __device__ T block_exclusive_scan(T v, T* warp_tot, T& total) {
@@ -67,209 +93,139 @@ __device__ T block_exclusive_scan(T v, T* warp_tot, T& total) {
   return before + x - v;
 }
 
-template <typename Tin, typename Tout>
-__global__ void scan_reduce_kernel(const Tin* __restrict__ in, int64_t n, Tout* __restrict__ part) {
-  __shared__ Tout wt[32];
-  int64_t base = (int64_t)blockIdx.x * kScanChunk;
-  Tout s = 0;
-  for (int k = 0; k < kScanItems; k++) {
-    int64_t i = base + (int64_t)k * kScanThreads + threadIdx.x;
-    if (i < n) s += (Tout)in[i];
-  }
-  Tout tot;
-  block_exclusive_scan<Tout>(s, wt, tot);
-  if (threadIdx.x == 0) part[blockIdx.x] = tot;
-}
+// ------------------------------------------------------------------ histogram
 
-template <typename T>
-__global__ void scan_partials_kernel(T* __restrict__ part, int64_t nb, T* __restrict__ total_out) {
-  __shared__ T wt[32];
-  T carry = 0;
-  for (int64_t b0 = 0; b0 < nb; b0 += blockDim.x) {
-    int64_t i = b0 + threadIdx.x;
-    T v = i < nb ? part[i] : T(0);
-    T tot;
-    T ex = block_exclusive_scan<T>(v, wt, tot);
-    if (i < nb) part[i] = carry + ex;
-    carry += tot;
-  }
-  if (threadIdx.x == 0 && total_out) *total_out = carry;
-}
+struct HistPasses {
+  int n;
+  int shift[4];
+  uint32_t mask[4];
+};
 
-template <typename Tin, typename Tout>
-__global__ void scan_apply_kernel(const Tin* in, Tout* out, int64_t n,
-                                  const Tout* __restrict__ part) {
-  __shared__ Tout buf[kScanChunk];
-  __shared__ Tout wt[32];
-  int64_t base = (int64_t)blockIdx.x * kScanChunk;
-  for (int k = 0; k < kScanItems; k++) {
-    int64_t i = base + (int64_t)k * kScanThreads + threadIdx.x;
-    buf[k * kScanThreads + threadIdx.x] = i < n ? (Tout)in[i] : Tout(0);
+// Global digit histograms of up to four passes in one read of the keys.
+__global__ void __launch_bounds__(256) hist_kernel(const uint32_t* __restrict__ keys,
+                                                   const int64_t* n_dev, int64_t n_host,
+                                                   HistPasses hp, uint32_t* __restrict__ ghist) {
+  __shared__ uint32_t h[4][kRadix];
+  const int lane = threadIdx.x & 31;
+  for (int i = threadIdx.x; i < 4 * kRadix; i += 256) (&h[0][0])[i] = 0;
+  __syncthreads();
+  const int64_t n = item_count(n_dev, n_host);
+  const int64_t stride = (int64_t)gridDim.x * 256;
+  for (int64_t b = (int64_t)blockIdx.x * 256; b < n; b += stride) {
+    const int64_t idx = b + threadIdx.x;
+    const bool valid = idx < n;
+    const uint32_t k = valid ? keys[idx] : 0u;
+    for (int p = 0; p < hp.n; p++) {
+      const uint32_t d = valid ? (k >> hp.shift[p]) & hp.mask[p] : (uint32_t)(kRadix + lane);
+      const uint32_t peers = __match_any_sync(0xffffffffu, d);
+      if (valid && lane == __ffs(peers) - 1) atomicAdd(&h[p][d], (uint32_t)__popc(peers));
+    }
   }
   __syncthreads();
-  Tout loc[kScanItems];
-  Tout s = 0;
-#pragma unroll
-  for (int k = 0; k < kScanItems; k++) {
-    loc[k] = s;
-    s += buf[threadIdx.x * kScanItems + k];
-  }
-  Tout tot;
-  Tout ex = block_exclusive_scan<Tout>(s, wt, tot) + part[blockIdx.x];
-#pragma unroll
-  for (int k = 0; k < kScanItems; k++) buf[threadIdx.x * kScanItems + k] = ex + loc[k];
-  __syncthreads();
-  for (int k = 0; k < kScanItems; k++) {
-    int64_t i = base + (int64_t)k * kScanThreads + threadIdx.x;
-    if (i < n) out[i] = buf[k * kScanThreads + threadIdx.x];
+  for (int i = threadIdx.x; i < hp.n * kRadix; i += 256) {
+    const uint32_t c = (&h[0][0])[i];
+    if (c) atomicAdd(ghist + i, c);
   }
 }
 
-template <typename Tin, typename Tout>
-static void exclusive_scan(const Tin* in, Tout* out, int64_t n, Tout* part, Tout* total,
-                           cudaStream_t s) {
-  int64_t nb = (n + kScanChunk - 1) / kScanChunk;
-  if (nb == 0) nb = 1;
-  scan_reduce_kernel<Tin, Tout><<<(unsigned)nb, kScanThreads, 0, s>>>(in, n, part);
-  scan_partials_kernel<Tout><<<1, 1024, 0, s>>>(part, nb, total);
-  scan_apply_kernel<Tin, Tout><<<(unsigned)nb, kScanThreads, 0, s>>>(in, out, n, part);
-}
+// ------------------------------------------------------------------ onesweep pass
 
-static int64_t scan_partials_len(int64_t n) { return (n + kScanChunk - 1) / kScanChunk + 1; }
-
-// ------------------------------------------------------------------ radix pass
-// Per pass: per-block digit histograms (digit-major, so one exclusive scan
-// gives every block's output offset per digit), then a stable scatter that
-// ranks keys inside each warp with match_any, orders them by digit in shared
-// memory and writes each digit's run contiguously.
-
-__global__ void __launch_bounds__(kSortThreads)
-radix_hist_kernel(const uint32_t* __restrict__ keys, const int64_t* n_dev, int64_t n_host,
-                  int shift, uint32_t mask, uint32_t* __restrict__ counts, int nblocks) {
-  __shared__ uint32_t h[kSortThreads / 32][kRadix];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int i = threadIdx.x; i < (kSortThreads / 32) * kRadix; i += kSortThreads)
-    (&h[0][0])[i] = 0;
-  __syncthreads();
-  int64_t n = item_count(n_dev, n_host);
-  int64_t base = (int64_t)blockIdx.x * kSortTile + warp * (32 * kSortItems);
-#pragma unroll
-  for (int r = 0; r < kSortItems; r++) {
-    int64_t idx = base + r * 32 + lane;
-    bool valid = idx < n;
-    uint32_t d = valid ? (keys[idx] >> shift) & mask : (uint32_t)(kRadix + lane);
-    uint32_t peers = __match_any_sync(0xffffffffu, d);
-    if (valid && lane == __ffs(peers) - 1) h[warp][d] += __popc(peers);
-  }
-  __syncthreads();
-  for (int d = threadIdx.x; d < kRadix; d += kSortThreads) {
-    uint32_t s = 0;
-#pragma unroll
-    for (int w = 0; w < kSortThreads / 32; w++) s += h[w][d];
-    counts[(int64_t)d * nblocks + blockIdx.x] = s;
-  }
-}
-
-__global__ void __launch_bounds__(kSortThreads)
-radix_scatter_kernel(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin,
-                     uint32_t* __restrict__ kout, uint32_t* __restrict__ vout,
-                     const int64_t* n_dev, int64_t n_host, int shift, uint32_t mask,
-                     const uint32_t* __restrict__ offsets, int nblocks) {
-  __shared__ uint32_t wcnt[kSortThreads / 32][kRadix];
+__global__ void __launch_bounds__(kOsThreads)
+onesweep_kernel(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin,
+                uint32_t* __restrict__ kout, uint32_t* __restrict__ vout, const int64_t* n_dev,
+                int64_t n_host, int shift, uint32_t mask, const uint32_t* __restrict__ ghist,
+                uint32_t* status, uint32_t* counter) {
+  __shared__ uint32_t wcnt[kOsThreads / 32][kRadix];
   __shared__ uint32_t dstart[kRadix];
+  __shared__ uint32_t goff[kRadix];
   __shared__ uint32_t wt[32];
-  __shared__ uint32_t sk[kSortTile], sv[kSortTile];
+  __shared__ uint32_t sk[kOsTile], sv[kOsTile];
+  __shared__ uint32_t s_tile;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int i = threadIdx.x; i < (kSortThreads / 32) * kRadix; i += kSortThreads)
+  for (int i = threadIdx.x; i < (kOsThreads / 32) * kRadix; i += kOsThreads)
     (&wcnt[0][0])[i] = 0;
+  if (threadIdx.x == 0) s_tile = atomicAdd(counter, 1u);
   __syncthreads();
-  int64_t n = item_count(n_dev, n_host);
-  int64_t blk0 = (int64_t)blockIdx.x * kSortTile;
+  const uint32_t tile = s_tile;
+  const int64_t n = item_count(n_dev, n_host);
+  const int64_t blk0 = (int64_t)tile * kOsTile;
   if (blk0 >= n) return;
-  int64_t base = blk0 + warp * (32 * kSortItems);
-  uint32_t key[kSortItems], val[kSortItems], rank[kSortItems];
+  const int64_t base = blk0 + warp * (32 * kOsItems);
+  uint32_t key[kOsItems], val[kOsItems], rank[kOsItems];
   const uint32_t lt = lanemask_lt();
 #pragma unroll
-  for (int r = 0; r < kSortItems; r++) {
-    int64_t idx = base + r * 32 + lane;
-    bool valid = idx < n;
+  for (int r = 0; r < kOsItems; r++) {
+    const int64_t idx = base + r * 32 + lane;
+    const bool valid = idx < n;
     key[r] = valid ? kin[idx] : 0u;
     val[r] = valid ? vin[idx] : 0u;
-    uint32_t d = valid ? (key[r] >> shift) & mask : (uint32_t)(kRadix + lane);
-    uint32_t peers = __match_any_sync(0xffffffffu, d);
-    uint32_t prior = valid ? wcnt[warp][d] : 0u;
+    const uint32_t d = valid ? (key[r] >> shift) & mask : (uint32_t)(kRadix + lane);
+    const uint32_t peers = __match_any_sync(0xffffffffu, d);
+    const uint32_t prior = valid ? wcnt[warp][d] : 0u;
     rank[r] = prior + __popc(peers & lt);
     __syncwarp();
     if (valid && lane == __ffs(peers) - 1) wcnt[warp][d] = prior + __popc(peers);
     __syncwarp();
   }
   __syncthreads();
-  // per digit: exclusive offsets across warps, then across digits
+  const int d = threadIdx.x;  // one digit per thread
   uint32_t tot = 0;
-  if (threadIdx.x < kRadix) {
-    int d = threadIdx.x;
 #pragma unroll
-    for (int w = 0; w < kSortThreads / 32; w++) {
-      uint32_t t = wcnt[w][d];
-      wcnt[w][d] = tot;
-      tot += t;
-    }
+  for (int w = 0; w < kOsThreads / 32; w++) {
+    const uint32_t t = wcnt[w][d];
+    wcnt[w][d] = tot;
+    tot += t;
   }
   uint32_t all;
-  uint32_t ex = block_exclusive_scan<uint32_t>(tot, wt, all);
-  if (threadIdx.x < kRadix) dstart[threadIdx.x] = ex;
+  dstart[d] = block_exclusive_scan<uint32_t>(tot, wt, all);
+  const uint32_t gbase = block_exclusive_scan<uint32_t>(ghist[d], wt, all);
+  // decoupled look-back over the earlier tiles' published counts of digit d
+  uint32_t prefix = 0;
+  uint32_t* st = status + (size_t)tile * kRadix;
+  if (tile == 0) {
+    st_relaxed(st + d, tot | kFlagInc);
+  } else {
+    st_relaxed(st + d, tot | kFlagAgg);
+    int64_t j = (int64_t)tile - 1;
+    uint32_t spins = 0;
+    while (j >= 0) {
+      const uint32_t v = ld_relaxed(status + (size_t)j * kRadix + d);
+      const uint32_t flag = v & ~kValMask;
+      if (flag == 0) {
+        if (++spins > kSpinLimit) {
+          atomicOr(&g_sort_error, 1u);
+          break;
+        }
+        continue;
+      }
+      prefix += v & kValMask;
+      if (flag == kFlagInc) break;
+      j--;
+    }
+    st_relaxed(st + d, (prefix + tot) | kFlagInc);
+  }
+  goff[d] = gbase + prefix;
   __syncthreads();
 #pragma unroll
-  for (int r = 0; r < kSortItems; r++) {
-    int64_t idx = base + r * 32 + lane;
+  for (int r = 0; r < kOsItems; r++) {
+    const int64_t idx = base + r * 32 + lane;
     if (idx < n) {
-      uint32_t d = (key[r] >> shift) & mask;
-      uint32_t pos = dstart[d] + wcnt[warp][d] + rank[r];
+      const uint32_t dd = (key[r] >> shift) & mask;
+      const uint32_t pos = dstart[dd] + wcnt[warp][dd] + rank[r];
       sk[pos] = key[r];
       sv[pos] = val[r];
     }
   }
   __syncthreads();
-  int m = (int)((n - blk0) < (int64_t)kSortTile ? (n - blk0) : (int64_t)kSortTile);
-  for (int j = threadIdx.x; j < m; j += kSortThreads) {
-    uint32_t k = sk[j];
-    uint32_t d = (k >> shift) & mask;
-    uint32_t o = offsets[(int64_t)d * nblocks + blockIdx.x] + (uint32_t)j - dstart[d];
+  const int m = (int)((n - blk0) < (int64_t)kOsTile ? (n - blk0) : (int64_t)kOsTile);
+  for (int j = threadIdx.x; j < m; j += kOsThreads) {
+    const uint32_t k = sk[j];
+    const uint32_t dd = (k >> shift) & mask;
+    const uint32_t o = goff[dd] + (uint32_t)j - dstart[dd];
     kout[o] = k;
     vout[o] = sv[j];
   }
 }
-
-struct SortBufs {
-  uint32_t* counts;   // [kRadix * nblocks]
-  uint32_t* part;     // scan partials
-};
-
-// Stable LSD sort of (key, val) pairs on bits [0, nbits); ping-pongs between
-// (k0, v0) and (k1, v1).  Returns true when the result ended in (k1, v1).
-static bool radix_sort(uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t* v1,
-                       const int64_t* n_dev, int64_t n_max, int nbits, const SortBufs& b,
-                       cudaStream_t s) {
-  int nblocks = (int)((n_max + kSortTile - 1) / kSortTile);
-  if (nblocks == 0) return false;
-  bool flipped = false;
-  for (int shift = 0; shift < nbits; shift += 8) {
-    int bits = std::min(8, nbits - shift);
-    uint32_t mask = (1u << bits) - 1u;
-    radix_hist_kernel<<<nblocks, kSortThreads, 0, s>>>(k0, n_dev, n_max, shift, mask, b.counts,
-                                                       nblocks);
-    exclusive_scan<uint32_t, uint32_t>(b.counts, b.counts, (int64_t)kRadix * nblocks, b.part,
-                                       (uint32_t*)nullptr, s);
-    radix_scatter_kernel<<<nblocks, kSortThreads, 0, s>>>(k0, v0, k1, v1, n_dev, n_max, shift,
-                                                          mask, b.counts, nblocks);
-    std::swap(k0, k1);
-    std::swap(v0, v1);
-    flipped = !flipped;
-  }
-  return flipped;
-}
-
-static int sort_passes(int nbits) { return (nbits + 7) / 8; }
 
 // ------------------------------------------------------------------ binning kernels
 
@@ -292,51 +248,148 @@ __global__ void camera_keys_kernel(const uint32_t* __restrict__ vals, int64_t m,
     keys[i] = vals[i] / n;
 }
 
-__global__ void tile_count_kernel(const uint32_t* __restrict__ order,
-                                  const ushort4* __restrict__ rect, int64_t m,
-                                  uint32_t* __restrict__ cnt) {
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    ushort4 r = rect[order[i]];
-    cnt[i] = (r.z > r.x && r.w > r.y) ? (uint32_t)(r.z - r.x) * (uint32_t)(r.w - r.y) : 0u;
+// Exclusive prefix of the covered-tile counts of the depth-ordered items
+// (single pass, decoupled look-back per 4096-item tile); the last tile also
+// writes K, and the number to sort (K, or 0 when K exceeds capacity).
+__global__ void __launch_bounds__(256)
+count_scan_kernel(const uint32_t* __restrict__ order, const ushort4* __restrict__ rect, int64_t m,
+                  uint64_t* __restrict__ offs, int64_t capacity, int64_t* __restrict__ k_out,
+                  int64_t* __restrict__ sort_n, uint64_t* status, uint32_t* counter) {
+  __shared__ uint64_t wt[32];
+  __shared__ uint64_t s_prefix;
+  __shared__ uint32_t s_tile;
+  if (threadIdx.x == 0) s_tile = atomicAdd(counter, 1u);
+  __syncthreads();
+  const uint32_t tile = s_tile;
+  const int64_t blk0 = (int64_t)tile * kOsTile;
+  if (blk0 >= m) return;
+  const int64_t i0 = blk0 + (int64_t)threadIdx.x * kOsItems;
+  uint32_t c[kOsItems];
+  uint64_t sum = 0;
+#pragma unroll
+  for (int k = 0; k < kOsItems; k++) {
+    const int64_t i = i0 + k;
+    c[k] = 0;
+    if (i < m) {
+      const ushort4 r = rect[order[i]];
+      if (r.z > r.x && r.w > r.y) c[k] = (uint32_t)(r.z - r.x) * (uint32_t)(r.w - r.y);
+    }
+    sum += c[k];
+  }
+  uint64_t total;
+  const uint64_t ex = block_exclusive_scan<uint64_t>(sum, wt, total);
+  if (threadIdx.x == 0) {
+    uint64_t prefix = 0;
+    if (tile == 0) {
+      st_relaxed64(status, total | kFlag64Inc);
+    } else {
+      st_relaxed64(status + tile, total | kFlag64Agg);
+      int64_t j = (int64_t)tile - 1;
+      uint32_t spins = 0;
+      while (j >= 0) {
+        const uint64_t v = ld_relaxed64(status + j);
+        const uint64_t flag = v & ~kVal64Mask;
+        if (flag == 0) {
+          if (++spins > kSpinLimit) {
+            atomicOr(&g_sort_error, 2u);
+            break;
+          }
+          continue;
+        }
+        prefix += v & kVal64Mask;
+        if (flag == kFlag64Inc) break;
+        j--;
+      }
+      st_relaxed64(status + tile, (prefix + total) | kFlag64Inc);
+    }
+    s_prefix = prefix;
+    if (blk0 + kOsTile >= m) {  // the last tile
+      const uint64_t k = prefix + total;
+      offs[m] = k;
+      *k_out = (int64_t)k;
+      *sort_n = (int64_t)k <= capacity ? (int64_t)k : 0;
+    }
+  }
+  __syncthreads();
+  uint64_t run = s_prefix + ex;
+#pragma unroll
+  for (int k = 0; k < kOsItems; k++) {
+    const int64_t i = i0 + k;
+    if (i < m) offs[i] = run;
+    run += c[k];
   }
 }
 
-// K and the number of instances to sort (K, or 0 when K exceeds capacity).
-__global__ void finish_count_kernel(const uint64_t* __restrict__ total, int64_t capacity,
-                                    int64_t* __restrict__ k_out, int64_t* __restrict__ sort_n) {
-  uint64_t k = *total;
-  *k_out = (int64_t)k;
-  *sort_n = (int64_t)k <= capacity ? (int64_t)k : 0;
+// One thread per instance slot: slot o belongs to the depth-ordered item i
+// with offs[i] <= o < offs[i+1].  The block brackets its 2048 consecutive
+// slots by two binary searches; when they span at most 2049 items (always,
+// unless invisible items of one camera sit between) the block stages that
+// slice of offs in shared memory and every thread searches it, otherwise
+// threads search the bracket in global memory.  Writes are coalesced and the
+// work is balanced however many tiles a Gaussian covers.
+constexpr int kEmitThreads = 256;
+constexpr int kEmitPer = 8;
+constexpr int kEmitSlots = kEmitThreads * kEmitPer;
+
+// Last index i in [lo, hi) with a[i] <= o, given a[lo] <= o < a[hi].
+template <typename A>
+__device__ __forceinline__ int64_t last_le(const A& a, int64_t lo, int64_t hi, uint64_t o) {
+  while (hi - lo > 1) {
+    const int64_t mid = (lo + hi) >> 1;
+    if (a(mid) <= o) lo = mid;
+    else hi = mid;
+  }
+  return lo;
 }
 
-__global__ void emit_kernel(const uint32_t* __restrict__ order, const ushort4* __restrict__ rect,
-                            const uint64_t* __restrict__ offs, int64_t m, uint32_t n,
-                            int tiles_x, uint32_t tiles, const int64_t* __restrict__ sort_n,
-                            uint32_t* __restrict__ tkey, uint32_t* __restrict__ tval) {
-  if (*sort_n == 0) return;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    uint32_t item = order[i];
-    ushort4 r = rect[item];
-    if (!(r.z > r.x && r.w > r.y)) continue;
-    uint32_t c = item / n, g = item - c * n;
-    uint64_t o = offs[i];
-    for (int ty = r.y; ty < r.w; ty++)
-      for (int tx = r.x; tx < r.z; tx++) {
-        tkey[o] = c * tiles + (uint32_t)(ty * tiles_x + tx);
-        tval[o] = g;
-        o++;
-      }
+__global__ void __launch_bounds__(kEmitThreads)
+emit_kernel(const uint32_t* __restrict__ order, const ushort4* __restrict__ rect,
+            const uint64_t* __restrict__ offs, int64_t m, uint32_t n, int tiles_x, uint32_t tiles,
+            uint32_t n_tiles_all, const int64_t* __restrict__ sort_n,
+            uint32_t* __restrict__ tkey, uint32_t* __restrict__ tval) {
+  __shared__ uint64_t s_off[kEmitSlots + 2];
+  __shared__ int64_t s_lo, s_hi;
+  const int64_t K = *sort_n;
+  const int64_t o0 = (int64_t)blockIdx.x * kEmitSlots;
+  if (o0 >= K) return;
+  const int64_t o1 = o0 + kEmitSlots < K ? o0 + kEmitSlots : K;
+  auto g = [&](int64_t i) { return offs[i]; };
+  if (threadIdx.x == 0) s_lo = last_le(g, 0, m, (uint64_t)o0);
+  if (threadIdx.x == 32) s_hi = last_le(g, 0, m, (uint64_t)(o1 - 1));
+  __syncthreads();
+  const int64_t lo = s_lo, hi = s_hi;
+  const int64_t span = hi - lo + 1;  // items holding slots [o0, o1)
+  const bool staged = span <= kEmitSlots + 1;
+  if (staged)
+    for (int64_t j = threadIdx.x; j <= span; j += kEmitThreads) s_off[j] = offs[lo + j];
+  __syncthreads();
+  auto sm = [&](int64_t i) { return s_off[i]; };
+  for (int r = 0; r < kEmitPer; r++) {
+    const int64_t o = o0 + (int64_t)r * kEmitThreads + threadIdx.x;
+    if (o >= o1) break;
+    const int64_t i = staged ? lo + last_le(sm, 0, span, (uint64_t)o)
+                             : last_le(g, lo, hi + 1, (uint64_t)o);
+    const uint32_t item = order[i];
+    const ushort4 rc = rect[item];
+    const uint32_t w = (uint32_t)(rc.z - rc.x), h = (uint32_t)(rc.w - rc.y);
+    const uint64_t local = (uint64_t)o - offs[i];
+    if (rc.z <= rc.x || rc.w <= rc.y || local >= (uint64_t)w * h) continue;  // cannot happen
+    const uint32_t ty = rc.y + (uint32_t)local / w, tx = rc.x + (uint32_t)local % w;
+    const uint32_t c = item / n;
+    const uint32_t key = c * tiles + ty * (uint32_t)tiles_x + tx;
+    if (key >= n_tiles_all) continue;  // cannot happen
+    tkey[o] = key;
+    tval[o] = item - c * n;
   }
 }
 
 __global__ void ranges_kernel(const uint32_t* __restrict__ tkey, const int64_t* __restrict__ sort_n,
-                              uint2* __restrict__ ranges) {
+                              uint32_t n_tiles_all, uint2* __restrict__ ranges) {
   int64_t k = *sort_n;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < k;
        i += (int64_t)gridDim.x * blockDim.x) {
     uint32_t t = tkey[i];
+    if (t >= n_tiles_all) continue;
     if (i == 0 || tkey[i - 1] != t) ranges[t].x = (uint32_t)i;
     if (i == k - 1 || tkey[i + 1] != t) ranges[t].y = (uint32_t)(i + 1);
   }
@@ -357,32 +410,68 @@ __global__ void keys_kernel(const uint32_t* __restrict__ tkey, const uint32_t* _
 
 // ------------------------------------------------------------------ workspace
 
-struct Layout {
-  size_t dk0, dk1, dv0, dv1, cnt, offs, tk0, tk1, tv, counts, part, part64, scal, total;
-};
-
 static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+static int64_t tiles_of(int64_t n) { return (n + kOsTile - 1) / kOsTile; }
+
+struct Layout {
+  size_t dk0, dk1, dv0, dv1, offs, tk0, tk1, tv;
+  size_t zero_begin, ghist, counters, status[kPassesMax], scan_status, scal, zero_end;
+  size_t total;
+};
 
 static Layout layout(int64_t n, int n_cams, int64_t capacity) {
   Layout L;
-  int64_t m = (int64_t)n_cams * n;
-  int64_t nmax = std::max<int64_t>(m, capacity);
-  int64_t nblocks = (nmax + kSortTile - 1) / kSortTile;
+  const int64_t m = (int64_t)n_cams * n;
   size_t o = 0;
   auto take = [&](size_t bytes) { size_t at = o; o += align256(bytes); return at; };
   L.dk0 = take(4 * m); L.dk1 = take(4 * m); L.dv0 = take(4 * m); L.dv1 = take(4 * m);
-  L.cnt = take(4 * m);
   L.offs = take(8 * (m + 1));
   L.tk0 = take(4 * capacity); L.tk1 = take(4 * capacity); L.tv = take(4 * capacity);
-  L.counts = take(4 * (size_t)kRadix * std::max<int64_t>(nblocks, 1));
-  L.part = take(4 * scan_partials_len((int64_t)kRadix * std::max<int64_t>(nblocks, 1)));
-  L.part64 = take(8 * scan_partials_len(m + 1));
+  L.zero_begin = o;
+  L.ghist = take(4 * kPassesMax * kRadix);
+  L.counters = take(4 * (kPassesMax + 1));
+  for (int p = 0; p < kPassesMax; p++)
+    L.status[p] = take(4 * (size_t)kRadix * std::max<int64_t>(1, tiles_of(p < 5 ? m : capacity)));
+  L.scan_status = take(8 * std::max<int64_t>(1, tiles_of(m)));
   L.scal = take(8 * 4);
+  L.zero_end = o;
   L.total = o;
   return L;
 }
 
-static int grid_for(int64_t m) { return (int)std::max<int64_t>(1, std::min<int64_t>((m + 255) / 256, 152 * 16)); }
+static int grid_for(int64_t m) {
+  return (int)std::max<int64_t>(1, std::min<int64_t>((m + 255) / 256, 152 * 16));
+}
+
+// Stable LSD sort of (key, val) on bits [bit0, bit0 + nbits) with onesweep
+// passes of <= 8 bits, passes numbered from pass0 in the workspace.  Returns
+// true when the result ended in (k1, v1).
+static bool onesweep_sort(uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t* v1,
+                          const int64_t* n_dev, int64_t n_max, int nbits, int pass0,
+                          const Layout& L, char* ws, cudaStream_t s) {
+  const int npass = (nbits + 7) / 8;
+  uint32_t* ghist = (uint32_t*)(ws + L.ghist) + pass0 * kRadix;
+  uint32_t* counters = (uint32_t*)(ws + L.counters);
+  HistPasses hp{npass, {0, 0, 0, 0}, {0, 0, 0, 0}};
+  for (int p = 0; p < npass; p++) {
+    hp.shift[p] = 8 * p;
+    const int bits = std::min(8, nbits - 8 * p);
+    hp.mask[p] = (1u << bits) - 1u;
+  }
+  const int64_t ntile = std::max<int64_t>(1, tiles_of(n_max));
+  hist_kernel<<<(unsigned)std::min<int64_t>(ntile * 2, 152 * 4), 256, 0, s>>>(k0, n_dev, n_max, hp,
+                                                                           ghist);
+  bool flipped = false;
+  for (int p = 0; p < npass; p++) {
+    onesweep_kernel<<<(unsigned)ntile, kOsThreads, 0, s>>>(
+        k0, v0, k1, v1, n_dev, n_max, hp.shift[p], hp.mask[p], ghist + p * kRadix,
+        (uint32_t*)(ws + L.status[pass0 + p]), counters + pass0 + p);
+    std::swap(k0, k1);
+    std::swap(v0, v1);
+    flipped = !flipped;
+  }
+  return flipped;
+}
 
 }  // namespace lgs
 
@@ -405,7 +494,8 @@ extern "C" lgs_status gs_bin_sort(const float* proj, const uint16_t* rect, int64
   LGS_CHECK_ARG(n_cams >= 1 && n_cams <= LGS_MAX_CAMS, "n_cams out of range");
   LGS_CHECK_ARG(tiles_x >= 1 && tiles_y >= 1 && tiles_x <= 65535 && tiles_y <= 65535,
                 "bad tile grid");
-  LGS_CHECK_ARG(capacity >= 0 && capacity < ((int64_t)1 << 32), "capacity out of range");
+  LGS_CHECK_ARG(capacity >= 0 && capacity < ((int64_t)1 << 30), "capacity out of range");
+  LGS_CHECK_ARG((int64_t)n_cams * n < ((int64_t)1 << 30), "n_cams * n out of range");
   LGS_CHECK_ARG(ranges && n_instances_dev && workspace, "null pointer");
   LGS_CHECK_ARG(n == 0 || (proj && rect), "null pointer");
   LGS_CHECK_ARG(capacity == 0 || ids, "ids is null");
@@ -419,56 +509,65 @@ extern "C" lgs_status gs_bin_sort(const float* proj, const uint16_t* rect, int64
   cudaStream_t s = as_stream(stream);
   char* ws = (char*)workspace;
   auto U32 = [&](size_t off) { return (uint32_t*)(ws + off); };
-  int64_t* scal = (int64_t*)(ws + L.scal);
-  int64_t* sort_n = scal;
-  SortBufs sb{U32(L.counts), U32(L.part)};
+  int64_t* sort_n = (int64_t*)(ws + L.scal);
 
   LGS_CHECK_CUDA(cudaMemsetAsync(ranges, 0, sizeof(uint32_t) * 2 * (size_t)n_cams * tiles, s));
   if (m == 0) {
     LGS_CHECK_CUDA(cudaMemsetAsync(n_instances_dev, 0, sizeof(int64_t), s));
     return LGS_OK;
   }
+  LGS_CHECK_CUDA(cudaMemsetAsync(ws + L.zero_begin, 0, L.zero_end - L.zero_begin, s));
   // 1. (camera, Gaussian) items by depth, then stably by camera
   uint32_t *dk0 = U32(L.dk0), *dk1 = U32(L.dk1), *dv0 = U32(L.dv0), *dv1 = U32(L.dv1);
   depth_keys_kernel<<<grid_for(m), 256, 0, s>>>((const float4*)proj, (const ushort4*)rect, m,
                                                 dk0, dv0);
-  if (radix_sort(dk0, dv0, dk1, dv1, nullptr, m, 32, sb, s)) {
+  if (onesweep_sort(dk0, dv0, dk1, dv1, nullptr, m, 32, 0, L, ws, s)) {
     std::swap(dk0, dk1);
     std::swap(dv0, dv1);
   }
   if (n_cams > 1) {
     camera_keys_kernel<<<grid_for(m), 256, 0, s>>>(dv0, m, (uint32_t)n, dk0);
-    int cbits = 32 - __builtin_clz((unsigned)(n_cams - 1));
-    if (radix_sort(dk0, dv0, dk1, dv1, nullptr, m, cbits, sb, s)) {
+    const int cbits = 32 - __builtin_clz((unsigned)(n_cams - 1));
+    if (onesweep_sort(dk0, dv0, dk1, dv1, nullptr, m, cbits, 4, L, ws, s)) {
       std::swap(dk0, dk1);
       std::swap(dv0, dv1);
     }
   }
   const uint32_t* order = dv0;
-  // 2. instance counts and offsets
-  uint32_t* cnt = U32(L.cnt);
+  // 2. instance offsets of the depth-ordered items, K and the sort count
   uint64_t* offs = (uint64_t*)(ws + L.offs);
-  tile_count_kernel<<<grid_for(m), 256, 0, s>>>(order, (const ushort4*)rect, m, cnt);
-  exclusive_scan<uint32_t, uint64_t>(cnt, offs, m, (uint64_t*)(ws + L.part64), offs + m, s);
-  finish_count_kernel<<<1, 1, 0, s>>>(offs + m, capacity, n_instances_dev, sort_n);
+  count_scan_kernel<<<(unsigned)std::max<int64_t>(1, tiles_of(m)), 256, 0, s>>>(
+      order, (const ushort4*)rect, m, offs, capacity, n_instances_dev, sort_n,
+      (uint64_t*)(ws + L.scan_status), U32(L.counters) + kPassesMax);
   LGS_CHECK_LAUNCH();
   if (capacity == 0) return LGS_OK;
   // 3. emit (tile, Gaussian) pairs and sort them stably by tile
   int tbits = 1;
   while (tbits < 32 && ((uint64_t)1 << tbits) < (uint64_t)n_cams * tiles) tbits++;
-  bool odd = sort_passes(tbits) & 1;
+  const bool odd = ((tbits + 7) / 8) & 1;
   uint32_t *tk0 = U32(L.tk0), *tk1 = U32(L.tk1);
-  uint32_t* tv0 = odd ? U32(L.tv) : ids;   // the last pass lands in ids
+  uint32_t* tv0 = odd ? U32(L.tv) : ids;  // the last pass lands in ids
   uint32_t* tv1 = odd ? ids : U32(L.tv);
-  emit_kernel<<<grid_for(m), 256, 0, s>>>(order, (const ushort4*)rect, offs, m, (uint32_t)n,
-                                          tiles_x, tiles, sort_n, tk0, tv0);
-  bool flipped = radix_sort(tk0, tv0, tk1, tv1, sort_n, capacity, tbits, sb, s);
+  emit_kernel<<<(unsigned)std::max<int64_t>(1, (capacity + kEmitSlots - 1) / kEmitSlots),
+                kEmitThreads, 0, s>>>(order, (const ushort4*)rect, offs, m, (uint32_t)n, tiles_x,
+                                      tiles, (uint32_t)n_cams * tiles, sort_n, tk0, tv0);
+  const bool flipped = onesweep_sort(tk0, tv0, tk1, tv1, sort_n, capacity, tbits, 5, L, ws, s);
   const uint32_t* tkey = flipped ? tk1 : tk0;
   // 4. per-tile ranges and (optionally) the 64-bit keys
-  ranges_kernel<<<grid_for(capacity), 256, 0, s>>>(tkey, sort_n, (uint2*)ranges);
+  ranges_kernel<<<grid_for(capacity), 256, 0, s>>>(tkey, sort_n, (uint32_t)n_cams * tiles,
+                                                    (uint2*)ranges);
   if (keys_opt)
     keys_kernel<<<grid_for(capacity), 256, 0, s>>>(tkey, ids, (const float4*)proj, sort_n,
                                                    (uint32_t)n, tiles, keys_opt);
   LGS_CHECK_LAUNCH();
   return LGS_OK;
 }
+
+namespace lgs {
+unsigned sort_error_word() {
+  unsigned v = 0, zero = 0;
+  if (cudaMemcpyFromSymbol(&v, g_sort_error, sizeof(v)) != cudaSuccess) return 0;
+  cudaMemcpyToSymbol(g_sort_error, &zero, sizeof(zero));
+  return v;
+}
+}  // namespace lgs

@@ -23,5 +23,7 @@ lgs_status launch_decode_fused(const lgs_ae_weights* w, const float* z, int64_t 
                                void* pack, cudaStream_t s);
 // Reads and clears the fused kernel's timeout word.
 unsigned fused_error_word();
+// Reads and clears the binning sort's look-back timeout word.
+unsigned sort_error_word();
 
 }  // namespace lgs

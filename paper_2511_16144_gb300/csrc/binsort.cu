@@ -66,6 +66,72 @@ __device__ __forceinline__ void st_relaxed64(uint64_t* p, uint64_t v) {
   asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
 
+// Sum of the published counts of tiles j, j-1, ... back to (and including)
+// the nearest inclusive prefix; `col` points at tile 0's entry and
+// consecutive tiles are `stride` words apart.  Loads 16 predecessors per
+// round so a long chain of aggregates costs few dependent round trips.
+constexpr int kLookAhead = 16;
+__device__ __forceinline__ uint32_t look_back(const uint32_t* col, int64_t stride, int64_t j) {
+  uint32_t prefix = 0, spins = 0;
+  while (j >= 0) {
+    uint32_t v[kLookAhead];
+#pragma unroll
+    for (int q = 0; q < kLookAhead; q++)
+      v[q] = (j - q >= 0) ? ld_relaxed(col + (j - q) * stride) : kFlagInc;
+    int q = 0;
+    bool done = false;
+#pragma unroll
+    for (int k = 0; k < kLookAhead; k++) {
+      if (q == k) {
+        const uint32_t flag = v[k] & ~kValMask;
+        if (flag != 0) {
+          prefix += v[k] & kValMask;
+          if (flag == kFlagInc) done = true;
+          else q++;
+        }
+      }
+    }
+    if (done) break;
+    j -= q;
+    if (q < kLookAhead && ++spins > kSpinLimit) {  // stalled on an unpublished tile
+      atomicOr(&g_sort_error, 1u);
+      break;
+    }
+  }
+  return prefix;
+}
+
+__device__ __forceinline__ uint64_t look_back64(const uint64_t* col, int64_t j) {
+  uint64_t prefix = 0;
+  uint32_t spins = 0;
+  while (j >= 0) {
+    uint64_t v[kLookAhead];
+#pragma unroll
+    for (int q = 0; q < kLookAhead; q++)
+      v[q] = (j - q >= 0) ? ld_relaxed64(col + (j - q)) : kFlag64Inc;
+    int q = 0;
+    bool done = false;
+#pragma unroll
+    for (int k = 0; k < kLookAhead; k++) {
+      if (q == k) {
+        const uint64_t flag = v[k] & ~kVal64Mask;
+        if (flag != 0) {
+          prefix += v[k] & kVal64Mask;
+          if (flag == kFlag64Inc) done = true;
+          else q++;
+        }
+      }
+    }
+    if (done) break;
+    j -= q;
+    if (q < kLookAhead && ++spins > kSpinLimit) {
+      atomicOr(&g_sort_error, 2u);
+      break;
+    }
+  }
+  return prefix;
+}
+
 template <typename T>
 __device__ T block_exclusive_scan(T v, T* warp_tot, T& total) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -180,28 +246,13 @@ onesweep_kernel(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ v
   dstart[d] = block_exclusive_scan<uint32_t>(tot, wt, all);
   const uint32_t gbase = block_exclusive_scan<uint32_t>(ghist[d], wt, all);
   // decoupled look-back over the earlier tiles' published counts of digit d
-  uint32_t prefix = 0;
   uint32_t* st = status + (size_t)tile * kRadix;
+  uint32_t prefix = 0;
   if (tile == 0) {
     st_relaxed(st + d, tot | kFlagInc);
   } else {
     st_relaxed(st + d, tot | kFlagAgg);
-    int64_t j = (int64_t)tile - 1;
-    uint32_t spins = 0;
-    while (j >= 0) {
-      const uint32_t v = ld_relaxed(status + (size_t)j * kRadix + d);
-      const uint32_t flag = v & ~kValMask;
-      if (flag == 0) {
-        if (++spins > kSpinLimit) {
-          atomicOr(&g_sort_error, 1u);
-          break;
-        }
-        continue;
-      }
-      prefix += v & kValMask;
-      if (flag == kFlagInc) break;
-      j--;
-    }
+    prefix = look_back(status + d, kRadix, (int64_t)tile - 1);
     st_relaxed(st + d, (prefix + tot) | kFlagInc);
   }
   goff[d] = gbase + prefix;
@@ -284,22 +335,7 @@ count_scan_kernel(const uint32_t* __restrict__ order, const ushort4* __restrict_
       st_relaxed64(status, total | kFlag64Inc);
     } else {
       st_relaxed64(status + tile, total | kFlag64Agg);
-      int64_t j = (int64_t)tile - 1;
-      uint32_t spins = 0;
-      while (j >= 0) {
-        const uint64_t v = ld_relaxed64(status + j);
-        const uint64_t flag = v & ~kVal64Mask;
-        if (flag == 0) {
-          if (++spins > kSpinLimit) {
-            atomicOr(&g_sort_error, 2u);
-            break;
-          }
-          continue;
-        }
-        prefix += v & kVal64Mask;
-        if (flag == kFlag64Inc) break;
-        j--;
-      }
+      prefix = look_back64(status, (int64_t)tile - 1);
       st_relaxed64(status + tile, (prefix + total) | kFlag64Inc);
     }
     s_prefix = prefix;

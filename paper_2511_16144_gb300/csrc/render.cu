@@ -228,7 +228,8 @@ struct BwdSmem {
 };
 
 template <int FC, typename TC, bool RGB>
-__global__ void __launch_bounds__(kThreads) render_bwd_kernel(RasterArgs A, int chunk_base) {
+__global__ void __launch_bounds__(kThreads, FC <= 16 ? 3 : 2)
+render_bwd_kernel(RasterArgs A, int chunk_base) {
   using L = BwdSmem<FC, RGB>;
   constexpr int NCH = L::NCH, NV = L::NV, B = kBwdBatch;
   extern __shared__ float4 smem4[];
@@ -306,9 +307,12 @@ __global__ void __launch_bounds__(kThreads) render_bwd_kernel(RasterArgs A, int 
     }
     __syncthreads();
 
-    // phase 1: per pixel, back to front through the batch
+    // phase 1: per pixel, back to front through the batch (a warp whose
+    // pixels all end before this batch has nothing to add to it)
     float* wrow = s_w + warp * B * L::WROW;
     float* prow = s_p + warp * B * L::WROW;
+    const bool warp_active = __any_sync(0xffffffffu, (uint32_t)lo < my_last);
+    if (warp_active)
     for (int j = nb - 1; j >= 0; j--) {
       float w = 0.f, dp = 0.f;
       if ((uint32_t)(lo + j) < my_last) {
@@ -345,7 +349,7 @@ __global__ void __launch_bounds__(kThreads) render_bwd_kernel(RasterArgs A, int 
     __syncwarp();
 
     // phase 2: lane (j, h) reduces instance j over the warp's tile row h
-    {
+    if (warp_active) {
       const int j = lane & 15, h = lane >> 4;
       const float* wr = wrow + j * L::WROW + 16 * h;
       const float* pr = prow + j * L::WROW + 16 * h;

@@ -139,8 +139,12 @@ __device__ unsigned g_fused_error;
 
 constexpr int kEpiWarps = 16;
 constexpr int kFusedThreads = (kEpiWarps + 2) * 32;   // + producer warp + MMA warp
+// barriers: full[kStages], empty[kStages], accbar, opbar, then the TMEM slot
+constexpr uint32_t kBarBytes = (2 * kStages + 2) * 8 + 4;
 constexpr uint32_t SM_BIAS = SM_BAR + 128;             // b4 | b5 | b6 | b7 (960 floats)
 constexpr uint32_t SM_ALL = SM_BIAS + 960 * 4;
+static_assert(kBarBytes <= SM_BIAS - SM_BAR, "barrier block overlaps the biases");
+static_assert(SM_ALL <= 232448, "shared-memory map exceeds 227 KB");
 
 __global__ void __launch_bounds__(kFusedThreads, 1)
 decode_fused_kernel(const __grid_constant__ FusedArgs a) {

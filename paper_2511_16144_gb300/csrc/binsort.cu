@@ -220,11 +220,15 @@ onesweep_kernel(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ v
   uint32_t key[kOsItems], val[kOsItems], rank[kOsItems];
   const uint32_t lt = lanemask_lt();
 #pragma unroll
+  for (int r = 0; r < kOsItems; r++) {  // all loads in flight before any ranking
+    const int64_t idx = base + r * 32 + lane;
+    key[r] = idx < n ? kin[idx] : 0u;
+    val[r] = idx < n ? vin[idx] : 0u;
+  }
+#pragma unroll
   for (int r = 0; r < kOsItems; r++) {
     const int64_t idx = base + r * 32 + lane;
     const bool valid = idx < n;
-    key[r] = valid ? kin[idx] : 0u;
-    val[r] = valid ? vin[idx] : 0u;
     const uint32_t d = valid ? (key[r] >> shift) & mask : (uint32_t)(kRadix + lane);
     const uint32_t peers = __match_any_sync(0xffffffffu, d);
     const uint32_t prior = valid ? wcnt[warp][d] : 0u;
@@ -302,10 +306,13 @@ __global__ void camera_keys_kernel(const uint32_t* __restrict__ vals, int64_t m,
 // Exclusive prefix of the covered-tile counts of the depth-ordered items
 // (single pass, decoupled look-back per 4096-item tile); the last tile also
 // writes K, and the number to sort (K, or 0 when K exceeds capacity).
+constexpr int kEmitSlots = 2048;  // instance slots per emission block
+
 __global__ void __launch_bounds__(256)
 count_scan_kernel(const uint32_t* __restrict__ order, const ushort4* __restrict__ rect, int64_t m,
                   uint64_t* __restrict__ offs, int64_t capacity, int64_t* __restrict__ k_out,
-                  int64_t* __restrict__ sort_n, uint64_t* status, uint32_t* counter) {
+                  int64_t* __restrict__ sort_n, uint64_t* status, uint32_t* counter,
+                  uint32_t* __restrict__ bstart) {
   __shared__ uint64_t wt[32];
   __shared__ uint64_t s_prefix;
   __shared__ uint32_t s_tile;
@@ -348,24 +355,31 @@ count_scan_kernel(const uint32_t* __restrict__ order, const ushort4* __restrict_
   }
   __syncthreads();
   uint64_t run = s_prefix + ex;
+  const uint64_t nblk = ((uint64_t)capacity + kEmitSlots - 1) / kEmitSlots;
 #pragma unroll
   for (int k = 0; k < kOsItems; k++) {
     const int64_t i = i0 + k;
-    if (i < m) offs[i] = run;
+    if (i < m) {
+      offs[i] = run;
+      // the item holding the first slot of every emission block in its range
+      for (uint64_t b = (run + kEmitSlots - 1) / kEmitSlots; b < nblk && b * kEmitSlots < run + c[k];
+           b++)
+        bstart[b] = (uint32_t)i;
+    }
     run += c[k];
   }
 }
 
 // One thread per instance slot: slot o belongs to the depth-ordered item i
-// with offs[i] <= o < offs[i+1].  The block brackets its 2048 consecutive
-// slots by two binary searches; when they span at most 2049 items (always,
-// unless invisible items of one camera sit between) the block stages that
-// slice of offs in shared memory and every thread searches it, otherwise
-// threads search the bracket in global memory.  Writes are coalesced and the
-// work is balanced however many tiles a Gaussian covers.
+// with offs[i] <= o < offs[i+1].  The offset scan recorded the item holding
+// each block's first slot, so a block knows its bracket of items at once;
+// when the bracket spans at most 2049 items (always, unless invisible items
+// of one camera sit between) it is staged in shared memory and every thread
+// binary-searches it, otherwise threads search the bracket in global memory.
+// Writes are coalesced and the work is balanced however many tiles a
+// Gaussian covers.
 constexpr int kEmitThreads = 256;
-constexpr int kEmitPer = 8;
-constexpr int kEmitSlots = kEmitThreads * kEmitPer;
+constexpr int kEmitPer = kEmitSlots / kEmitThreads;
 
 // Last index i in [lo, hi) with a[i] <= o, given a[lo] <= o < a[hi].
 template <typename A>
@@ -380,25 +394,23 @@ __device__ __forceinline__ int64_t last_le(const A& a, int64_t lo, int64_t hi, u
 
 __global__ void __launch_bounds__(kEmitThreads)
 emit_kernel(const uint32_t* __restrict__ order, const ushort4* __restrict__ rect,
-            const uint64_t* __restrict__ offs, int64_t m, uint32_t n, int tiles_x, uint32_t tiles,
-            uint32_t n_tiles_all, const int64_t* __restrict__ sort_n,
-            uint32_t* __restrict__ tkey, uint32_t* __restrict__ tval) {
+            const uint64_t* __restrict__ offs, const uint32_t* __restrict__ bstart, int64_t m,
+            uint32_t n, int tiles_x, uint32_t tiles, uint32_t n_tiles_all,
+            const int64_t* __restrict__ sort_n, uint32_t* __restrict__ tkey,
+            uint32_t* __restrict__ tval) {
   __shared__ uint64_t s_off[kEmitSlots + 2];
-  __shared__ int64_t s_lo, s_hi;
   const int64_t K = *sort_n;
   const int64_t o0 = (int64_t)blockIdx.x * kEmitSlots;
   if (o0 >= K) return;
   const int64_t o1 = o0 + kEmitSlots < K ? o0 + kEmitSlots : K;
-  auto g = [&](int64_t i) { return offs[i]; };
-  if (threadIdx.x == 0) s_lo = last_le(g, 0, m, (uint64_t)o0);
-  if (threadIdx.x == 32) s_hi = last_le(g, 0, m, (uint64_t)(o1 - 1));
-  __syncthreads();
-  const int64_t lo = s_lo, hi = s_hi;
-  const int64_t span = hi - lo + 1;  // items holding slots [o0, o1)
+  const int64_t lo = bstart[blockIdx.x];
+  const int64_t hi = o1 < K ? (int64_t)bstart[blockIdx.x + 1] : m - 1;  // holds slot o1 - 1
+  const int64_t span = hi - lo + 1;
   const bool staged = span <= kEmitSlots + 1;
   if (staged)
     for (int64_t j = threadIdx.x; j <= span; j += kEmitThreads) s_off[j] = offs[lo + j];
   __syncthreads();
+  auto g = [&](int64_t i) { return offs[i]; };
   auto sm = [&](int64_t i) { return s_off[i]; };
   for (int r = 0; r < kEmitPer; r++) {
     const int64_t o = o0 + (int64_t)r * kEmitThreads + threadIdx.x;
@@ -450,7 +462,7 @@ static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 static int64_t tiles_of(int64_t n) { return (n + kOsTile - 1) / kOsTile; }
 
 struct Layout {
-  size_t dk0, dk1, dv0, dv1, offs, tk0, tk1, tv;
+  size_t dk0, dk1, dv0, dv1, offs, bstart, tk0, tk1, tv;
   size_t zero_begin, ghist, counters, status[kPassesMax], scan_status, scal, zero_end;
   size_t total;
 };
@@ -462,6 +474,7 @@ static Layout layout(int64_t n, int n_cams, int64_t capacity) {
   auto take = [&](size_t bytes) { size_t at = o; o += align256(bytes); return at; };
   L.dk0 = take(4 * m); L.dk1 = take(4 * m); L.dv0 = take(4 * m); L.dv1 = take(4 * m);
   L.offs = take(8 * (m + 1));
+  L.bstart = take(4 * ((capacity + kEmitSlots - 1) / kEmitSlots + 1));
   L.tk0 = take(4 * capacity); L.tk1 = take(4 * capacity); L.tv = take(4 * capacity);
   L.zero_begin = o;
   L.ghist = take(4 * kPassesMax * kRadix);
@@ -574,7 +587,7 @@ extern "C" lgs_status gs_bin_sort(const float* proj, const uint16_t* rect, int64
   uint64_t* offs = (uint64_t*)(ws + L.offs);
   count_scan_kernel<<<(unsigned)std::max<int64_t>(1, tiles_of(m)), 256, 0, s>>>(
       order, (const ushort4*)rect, m, offs, capacity, n_instances_dev, sort_n,
-      (uint64_t*)(ws + L.scan_status), U32(L.counters) + kPassesMax);
+      (uint64_t*)(ws + L.scan_status), U32(L.counters) + kPassesMax, U32(L.bstart));
   LGS_CHECK_LAUNCH();
   if (capacity == 0) return LGS_OK;
   // 3. emit (tile, Gaussian) pairs and sort them stably by tile
@@ -585,8 +598,9 @@ extern "C" lgs_status gs_bin_sort(const float* proj, const uint16_t* rect, int64
   uint32_t* tv0 = odd ? U32(L.tv) : ids;  // the last pass lands in ids
   uint32_t* tv1 = odd ? ids : U32(L.tv);
   emit_kernel<<<(unsigned)std::max<int64_t>(1, (capacity + kEmitSlots - 1) / kEmitSlots),
-                kEmitThreads, 0, s>>>(order, (const ushort4*)rect, offs, m, (uint32_t)n, tiles_x,
-                                      tiles, (uint32_t)n_cams * tiles, sort_n, tk0, tv0);
+                kEmitThreads, 0, s>>>(order, (const ushort4*)rect, offs, U32(L.bstart), m,
+                                      (uint32_t)n, tiles_x, tiles, (uint32_t)n_cams * tiles,
+                                      sort_n, tk0, tv0);
   const bool flipped = onesweep_sort(tk0, tv0, tk1, tv1, sort_n, capacity, tbits, 5, L, ws, s);
   const uint32_t* tkey = flipped ? tk1 : tk0;
   // 4. per-tile ranges and (optionally) the 64-bit keys

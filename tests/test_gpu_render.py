@@ -340,3 +340,56 @@ def test_l1_loss_matches_oracle(lgs, oracle_lib):
         l_ref, g_ref = oracle_lib.l1_loss_grad(pred, t_ref, 0.1)
         assert abs(loss.item() - l_ref) <= 1e-5 * l_ref
         np.testing.assert_allclose(_np(grad), g_ref, rtol=1e-6, atol=0)
+
+
+# ---------------------------------------------------------------- full-size windows
+
+def _crop_parity(fr, scene, cam, cam_index, crop, chan_scene=None):
+    from oracle import render as orender
+    o = orender(chan_scene or scene, cam, crop=crop)
+    x0, y0, w, h = crop
+    out = {k: _np(v[cam_index])[y0:y0 + h, x0:x0 + w] for k, v in fr.out.items() if v is not None}
+    _check_maps(out, o, robust_mask(o))
+    return o
+
+
+def _crop_backward(fr, scene, cams, cam_index, crop, seed, chan_scene=None):
+    from oracle import render as orender, render_backward
+    ref = chan_scene or scene
+    cam = cams[cam_index]
+    o = orender(ref, cam, crop=crop)
+    g = _upstream(o["depth"].shape, scene.feats.shape[1], robust_mask(o, 1e-3), seed)
+    C, H, W = len(cams), cam.height, cam.width
+    full = [np.zeros((C, H, W, 3), np.float32), np.zeros((C, H, W), np.float32),
+            np.zeros((C, H, W, scene.feats.shape[1]), np.float32)]
+    x0, y0, w, h = crop
+    for f, part in zip(full, g):
+        f[cam_index, y0:y0 + h, x0:x0 + w] = part
+    gg = _gpu_grads(fr, full)
+    go = render_backward(ref, cam, *g, crop=crop)
+    for k in ("colors", "feats", "opacity_logits", "means", "log_scales", "quats"):
+        grad_close(gg[k], go[k], name=k)
+
+
+def test_render_window8_full_size(lgs, oracle_lib):
+    """The differentiable mapping window: 8 keyframes of 640x480 over 300k
+    Gaussians in one launch; sampled crops of three cameras forward, and the
+    backward of an upstream gradient on one crop of one camera."""
+    scene, cams = synth.indoor(n_cams=8)
+    fr = _frame(scene, cams)
+    assert fr.k > 8 * 10 ** 6
+    for c, crop in ((0, (300, 220, 40, 40)), (3, (0, 0, 40, 40)), (7, (600, 440, 40, 40))):
+        _crop_parity(fr, scene, cams[c], c, crop)
+    _crop_backward(fr, scene, cams, 5, (280, 200, 48, 48), 11)
+
+
+def test_render_outdoor_full_size(lgs, oracle_lib):
+    """Large outdoor scale: 2M Gaussians in 40x40x8 m, 8 keyframes of
+    1200x680 (a partial bottom tile row), BF16 channels; sampled crops
+    forward (including the partial row) and one crop backward."""
+    scene, cams = synth.outdoor()
+    fr = _frame(scene, cams, chan=torch.bfloat16)
+    ref = bf16_scene(scene)
+    for c, crop in ((0, (584, 324, 32, 32)), (6, (1168, 648, 32, 32))):
+        _crop_parity(fr, scene, cams[c], c, crop, chan_scene=ref)
+    _crop_backward(fr, scene, cams, 2, (600, 300, 32, 32), 12, chan_scene=ref)

@@ -37,8 +37,8 @@ FP32_PEAK_NOTE = "152 SMs x 128 FP32 lanes x 2 FLOP x 2.07 GHz"
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
-    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="lgs", choices=["lgs", "reference"])
     ap.add_argument("--no-plain", action="store_true", help="skip the plain 512-d path")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle cpu_baseline")
@@ -64,24 +64,28 @@ def build_workload(rank):
 
 class Clocks:
     """nvidia-smi sampling of SM clocks and throttle reasons during timing."""
-    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    FIELDS = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
     def __init__(self, index):
         self.index, self.proc, self.lines = index, None, []
+        self.t0 = self.t1 = None
 
     def __enter__(self):
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "100"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            time.sleep(1.0)  # the sampler's own start-up, before the timed region
         except OSError:
             self.proc = None
+        self.t0 = time.time()
         return self
 
     def __exit__(self, *exc):
+        self.t1 = time.time()
         if self.proc is not None:
             self.proc.terminate()
             try:
@@ -94,10 +98,20 @@ class Clocks:
     def summary(self):
         sm, mx, reasons = [], None, set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        rows = []
         for l in self.lines:
             f = [x.strip() for x in l.split(",")]
-            if len(f) < 9:
+            if len(f) < 10:
                 continue
+            try:
+                ts = time.mktime(time.strptime(f[0].split(".")[0], "%Y/%m/%d %H:%M:%S"))
+                ts += float("0." + f[0].split(".")[1]) if "." in f[0] else 0.0
+            except (ValueError, IndexError):
+                ts = None
+            rows.append((ts, f[1:]))
+        # samples taken while the timed steps ran (all of them if none parse)
+        inside = [f for ts, f in rows if ts is not None and self.t0 - 0.05 <= ts <= self.t1 + 0.05]
+        for f in inside or [f for _, f in rows]:
             try:
                 sm.append(float(f[1]))
                 mx = float(f[2])
@@ -109,7 +123,7 @@ class Clocks:
         if not sm:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
-                "samples": len(sm)}
+                "samples": len(sm), "in_timed_window": bool(inside)}
 
 
 def measured_peaks():
@@ -237,7 +251,9 @@ def run_gpu(args, rank, world):
 
     # per-call durations of one eager step (events on the launching stream)
     calls = per_call_times(step16, flush, reps=5)
-    rf = roofline_render_bwd(step16, calls)
+    kern, counts = rooflines(step16, calls)
+    top = max(calls, key=calls.get)
+    rf = dict(kern[top], kernel=top)
 
     # FP32-channel variant and the plain 512-channel path (same geometry)
     extra = {}
@@ -292,7 +308,7 @@ def run_gpu(args, rank, world):
                        "graph": "one CUDA graph per step", "parallelism": "replicas" if world > 1 else "single"},
             "gpu_launches": nodes16 * args.steps if nodes16 > 0 else None,
             "kernels_per_step": nodes16,
-            "roofline": dict(rf, peak_source=kind),
+            "roofline": rf, "rooflines": kern, "work_counts": counts,
             "e2e": e2e,
             "clocks": clocks.summary(),
             "plain_512": plain, "decoded_cosine_error": cos_err, "variants": extra,
@@ -360,26 +376,61 @@ def per_call_times(step, flush, reps=5):
     return out
 
 
-def roofline_render_bwd(step, calls):
-    """Achieved FP32 rate of gs_render_bwd against the FP32 ALU peak.
+# ncu DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) per launch
+# of each call group at this workload, from the capture summarised under
+# profiles/; None once the kernel has changed since the capture.
+TRAFFIC = {"gs_project": 13217024, "gs_bin_sort": 71693568, "gs_render_fwd": 3313152,
+           "l1_losses": 9844992, "ae_decode": 350261248, "gs_render_bwd": 41910528}
 
-    Algorithmic FLOPs per launch (the per-unit figures of the hot-path
-    scope): 10 per evaluated (pixel, instance) pair E and 4(4+d) + 25 per
-    blended pair B, with E = sum over pixels of `last` (instances walked
-    back to front) and B = the number blended, read from the forward."""
-    import torch
+
+def rooflines(step, calls):
+    """Roofline position of every call group of the step.
+
+    Algorithmic work per launch (the per-unit figures of the hot-path scope,
+    times the units one launch processes):
+      gs_project    HBM  44 B per Gaussian read + 40 B per (camera, Gaussian) written
+      gs_bin_sort   HBM  36 B per instance (emit write + one read/write pass of
+                         12-byte records) + 8 B per tile range
+      gs_render_fwd ALU  10 FLOP per evaluated (pixel, instance) pair E +
+                         2 (4 + d) + 4 per blended pair B
+      l1_losses     HBM  48 B per pixel (RGB and depth: prediction, target, gradient)
+      ae_decode     BF16 tensor  2 x 346 112 FLOP per pixel (decoder forward and
+                         gradient to the rendered map)
+      gs_render_bwd ALU  10 FLOP per E + 4 (4 + d) + 25 per B
+    E = sum over pixels of `last` (instances walked), B = instances blended,
+    both read from the forward.  Peaks: measured HBM copy bandwidth and bf16
+    GEMM rate (burst: each call is timed alone), FP32 lanes x clock for ALU."""
+    peaks, kind = measured_peaks()
     E = float(step.out["last"].double().sum().item())
     B = float(step.count_blended().double().sum().item())
-    d = step.D
-    flops = 10.0 * E + (4.0 * (4 + d) + 25.0) * B
-    ms = calls["gs_render_bwd"]
-    achieved = flops / (ms / 1e3) / 1e12
-    peaks, _ = measured_peaks()
-    peak = 152 * 128 * 2 * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12
-    return {"kernel": "gs_render_bwd (raster backward + projection chain rule)", "bound": "alu",
-            "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-            "traffic": None, "flops_per_launch": flops, "E_pairs": E, "B_pairs": B,
-            "ms_per_launch": ms, "peak_note": FP32_PEAK_NOTE}
+    K = float(step.k_dev.item())
+    d, n, c, P = step.D, step.scene.n, len(step.cams), step.pixels
+    tiles = step.bufs.tiles_x * step.bufs.tiles_y * c
+    alu = 152 * 128 * 2 * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12
+    hbm, tc = float(peaks["hbm_gbs"]), float(peaks["bf16_tflops"])
+    work = {
+        "gs_project": ("hbm", 44.0 * n + 40.0 * c * n),
+        "gs_bin_sort": ("hbm", 36.0 * K + 8.0 * tiles),
+        "gs_render_fwd": ("alu", 10.0 * E + (2.0 * (4 + d) + 4.0) * B),
+        "l1_losses": ("hbm", 48.0 * P),
+        "ae_decode": ("tensor", 2.0 * 346112.0 * P),
+        "gs_render_bwd": ("alu", 10.0 * E + (4.0 * (4 + d) + 25.0) * B),
+    }
+    out = {}
+    for name, ms in calls.items():
+        bound, units = work[name]
+        if bound == "hbm":
+            achieved, peak, unit = units / (ms / 1e3) / 1e9, hbm, "GB/s"
+        else:
+            achieved = units / (ms / 1e3) / 1e12
+            peak, unit = (tc, "TFLOP/s") if bound == "tensor" else (alu, "TFLOP/s")
+        out[name] = {"bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
+                     "frac": achieved / peak, "traffic": TRAFFIC.get(name),
+                     "work_per_launch": units, "ms_per_launch": ms,
+                     "peak_source": ("fp32 lanes: " + FP32_PEAK_NOTE) if bound == "alu"
+                     else kind + (" bf16 burst" if bound == "tensor" else " copy")}
+    counts = {"E_pairs": E, "B_pairs": B, "instances": K}
+    return out, counts
 
 
 def measure_e2e(steps, graphs, k, warm):
@@ -445,40 +496,70 @@ def oracle_prepare(W):
     return sc, dec
 
 
-def oracle_step(W, side, prep):
-    """One bounded sample of the workload on the FP64 oracle: a side x side
-    centre crop rendered (RGB, depth, 16-d feature), decoded against F_gt
-    with its gradient, and back-propagated to every Gaussian parameter."""
+def centre_crop(cam, px):
+    """A centre crop of about px pixels with the frame's aspect ratio."""
+    w = max(8, min(cam.width, int(math.sqrt(px * cam.width / cam.height))))
+    h = max(8, min(cam.height, int(px // w)))
+    return (cam.width // 2 - w // 2, cam.height // 2 - h // 2, w, h)
+
+
+def crop_f_gt(W, crop):
+    """F_gt of a crop: the GPU arm's target map when there is one, else the
+    semantic field rendered by the oracle itself (512 channels)."""
+    import oracle
+    x0, y0, w, h = crop
+    if W.get("f_gt") is not None:
+        return W["f_gt"][y0:y0 + h, x0:x0 + w].reshape(-1, 512)
+    cache = W.setdefault("f_gt_crops", {})
+    if crop not in cache:
+        o = oracle.render(W["scene"].with_feats(W["g512"]), W["cam"], crop=crop)
+        cache[crop] = o["feat"].reshape(-1, 512)
+    return cache[crop]
+
+
+def oracle_step(W, crop, prep):
+    """One bounded sample of the workload on the FP64 oracle: a crop rendered
+    (RGB, depth, 16-d feature), decoded against F_gt with its gradient, and
+    back-propagated to every Gaussian parameter.  Returns (pixels, seconds)."""
     import oracle
     from oracle import ae
     sc, dec = prep
     cam = W["cam"]
-    x0, y0 = cam.width // 2 - side // 2, cam.height // 2 - side // 2
-    crop = (x0, y0, side, side)
+    x0, y0, w, h = crop
+    f_gt = crop_f_gt(W, crop)
+    t0 = time.time()
     o = oracle.render(sc, cam, crop=crop)
-    _, g_rgb = oracle.l1_loss_grad(o["rgb"], W["rgb_t"][y0:y0 + side, x0:x0 + side])
-    _, g_dep = oracle.l1_loss_grad(o["depth"], W["dep_t"][y0:y0 + side, x0:x0 + side], 0.1)
-    f_gt = W["f_gt"][y0:y0 + side, x0:x0 + side].reshape(-1, 512)
+    _, g_rgb = oracle.l1_loss_grad(o["rgb"], W["rgb_t"][y0:y0 + h, x0:x0 + w])
+    _, g_dep = oracle.l1_loss_grad(o["depth"], W["dep_t"][y0:y0 + h, x0:x0 + w], 0.1)
     _, dz = ae.distill(dec, o["feat"].reshape(-1, 16), f_gt)
-    oracle.render_backward(sc, cam, g_rgb, g_dep, dz.reshape(side, side, 16), crop=crop)
-    return side * side
+    oracle.render_backward(sc, cam, g_rgb, g_dep, dz.reshape(h, w, 16), crop=crop)
+    return w * h, time.time() - t0
+
+
+def size_crop(W, prep, budget_s):
+    """Grows a centre crop (x4 pixels a time) until one oracle step takes an
+    eighth of budget_s, then scales it to about budget_s (at most the whole
+    frame)."""
+    cam = W["cam"]
+    px = 256
+    while True:
+        n, dt = oracle_step(W, centre_crop(cam, px), prep)
+        if dt >= budget_s / 8 or n >= cam.width * cam.height:
+            break
+        px *= 4
+    return centre_crop(cam, min(cam.width * cam.height, n * budget_s / max(dt, 1e-3)))
 
 
 def cpu_baseline(W, budget_s=15.0):
-    """Times the oracle on centre crops sized to about budget_s seconds."""
+    """Times the oracle on one crop sized to about budget_s seconds."""
     import oracle
     oracle.build()
     prep = oracle_prepare(W)
-    t0 = time.time()
-    oracle_step(W, 8, prep)
-    t_small = max(time.time() - t0, 1e-3)
-    side = int(max(8, min(128, 8 * math.sqrt(budget_s / t_small))))
-    t0 = time.time()
-    px = oracle_step(W, side, prep)
-    dt = time.time() - t0
+    crop = size_crop(W, prep, budget_s)
+    px, dt = oracle_step(W, crop, prep)
     return {"value": px / 1e6 / dt, "unit": "Mpix/s", "cores": oracle.num_threads(),
             "kind": "oracle", "seconds": dt,
-            "sample": f"{side}x{side} centre crop of the 640x480 frame, 300k Gaussians: "
+            "sample": f"{crop[2]}x{crop[3]} centre crop of the 640x480 frame, 300k Gaussians: "
                       "FP64 brute-force render + decoder L1 + analytic backward"}
 
 
@@ -488,45 +569,28 @@ def run_reference(args, rank, world):
     import oracle
     oracle.build()
     W = build_workload(0)
+    W["f_gt"] = None  # rendered by the oracle per crop, outside the timed steps
     prep = oracle_prepare(W)
-    W["f_gt"] = reference_f_gt(W, 160)
-    t0 = time.time()
-    oracle_step(W, 8, prep)
-    t_small = max(time.time() - t0, 1e-3)
-    per_step = 150.0 / max(args.steps + args.warmup, 1)
-    side = int(max(8, min(160, 8 * math.sqrt(per_step / t_small))))
+    crop = size_crop(W, prep, 150.0 / max(args.steps + args.warmup, 1))
     for _ in range(args.warmup):
-        oracle_step(W, side, prep)
+        oracle_step(W, crop, prep)
     ts = []
     for _ in range(args.steps):
-        t0 = time.time()
-        px = oracle_step(W, side, prep)
-        ts.append(time.time() - t0)
+        px, dt = oracle_step(W, crop, prep)
+        ts.append(dt)
     ms = 1e3 * float(np.mean(ts))
     value = px / 1e6 / (ms / 1e3)
+    sample = f"{crop[2]}x{crop[3]} centre crop of the 640x480 frame per step, FP64 brute force"
     line = {"metric": METRIC, "value": value, "unit": "Mpix/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "impl": "reference",
-            "config": {"workload": WORKLOAD, "gaussians": W["scene"].n, "sample": f"{side}x{side} centre crop"},
+            "config": {"workload": WORKLOAD, "gaussians": W["scene"].n, "sample": sample},
             "cpu_baseline": {"value": value, "unit": "Mpix/s", "cores": oracle.num_threads(),
-                             "kind": "oracle",
-                             "sample": f"{side}x{side} centre crop per step, FP64 brute force"},
+                             "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": "Mpix/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
-
-
-def reference_f_gt(W, side):
-    """F_gt of the centre crop for the oracle arm: the semantic field rendered
-    by the oracle itself (512 channels), in a full-frame array."""
-    import oracle
-    cam = W["cam"]
-    x0, y0 = cam.width // 2 - side // 2, cam.height // 2 - side // 2
-    o = oracle.render(W["scene"].with_feats(W["g512"]), cam, crop=(x0, y0, side, side))
-    full = np.zeros((cam.height, cam.width, 512), np.float32)
-    full[y0:y0 + side, x0:x0 + side] = o["feat"]
-    return full
 
 
 def main():

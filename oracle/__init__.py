@@ -12,6 +12,10 @@ Contents
   the analytic backward, and the stable-sort binning definition.  The paper
   (LEGO-SLAM, Sec. III-B.1) defers the rasteriser to "the standard 3DGS
   pipeline"; the C file's header lists the textbook definition it writes out.
+* ``prune_oracle.c`` (same library): language-guided pruning (Sec. III-C,
+  Eq. 4) with the geometric criteria, by brute-force neighbour search; its
+  mask decisions are taken in FP32 with a fixed operation order (they turn
+  float comparisons into bits), everything else here is float64.
 * ``ae.py``: the scene-adaptive autoencoder (Sec. III-B.3 Eq. 2, Sec. III-B.4
   Eq. 3, Sec. IV-A.2 pretraining) in numpy float64.
 * ``losses``: the L1 terms of Eq. 1.
@@ -30,6 +34,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "lgs_oracle.c")
+_SRCS = (_SRC, os.path.join(_HERE, "prune_oracle.c"))
 _SO = os.path.join(_HERE, "liblgs_oracle.so")
 _lib = None
 
@@ -37,12 +42,12 @@ _lib = None
 def build(force: bool = False) -> str:
     """Compile the C oracle (gcc, -O2, OpenMP).  Idempotent."""
     if (not force and os.path.exists(_SO)
-            and os.path.getmtime(_SO) >= os.path.getmtime(_SRC)):
+            and all(os.path.getmtime(_SO) >= os.path.getmtime(f) for f in _SRCS)):
         return _SO
     fd, tmp = tempfile.mkstemp(suffix=".so", dir=_HERE)
     os.close(fd)
-    subprocess.check_call(["gcc", "-O2", "-std=c11", "-fopenmp", "-fPIC", "-shared",
-                           "-o", tmp, _SRC, "-lm"])
+    subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fopenmp", "-fPIC",
+                           "-shared", "-o", tmp, *_SRCS, "-lm"])
     os.replace(tmp, _SO)
     return _SO
 
@@ -65,6 +70,9 @@ def _load():
     lib.lgso_bin_count.restype = I64
     lib.lgso_bin_sort.argtypes = [I64, I32, I32, I32, P, P, P, P, P]
     lib.lgso_num_threads.restype = I32
+    F32 = ctypes.c_float
+    lib.lgso_prune.argtypes = [I64, I32, P, P, P, P, I32, F32, F32, F32, F32, P]
+    lib.lgso_prune_sample.argtypes = [I64, I32, P, P, P, P, I32, F32, F32, F32, F32, P, I64, P]
     _lib = lib
     return lib
 
@@ -207,3 +215,42 @@ def l1_loss_grad(pred, target, weight=1.0):
     diff = p - t
     loss = weight * np.abs(diff).mean() if diff.size else 0.0
     return loss, weight * np.sign(diff) / max(diff.size, 1)
+
+
+def prune_thresholds(min_opacity, max_scale):
+    """The geometric thresholds as the float comparisons take them:
+    logit(min_opacity) (-inf when min_opacity <= 0) and log(max_scale) (+inf
+    when max_scale is not positive and finite), each rounded to float once."""
+    import math
+    lo = -math.inf if min_opacity <= 0 else math.log(min_opacity / (1.0 - min_opacity))
+    hi = math.inf if not (0 < max_scale < math.inf) else math.log(max_scale)
+    return float(np.float32(lo)), float(np.float32(hi))
+
+
+def _f32(a):
+    return np.ascontiguousarray(np.asarray(a, dtype=np.float32))
+
+
+def prune(means, logits, log_scales, feats, k=8, tau_dist=0.05, tau_sim=0.9,
+          min_opacity=0.005, max_scale=float("inf"), idx=None):
+    """Language-guided pruning mask (Sec. III-C, Eq. 4) unioned with the
+    geometric criteria: uint8 per Gaussian, bit 0 geometric, bit 1 redundant
+    (0 keeps the Gaussian).  With ``idx`` only those Gaussians' entries are
+    decided (each from scratch) and returned in that order."""
+    lib = _load()
+    p, lg, ls, f = _f32(means), _f32(logits), _f32(log_scales), _f32(feats)
+    n, d = f.shape
+    tl, ts = prune_thresholds(min_opacity, max_scale)
+    if idx is None:
+        out = np.zeros(n, np.uint8)
+        rc = lib.lgso_prune(n, d, _ptr(p), _ptr(lg), _ptr(ls), _ptr(f), int(k), float(tau_dist),
+                            float(tau_sim), tl, ts, _ptr(out))
+    else:
+        ix = np.ascontiguousarray(np.asarray(idx, np.int64))
+        out = np.zeros(ix.shape[0], np.uint8)
+        rc = lib.lgso_prune_sample(n, d, _ptr(p), _ptr(lg), _ptr(ls), _ptr(f), int(k),
+                                   float(tau_dist), float(tau_sim), tl, ts, _ptr(ix),
+                                   ix.shape[0], _ptr(out))
+    if rc != 0:
+        raise ValueError("lgso_prune: bad arguments")
+    return out

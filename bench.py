@@ -286,6 +286,8 @@ def run_gpu(args, rank, world):
     # end to end through the C ABI with host buffers: per step the keyframe's
     # targets (RGB, depth, F_gt) go host -> device from pinned memory and the
     # loss comes back
+    prune = measure_prune(s16_bf, flush)
+
     rgb_b, dep_b, fgt_b = rgb_t.clone(), dep_t.clone(), f_gt.clone()
     step16b = MappingStep(s16_bf, cams, rgb_b, dep_b, fgt_b, model=model,
                           capacity=step16.bufs.capacity)
@@ -312,6 +314,7 @@ def run_gpu(args, rank, world):
             "e2e": e2e,
             "clocks": clocks.summary(),
             "plain_512": plain, "decoded_cosine_error": cos_err, "variants": extra,
+            "prune": prune,
             "per_call_ms": calls,
             "ae_pretrain": {"steps": args.ae_steps, "loss_first": ae_losses[0],
                             "loss_last": ae_losses[-1], "seconds": ae_train_s},
@@ -431,6 +434,80 @@ def rooflines(step, calls):
                      else kind + (" bf16 burst" if bound == "tensor" else " copy")}
     counts = {"E_pairs": E, "B_pairs": B, "instances": K}
     return out, counts
+
+
+PRUNE_PARAMS = dict(k=8, tau_dist=0.05, tau_sim=0.9, min_opacity=0.005, max_scale=0.5)
+
+
+def measure_prune(scene, flush, reps=20):
+    """Language-guided pruning (Sec. III-C, Eq. 4 + geometric criteria) over
+    the whole map with its 16-d BF16 features, and the compaction of every
+    parameter array that follows; each captured in a CUDA graph and timed
+    between CUDA events with L2 flushed before every replay.  Algorithmic
+    bytes of the mask: one read of the parameters the rule looks at (means,
+    logit, log-scales, 16 BF16 features = 60 B) + 1 mask byte per Gaussian."""
+    import ctypes
+
+    import torch
+    from paper_2511_16144_gb300 import lgs, synth
+    L = lgs.load()
+    n = scene.n
+    dev = scene.means.device
+    params = lgs.prune_params(synth.ROOM_LO, synth.ROOM_HI, **PRUNE_PARAMS)
+    mask = torch.empty(n, dtype=torch.uint8, device=dev)
+    cnt = torch.empty(1, dtype=torch.int64, device=dev)
+    ws = torch.empty(int(L.gs_prune_workspace(n)), dtype=torch.uint8, device=dev)
+    arrays = [scene.means, scene.quats, scene.log_scales, scene.opacity_logits, scene.colors,
+              scene.feats]
+    dst = [torch.empty_like(a) for a in arrays]
+    new_index = torch.empty(n, dtype=torch.int32, device=dev)
+    kept = torch.empty(1, dtype=torch.int64, device=dev)
+    cws = torch.empty(int(L.gs_compact_workspace(n)), dtype=torch.uint8, device=dev)
+    p = lgs._p
+
+    def run_prune():
+        lgs.gs_prune(scene.means, scene.opacity_logits, scene.log_scales, scene.feats, params,
+                     mask, cnt, ws)
+
+    def run_compact():
+        lgs._check(L.gs_compact_index(p(mask), n, p(new_index), p(kept), p(cws), cws.numel(),
+                                      lgs._stream()), "gs_compact_index")
+        for a, d in zip(arrays, dst):
+            lgs._check(L.gs_gather_rows(p(a), n, a[0].numel() * a.element_size(), p(new_index),
+                                        p(d), lgs._stream()), "gs_gather_rows")
+
+    def time_graph(fn):
+        fn()
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            fn()
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(reps):
+            flush.fill_(1.0)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            g.replay()
+            b.record()
+            torch.cuda.synchronize()
+            ts.append(a.elapsed_time(b))
+        return float(np.median(ts))
+
+    ms = time_graph(run_prune)
+    m = mask.cpu().numpy()
+    ms_c = time_graph(run_compact)
+    peaks, kind = measured_peaks()
+    achieved = 61.0 * n / (ms / 1e3) / 1e9
+    return {"ms": ms, "gaussians_per_s": n / (ms / 1e3), "params": PRUNE_PARAMS,
+            "pruned_fraction": float((m != 0).mean()),
+            "redundant_fraction": float(((m & 2) != 0).mean()),
+            "geometric_fraction": float(((m & 1) != 0).mean()),
+            "compaction_ms": ms_c,
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": float(peaks["hbm_gbs"]),
+                         "unit": "GB/s", "frac": achieved / float(peaks["hbm_gbs"]),
+                         "traffic": None, "peak_source": kind + " copy",
+                         "note": "61 B per Gaussian: the inputs the rule reads once, the mask byte"}}
 
 
 def measure_e2e(steps, graphs, k, warm):

@@ -119,8 +119,9 @@ lgs_status gs_project(const float* means, const float* quats, const float* log_s
  * alpha compositing within every tile.
  *
  * proj, rect: gs_project outputs for n Gaussians and n_cams cameras.
- * tiles_x, tiles_y: grid size (ceil(W/16), ceil(H/16)).
- * capacity: length of ids (and keys_opt).
+ * tiles_x, tiles_y: grid size (ceil(W/16), ceil(H/16)); n_cams * tiles_x *
+ *   tiles_y at most 2^24 (LGS_ERR_INVALID above).
+ * capacity: length of ids (and keys_opt), below 2^30.
  * ids [capacity] uint32 out: Gaussian index of each sorted instance.
  * ranges [n_cams*tiles_x*tiles_y, 2] uint32 out: [start, end) of each
  *   tile's instances in ids; (0, 0) for an empty tile.
@@ -311,6 +312,70 @@ lgs_status ae_train_step(lgs_ae_state* st, const uint16_t* x, const float* targe
 
 /* Refreshes Wbf / Wtbf of layers first..last from the FP32 masters. */
 lgs_status ae_pack(lgs_ae_state* st, int first, int last, void* stream);
+
+/* ------------------------------------------------------------------------
+ * gs_prune -- language-guided pruning (Sec. III-C, Eq. 4) unioned with the
+ * geometric criteria (low opacity, large scale), run periodically over the
+ * map (every 200 mapping iterations in Sec. IV-A).
+ *
+ * Eq. 4: each Gaussian G_i takes its K nearest neighbours G_j in 3D; G_j is
+ * redundant when d(p_i, p_j) < tau_dist and cos(f_i, f_j) > tau_sim on the
+ * compact language features.  Readings where the paper is silent: the
+ * neighbours are the K nearest among those closer than tau_dist, ranked by
+ * (squared distance, index); G_i marks G_j only if G_i is the one to keep
+ * (higher opacity logit, or the same logit and the lower index), so mutual
+ * neighbours lose one member, not both; the cosine of a zero feature is 0;
+ * low opacity is logit < logit(min_opacity), large scale is
+ * max_k log_s_k > log(max_scale) (thresholds rounded to float once).
+ * Each decision is taken in FP32 with a fixed operation order:
+ * d2 = (dx dx + dy dy) + dz dz with dx = x_j - x_i, d = sqrt(d2);
+ * |f| = sqrt of the left-to-right sum of f_k f_k; sim = (left-to-right
+ * sum of f_ik f_jk) / (|f_i| |f_j|); no fused multiply-add.
+ *
+ * means [n,3], opacity_logits [n], log_scales [n,3] fp32; feats [n,feat_dim]
+ * fp32 or bf16 (feat_dtype), feat_dim in [1, 64].  params (host): k in
+ * [1, 16]; tau_dist > 0 (metres); tau_sim; min_opacity in [0, 1) (0 turns the
+ * opacity test off); max_scale > 0 (+inf turns it off); lo/hi: bounds of the
+ * neighbour grid (cells 1.05 tau_dist wide, at most 2^16 per axis and 2^32
+ * in all).  Gaussians outside the bounds are still handled exactly (they
+ * fall into the border cells); the bounds only affect speed.
+ * mask [n] uint8 out: bit 0 geometric, bit 1 redundant; 0 keeps G_i.
+ * n_pruned_dev: device int64 out, the number of nonzero entries.
+ * workspace: gs_prune_workspace(n) bytes, 256-byte aligned.
+ * Errors: LGS_ERR_INVALID for a bad argument (nothing enqueued).
+ * ---------------------------------------------------------------------- */
+typedef struct {
+  int k;
+  float tau_dist;
+  float tau_sim;
+  float min_opacity;
+  float max_scale;
+  float lo[3];
+  float hi[3];
+} lgs_prune_params;
+
+size_t gs_prune_workspace(int64_t n);
+lgs_status gs_prune(const float* means, const float* opacity_logits, const float* log_scales,
+                    const void* feats, int feat_dim, int feat_dtype, int64_t n,
+                    const lgs_prune_params* params, uint8_t* mask, int64_t* n_pruned_dev,
+                    void* workspace, size_t workspace_bytes, void* stream);
+
+/* Order-preserving compaction after pruning (no counterpart in the paper,
+ * which only says the pruned Gaussians are removed).
+ * gs_compact_index: new_index [n] uint32 out = the rank of G_i among the
+ * kept Gaussians (mask == 0), 0xffffffff for a pruned one; n_kept_dev:
+ * device int64 out.  workspace: gs_compact_workspace(n) bytes, 256-byte
+ * aligned.
+ * gs_gather_rows: dst[new_index[i]] = src[i] for every kept row of
+ * row_bytes bytes (a positive even number; rows aligned to 4 bytes when
+ * row_bytes is a multiple of 4, else to 2; LGS_ERR_INVALID otherwise); dst holds
+ * at least n_kept rows and must not overlap src. */
+size_t gs_compact_workspace(int64_t n);
+lgs_status gs_compact_index(const uint8_t* mask, int64_t n, uint32_t* new_index,
+                            int64_t* n_kept_dev, void* workspace, size_t workspace_bytes,
+                            void* stream);
+lgs_status gs_gather_rows(const void* src, int64_t n, int row_bytes, const uint32_t* new_index,
+                          void* dst, void* stream);
 
 /* Reads and clears the device error word that kernels with bounded waits
  * set when a wait gives up (0 = none).  Synchronises the device. */

@@ -492,15 +492,14 @@ static int grid_for(int64_t m) {
   return (int)std::max<int64_t>(1, std::min<int64_t>((m + 255) / 256, 152 * 16));
 }
 
-// Stable LSD sort of (key, val) on bits [bit0, bit0 + nbits) with onesweep
-// passes of <= 8 bits, passes numbered from pass0 in the workspace.  Returns
-// true when the result ended in (k1, v1).
-static bool onesweep_sort(uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t* v1,
-                          const int64_t* n_dev, int64_t n_max, int nbits, int pass0,
-                          const Layout& L, char* ws, cudaStream_t s) {
+// Stable LSD sort of (key, val) on key bits [0, nbits) with onesweep passes
+// of <= 8 bits.  ghist: 4 x kRadix digit counts, counters: one tile counter
+// per pass, status[p]: kRadix look-back words per tile of pass p; all zeroed
+// by the caller.  Returns true when the result ended in (k1, v1).
+static bool onesweep_passes(uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t* v1,
+                            const int64_t* n_dev, int64_t n_max, int nbits, uint32_t* ghist,
+                            uint32_t* counters, uint32_t* const* status, cudaStream_t s) {
   const int npass = (nbits + 7) / 8;
-  uint32_t* ghist = (uint32_t*)(ws + L.ghist) + pass0 * kRadix;
-  uint32_t* counters = (uint32_t*)(ws + L.counters);
   HistPasses hp{npass, {0, 0, 0, 0}, {0, 0, 0, 0}};
   for (int p = 0; p < npass; p++) {
     hp.shift[p] = 8 * p;
@@ -513,13 +512,44 @@ static bool onesweep_sort(uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t* v1
   bool flipped = false;
   for (int p = 0; p < npass; p++) {
     onesweep_kernel<<<(unsigned)ntile, kOsThreads, 0, s>>>(
-        k0, v0, k1, v1, n_dev, n_max, hp.shift[p], hp.mask[p], ghist + p * kRadix,
-        (uint32_t*)(ws + L.status[pass0 + p]), counters + pass0 + p);
+        k0, v0, k1, v1, n_dev, n_max, hp.shift[p], hp.mask[p], ghist + p * kRadix, status[p],
+        counters + p);
     std::swap(k0, k1);
     std::swap(v0, v1);
     flipped = !flipped;
   }
   return flipped;
+}
+
+static bool onesweep_sort(uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t* v1,
+                          const int64_t* n_dev, int64_t n_max, int nbits, int pass0,
+                          const Layout& L, char* ws, cudaStream_t s) {
+  uint32_t* status[4] = {nullptr, nullptr, nullptr, nullptr};
+  for (int p = 0; p < 4 && pass0 + p < kPassesMax; p++)
+    status[p] = (uint32_t*)(ws + L.status[pass0 + p]);
+  return onesweep_passes(k0, v0, k1, v1, n_dev, n_max, nbits,
+                         (uint32_t*)(ws + L.ghist) + pass0 * kRadix,
+                         (uint32_t*)(ws + L.counters) + pass0, status, s);
+}
+
+size_t sort_pairs_scratch(int64_t n) {
+  const size_t per = align256(4 * (size_t)kRadix * std::max<int64_t>(1, tiles_of(n)));
+  return align256(4 * 4 * kRadix) + align256(4 * 4) + 4 * per;
+}
+
+bool sort_pairs(uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t* v1, int64_t n, int nbits,
+                void* scratch, cudaStream_t s) {
+  char* ws = (char*)scratch;
+  const size_t per = align256(4 * (size_t)kRadix * std::max<int64_t>(1, tiles_of(n)));
+  uint32_t* ghist = (uint32_t*)ws;
+  uint32_t* counters = (uint32_t*)(ws + align256(4 * 4 * kRadix));
+  char* st0 = ws + align256(4 * 4 * kRadix) + align256(4 * 4);
+  uint32_t* status[4];
+  for (int p = 0; p < 4; p++) status[p] = (uint32_t*)(st0 + p * per);
+  cudaMemsetAsync(scratch, 0, sort_pairs_scratch(n), s);
+  if (n == 0 || nbits < 1) return false;
+  return onesweep_passes(k0, v0, k1, v1, nullptr, n, std::min(nbits, 32), ghist, counters, status,
+                         s);
 }
 
 }  // namespace lgs
@@ -552,7 +582,8 @@ extern "C" lgs_status gs_bin_sort(const float* proj, const uint16_t* rect, int64
   LGS_CHECK_ARG(n == 0 || (aligned(proj, 16) && aligned(rect, 8)), "misaligned pointer");
   const int64_t m = (int64_t)n_cams * n;
   const uint32_t tiles = (uint32_t)tiles_x * (uint32_t)tiles_y;
-  LGS_CHECK_ARG((uint64_t)tiles * (uint64_t)n_cams < (1ull << 32), "too many tiles");
+  // the tile sort has at most three 8-bit passes
+  LGS_CHECK_ARG((uint64_t)tiles * (uint64_t)n_cams <= (1ull << 24), "too many tiles");
   Layout L = layout(n, n_cams, capacity);
   LGS_CHECK_ARG(workspace_bytes >= L.total, "workspace too small");
   cudaStream_t s = as_stream(stream);

@@ -23,6 +23,13 @@ lgs_status launch_decode_fused(const lgs_ae_weights* w, const float* z, int64_t 
                                void* pack, cudaStream_t s);
 // Reads and clears the fused kernel's timeout word.
 unsigned fused_error_word();
+// Stable LSD radix sort of n (key, value) pairs on key bits [0, nbits)
+// (nbits <= 32), one onesweep kernel per 8 bits.  `scratch` holds
+// sort_pairs_scratch(n) bytes (256-byte aligned) and is cleared here.
+// Returns true when the result is in (k1, v1), false when in (k0, v0).
+size_t sort_pairs_scratch(int64_t n);
+bool sort_pairs(uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t* v1, int64_t n, int nbits,
+                void* scratch, cudaStream_t s);
 // Reads and clears the binning sort's look-back timeout word.
 unsigned sort_error_word();
 

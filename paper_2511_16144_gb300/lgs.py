@@ -45,6 +45,13 @@ class AeState(ctypes.Structure):
                [("step", ctypes.c_int64)]
 
 
+class PruneParams(ctypes.Structure):
+    """lgs_prune_params."""
+    _fields_ = [("k", ctypes.c_int), ("tau_dist", ctypes.c_float), ("tau_sim", ctypes.c_float),
+                ("min_opacity", ctypes.c_float), ("max_scale", ctypes.c_float),
+                ("lo", ctypes.c_float * 3), ("hi", ctypes.c_float * 3)]
+
+
 class LgsCamera(ctypes.Structure):
     _fields_ = [("fx", ctypes.c_float), ("fy", ctypes.c_float), ("cx", ctypes.c_float),
                 ("cy", ctypes.c_float), ("width", ctypes.c_int32), ("height", ctypes.c_int32),
@@ -82,6 +89,11 @@ def load():
         "gs_render_bwd_static_capacity": ([], I64),
         "gs_render_bwd_static": ([P, P, P, P, P, P, P, I64, P, I32, P, P, I32, I32, P, P, P, P,
                                   P, P, P, P, P, P, P, P, P], I32),
+        "gs_prune_workspace": ([I64], SZ),
+        "gs_prune": ([P, P, P, P, I32, I32, I64, P, P, P, P, SZ, P], I32),
+        "gs_compact_workspace": ([I64], SZ),
+        "gs_compact_index": ([P, I64, P, P, P, SZ, P], I32),
+        "gs_gather_rows": ([P, I64, I32, P, P, P], I32),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -96,7 +108,8 @@ def exported_symbols():
     return ["lgs_version", "lgs_last_error", "gs_project", "gs_bin_sort_workspace", "gs_bin_sort",
             "gs_render_fwd", "gs_render_bwd", "lgs_l1_loss", "ae_workspace_bytes", "ae_encode",
             "ae_decode", "ae_train_step", "ae_pack", "lgs_device_error", "lgs_graph_kernel_nodes", "lgs_zero",
-            "gs_render_bwd_static_capacity", "gs_render_bwd_static"]
+            "gs_render_bwd_static_capacity", "gs_render_bwd_static", "gs_prune_workspace",
+            "gs_prune", "gs_compact_workspace", "gs_compact_index", "gs_gather_rows"]
 
 
 def _check(status, what):
@@ -325,3 +338,49 @@ def lgs_device_error():
     code = ctypes.c_int(0)
     _check(load().lgs_device_error(ctypes.byref(code)), "lgs_device_error")
     return code.value
+
+
+def prune_params(lo, hi, k=8, tau_dist=0.05, tau_sim=0.9, min_opacity=0.005,
+                 max_scale=float("inf")):
+    return PruneParams(int(k), float(tau_dist), float(tau_sim), float(min_opacity),
+                       float(max_scale), (ctypes.c_float * 3)(*[float(v) for v in lo]),
+                       (ctypes.c_float * 3)(*[float(v) for v in hi]))
+
+
+def gs_prune(means, opacity_logits, log_scales, feats, params: PruneParams, mask=None,
+             n_pruned=None, ws=None):
+    """Enqueues gs_prune; returns (mask uint8 [n], n_pruned int64 [1]) on the device."""
+    n, d = feats.shape
+    dev = feats.device
+    mask = torch.empty(n, dtype=torch.uint8, device=dev) if mask is None else mask
+    n_pruned = torch.empty(1, dtype=torch.int64, device=dev) if n_pruned is None else n_pruned
+    if ws is None:
+        ws = torch.empty(max(int(load().gs_prune_workspace(n)), 256), dtype=torch.uint8, device=dev)
+    _check(load().gs_prune(_p(means), _p(opacity_logits), _p(log_scales), _p(feats), d,
+                           _dtype_code(feats), n, ctypes.byref(params), _p(mask), _p(n_pruned),
+                           _p(ws), ws.numel(), _stream()), "gs_prune")
+    return mask, n_pruned
+
+
+def gs_compact(mask, tensors):
+    """Keeps the rows whose mask is 0, in order, of every tensor in
+    ``tensors`` (first dimension n).  Reads the kept count back (synchronises)."""
+    L = load()
+    n = mask.shape[0]
+    dev = mask.device
+    new_index = torch.empty(n, dtype=torch.int32, device=dev)
+    n_kept = torch.empty(1, dtype=torch.int64, device=dev)
+    ws = torch.empty(max(int(L.gs_compact_workspace(n)), 256), dtype=torch.uint8, device=dev)
+    _check(L.gs_compact_index(_p(mask), n, _p(new_index), _p(n_kept), _p(ws), ws.numel(),
+                              _stream()), "gs_compact_index")
+    k = int(n_kept.item())
+    out = []
+    for t in tensors:
+        dst = torch.empty((k,) + tuple(t.shape[1:]), dtype=t.dtype, device=dev)
+        out.append(dst)
+        if k == 0:
+            continue
+        row = t[0].numel() * t.element_size()
+        _check(L.gs_gather_rows(_p(t), n, row, _p(new_index), _p(dst), _stream()),
+               "gs_gather_rows")
+    return out, new_index

@@ -70,3 +70,35 @@ def test_host_argument_checks(lib_path):
     assert lib.gs_bin_sort_workspace(1000, 2, 40, 30, 100000) > 0
     # an empty call is a no-op that succeeds
     assert lib.lgs_l1_loss(None, None, 0, 0, 1.0, None, None, None) == 0
+
+
+def test_prune_host_argument_checks(lib_path):
+    from paper_2511_16144_gb300 import lgs
+    lib = lgs.load()
+    fake = ctypes.c_void_p(0x1000)
+    odd2 = ctypes.c_void_p(0x1002)
+    ws = lib.gs_prune_workspace(1000)
+    assert ws > 0 and lib.gs_compact_workspace(1000) > 0
+
+    def call(n=1000, d=16, dtype=0, ws_bytes=ws, **kw):
+        p = lgs.prune_params((0, 0, 0), (6, 6, 3), **kw)
+        return lib.gs_prune(fake, fake, fake, fake, d, dtype, n, ctypes.byref(p), fake, fake, fake,
+                            ws_bytes, None)
+
+    assert call(k=0) == 1 and b"k must" in lib.lgs_last_error()
+    assert call(k=17) == 1
+    assert call(tau_dist=0.0) == 1 and b"tau_dist" in lib.lgs_last_error()
+    assert call(min_opacity=1.0) == 1
+    assert call(max_scale=0.0) == 1
+    assert call(d=65) == 1 and b"feat_dim" in lib.lgs_last_error()
+    assert call(dtype=2) == 1
+    assert call(ws_bytes=16) == 1 and b"workspace" in lib.lgs_last_error()
+    # a 1 mm grid over a 100 m box has too many cells
+    p = lgs.prune_params((0, 0, 0), (100, 100, 100), tau_dist=0.001)
+    assert lib.gs_prune(fake, fake, fake, fake, 16, 0, 1000, ctypes.byref(p), fake, fake, fake,
+                        ws, None) == 1
+    assert b"grid" in lib.lgs_last_error()
+    assert lib.gs_gather_rows(fake, 10, 7, fake, fake, None) == 1
+    assert lib.gs_gather_rows(odd2, 10, 8, fake, fake, None) == 1
+    assert lib.gs_gather_rows(None, 0, 12, None, None, None) == 0
+    assert lib.gs_compact_index(fake, 10, fake, fake, fake, 8, None) == 1

@@ -271,6 +271,24 @@ def run_gpu(args, rank, world):
                  "channels": "bf16", "feat_dim": 512}
         plain["speedup_of_16d"] = value / world / plain["value"]
         del step512
+    # feature-width sweep (the d ablation of Sec. IV): the same step rendering
+    # d BF16 channels with an L1 against a d-channel target, no autoencoder
+    sweep = []
+    if not args.no_plain:
+        gen_f = torch.Generator(device=dev).manual_seed(4000)
+        for d in (8, 16, 32, 64, 128):
+            fd = torch.randn((scene.n, d), device=dev, generator=gen_f)
+            fd = (fd / fd.norm(dim=1, keepdim=True)).bfloat16().contiguous()
+            tgt = torch.randn((pixels, d), device=dev, generator=gen_f).bfloat16()
+            sd = DeviceScene(geom.means, geom.quats, geom.log_scales, geom.opacity_logits,
+                             colors_bf, fd)
+            st = MappingStep(sd, cams, rgb_t, dep_t, tgt, model=None,
+                             capacity=step16.bufs.capacity)
+            td, _, _ = timed(st, max(5, args.steps // 4), 3)
+            sweep.append({"d": d, "ms_per_step": float(np.mean(td)),
+                          "Mpix_per_s": pixels / 1e6 / (np.mean(td) / 1e3),
+                          "map_bytes_per_gaussian": 44 + 6 + 2 * d})
+            del st, sd, fd, tgt
     # decoded 16-d features against the plain 512-channel FP32 render, per pixel
     step16.run()
     torch.cuda.synchronize()
@@ -314,7 +332,7 @@ def run_gpu(args, rank, world):
             "e2e": e2e,
             "clocks": clocks.summary(),
             "plain_512": plain, "decoded_cosine_error": cos_err, "variants": extra,
-            "prune": prune,
+            "prune": prune, "feature_dim_sweep": sweep,
             "per_call_ms": calls,
             "ae_pretrain": {"steps": args.ae_steps, "loss_first": ae_losses[0],
                             "loss_last": ae_losses[-1], "seconds": ae_train_s},

@@ -153,7 +153,7 @@ lgs_status gs_bin_sort(const float* proj, const uint16_t* rect, int64_t n, int n
  * (chan_dtype) and accumulated in FP32.
  *
  * All cameras must share width and height.  colors [n,3], feats [n,D]
- * (16-byte aligned, D = feat_dim, a positive multiple of 16).
+ * (16-byte aligned, D = feat_dim, a multiple of 8 in [8, 4096]).
  * bg_host: float[3] background colour.
  * Outputs (float32 unless stated): rgb [C,H,W,3], depth [C,H,W],
  * feat [C,H,W,D], T_final [C,H,W], last [C,H,W] uint32 (position + 1, in

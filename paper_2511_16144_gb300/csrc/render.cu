@@ -62,6 +62,12 @@ template <typename TC, int FC>
 __device__ __forceinline__ void load_feats(const TC* __restrict__ src, float* dst);
 
 template <>
+__device__ __forceinline__ void load_feats<float, 8>(const float* __restrict__ src, float* dst) {
+  const float4* s4 = reinterpret_cast<const float4*>(src);
+#pragma unroll
+  for (int q = 0; q < 2; q++) reinterpret_cast<float4*>(dst)[q] = s4[q];
+}
+template <>
 __device__ __forceinline__ void load_feats<float, 16>(const float* __restrict__ src, float* dst) {
   const float4* s4 = reinterpret_cast<const float4*>(src);
 #pragma unroll
@@ -87,6 +93,11 @@ __device__ __forceinline__ void load_bf16_feats(const __nv_bfloat16* __restrict_
       dst[8 * q + 2 * k + 1] = f.y;
     }
   }
+}
+template <>
+__device__ __forceinline__ void load_feats<__nv_bfloat16, 8>(const __nv_bfloat16* __restrict__ src,
+                                                             float* dst) {
+  load_bf16_feats<8>(src, dst);
 }
 template <>
 __device__ __forceinline__ void load_feats<__nv_bfloat16, 16>(const __nv_bfloat16* __restrict__ src,
@@ -481,7 +492,8 @@ static lgs_status common_args(const float* proj, const uint32_t* ids, const uint
                               int chan_dtype, const float* bg_host, RasterArgs& A, int& ntile) {
   LGS_CHECK_ARG(n >= 0 && n < ((int64_t)1 << 31), "n out of range");
   LGS_CHECK_ARG(cams_host && n_cams >= 1 && n_cams <= LGS_MAX_CAMS, "bad cameras");
-  LGS_CHECK_ARG(feat_dim >= 16 && feat_dim % 16 == 0, "feat_dim must be a positive multiple of 16");
+  LGS_CHECK_ARG(feat_dim >= 8 && feat_dim % 8 == 0 && feat_dim <= 4096,
+                "feat_dim must be a multiple of 8 in [8, 4096]");
   LGS_CHECK_ARG(chan_dtype == LGS_F32 || chan_dtype == LGS_BF16, "bad channel dtype");
   LGS_CHECK_ARG(ranges && bg_host, "null pointer");
   LGS_CHECK_ARG(n == 0 || (proj && ids && colors && feats), "null pointer");
@@ -536,13 +548,18 @@ extern "C" lgs_status gs_render_fwd(const float* proj, const uint32_t* ids, cons
   A.n_contrib = n_contrib_opt;
   cudaStream_t s = as_stream(stream);
   const bool bf = chan_dtype == LGS_BF16;
+  // channel chunk FC: 16 for the compact features, else the widest of 32 /
+  // 16 / 8 that divides feat_dim
   if (feat_dim == 16)
     return bf ? launch_fwd<16, __nv_bfloat16>(A, ntile, 1, s) : launch_fwd<16, float>(A, ntile, 1, s);
   if (feat_dim % 32 == 0)
     return bf ? launch_fwd<32, __nv_bfloat16>(A, ntile, feat_dim / 32, s)
               : launch_fwd<32, float>(A, ntile, feat_dim / 32, s);
-  return bf ? launch_fwd<16, __nv_bfloat16>(A, ntile, feat_dim / 16, s)
-            : launch_fwd<16, float>(A, ntile, feat_dim / 16, s);
+  if (feat_dim % 16 == 0)
+    return bf ? launch_fwd<16, __nv_bfloat16>(A, ntile, feat_dim / 16, s)
+              : launch_fwd<16, float>(A, ntile, feat_dim / 16, s);
+  return bf ? launch_fwd<8, __nv_bfloat16>(A, ntile, feat_dim / 8, s)
+            : launch_fwd<8, float>(A, ntile, feat_dim / 8, s);
 }
 
 extern "C" lgs_status gs_render_bwd(const float* means, const float* quats,
@@ -590,9 +607,12 @@ extern "C" lgs_status gs_render_bwd(const float* means, const float* quats,
   else if (feat_dim % 32 == 0)
     st = bf ? launch_bwd<32, __nv_bfloat16>(A, ntile, feat_dim / 32, s)
             : launch_bwd<32, float>(A, ntile, feat_dim / 32, s);
-  else
+  else if (feat_dim % 16 == 0)
     st = bf ? launch_bwd<16, __nv_bfloat16>(A, ntile, feat_dim / 16, s)
             : launch_bwd<16, float>(A, ntile, feat_dim / 16, s);
+  else
+    st = bf ? launch_bwd<8, __nv_bfloat16>(A, ntile, feat_dim / 8, s)
+            : launch_bwd<8, float>(A, ntile, feat_dim / 8, s);
   if (st != LGS_OK) return st;
   return launch_project_bwd(means, quats, log_scales, opacity_logits, n, n_cams, cb, grad2d,
                             d_means, d_quats, d_log_scales, d_opacity_logits, s);

@@ -58,7 +58,7 @@ def test_host_argument_checks(lib_path):
     # misaligned quaternion array
     assert lib.gs_project(fake, odd, fake, fake, 10, cam, 1, fake, fake, None) == 1
     assert b"misaligned" in lib.lgs_last_error()
-    # feature width not a multiple of 16
+    # feature width not a multiple of 8
     bg = (ctypes.c_float * 3)(0, 0, 0)
     assert lib.gs_render_fwd(fake, fake, fake, 10, cam, 1, fake, fake, 12, 0, bg, fake, fake,
                              fake, fake, fake, None, None) == 1

@@ -58,12 +58,11 @@ std::vector<Unit> schedule() {
   auto add = [&](int m, int r0, int rows, int c0, int kc) { U.push_back({m, r0, rows, c0, kc}); };
   add(W4, 0, 64, 0, 16);                                                   // F1
   add(W5, 0, 128, 0, 64);                                                  // F2
-  for (int h = 0; h < 2; h++) for (int k = 0; k < 2; k++) add(W6, 128 * h, 128, 64 * k, 64);  // F3
+  for (int k = 0; k < 4; k++) add(W6, 0, 256, 32 * k, 32);                // F3 (N = 256)
   for (int k = 0; k < 4; k++) add(W7, 0, 128, 64 * k, 64);                // F4 chunk 0
   for (int k = 0; k < 4; k++) add(W7, 128, 128, 64 * k, 64);             // F4 chunk 1
-  auto b1 = [&](int c) {
-    for (int h = 0; h < 2; h++)
-      for (int k = 0; k < 2; k++) add(T7, 128 * h, 128, 128 * c + 64 * k, 64);
+  auto b1 = [&](int c) {  // N = 256
+    for (int k = 0; k < 4; k++) add(T7, 0, 256, 128 * c + 32 * k, 32);
   };
   b1(0);
   for (int k = 0; k < 4; k++) add(W7, 256, 128, 64 * k, 64);             // F4 chunk 2
@@ -71,7 +70,7 @@ std::vector<Unit> schedule() {
   for (int k = 0; k < 4; k++) add(W7, 384, 128, 64 * k, 64);             // F4 chunk 3
   b1(2);
   b1(3);
-  for (int h = 0; h < 2; h++) for (int k = 0; k < 2; k++) add(W6, 128 * h, 128, 64 * k, 64);  // R3
+  for (int k = 0; k < 4; k++) add(W6, 0, 256, 32 * k, 32);                // R3 (N = 256)
   for (int k = 0; k < 4; k++) add(T6, 0, 128, 64 * k, 64);               // B2
   add(W5, 0, 128, 0, 64);                                                  // R2
   for (int k = 0; k < 2; k++) add(T5, 0, 64, 64 * k, 64);                // B3
@@ -139,8 +138,9 @@ __device__ unsigned g_fused_error;
 
 constexpr int kEpiWarps = 16;
 constexpr int kFusedThreads = (kEpiWarps + 2) * 32;   // + producer warp + MMA warp
-// barriers: full[kStages], empty[kStages], accbar, opbar, then the TMEM slot
-constexpr uint32_t kBarBytes = (2 * kStages + 2) * 8 + 4;
+// barriers: full[kStages], empty[kStages], accbar, opbar, ybar[2], dyfree,
+// then the TMEM slot
+constexpr uint32_t kBarBytes = (2 * kStages + 5) * 8 + 4;
 constexpr uint32_t SM_BIAS = SM_BAR + 128;             // b4 | b5 | b6 | b7 (960 floats)
 constexpr uint32_t SM_ALL = SM_BIAS + 960 * 4;
 static_assert(kBarBytes <= SM_BIAS - SM_BAR, "barrier block overlaps the biases");
@@ -153,7 +153,9 @@ decode_fused_kernel(const __grid_constant__ FusedArgs a) {
   uint64_t* empty = full + kStages;
   uint64_t* accbar = full + 2 * kStages;
   uint64_t* opbar = accbar + 1;
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(opbar + 1);
+  uint64_t* ybar = opbar + 1;    // [2] output chunk ready in TMEM buffer c & 1
+  uint64_t* dyfree = ybar + 2;   // the backward product of the last dy chunk is done
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(dyfree + 1);
   float* sb = reinterpret_cast<float*>(sm + SM_BIAS);
   const float* sb4 = sb;
   const float* sb5 = sb + 64;
@@ -171,6 +173,9 @@ decode_fused_kernel(const __grid_constant__ FusedArgs a) {
     }
     tc::mbar_init(accbar, 1);
     tc::mbar_init(opbar, kEpiWarps * 32);
+    tc::mbar_init(&ybar[0], 1);
+    tc::mbar_init(&ybar[1], 1);
+    tc::mbar_init(dyfree, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   tc::fence_before();
@@ -236,25 +241,26 @@ decode_fused_kernel(const __grid_constant__ FusedArgs a) {
         unit(SM_H1, 64, 0, 64, 128, 0, true);                          // F2
         done();
         wait_op();
-        for (int h = 0; h < 2; h++)
-          for (int k = 0; k < 2; k++) unit(SM_H2, 128, 64 * k, 64, 128, 128 * h, k == 0);  // F3
+        for (int k = 0; k < 4; k++) unit(SM_H2, 128, 32 * k, 32, 256, 0, k == 0);         // F3
         done();
         wait_op();
-        for (int k = 0; k < 4; k++) unit(SM_H3, 256, 64 * k, 64, 128, 256, k == 0);       // F4 c0
-        done();
-        for (int k = 0; k < 4; k++) unit(SM_H3, 256, 64 * k, 64, 128, 384, k == 0);       // F4 c1
+        // output chunk c -> TMEM buffer c & 1, announced on ybar[c & 1]; each
+        // dy chunk's product is announced on dyfree (its buffer is free again)
+        auto f4 = [&](int c) {
+          for (int k = 0; k < 4; k++)
+            unit(SM_H3, 256, 64 * k, 64, 128, 256 + 128 * (c & 1), k == 0);
+          if (ok) tc::commit(&ybar[c & 1]);
+        };
+        f4(0);
+        f4(1);
         for (int c = 0; c < 4; c++) {
           wait_op();                                                   // dy chunk c written
-          for (int h = 0; h < 2; h++)
-            for (int k = 0; k < 2; k++)
-              unit(SM_DY, 128, 64 * k, 64, 128, 128 * h, c == 0 && k == 0);               // B1 c
-          if (c < 3) done();
-          if (c < 2)
-            for (int k = 0; k < 4; k++)
-              unit(SM_H3, 256, 64 * k, 64, 128, 256 + 128 * (c & 1), k == 0);             // F4 c+2
+          for (int k = 0; k < 4; k++)
+            unit(SM_DY, 128, 32 * k, 32, 256, 0, c == 0 && k == 0);                         // B1 c
+          if (ok) tc::commit(dyfree);
+          if (c < 2) f4(c + 2);
         }
-        for (int h = 0; h < 2; h++)
-          for (int k = 0; k < 2; k++) unit(SM_H2, 128, 64 * k, 64, 128, 256 + 128 * h, k == 0);  // R3
+        for (int k = 0; k < 4; k++) unit(SM_H2, 128, 32 * k, 32, 256, 256, k == 0);       // R3
         done();
         wait_op();                                                     // d3 written
         for (int k = 0; k < 4; k++) unit(SM_H3, 256, 64 * k, 64, 128, 0, k == 0);         // B2
@@ -349,7 +355,8 @@ decode_fused_kernel(const __grid_constant__ FusedArgs a) {
 #pragma unroll
           for (int k = 0; k < 4; k++) tg[k] = src[k];
         }
-        wait_acc();
+        ok = ok && tc::mbar_wait(&ybar[c & 1], (c >> 1) & 1, kLimit);
+        tc::fence_after();
         tc::tmem_ld32(tb + 256 + 128 * (c & 1) + 32 * qq, v);
 #pragma unroll
         for (int k = 0; k < 4; k++) {
@@ -365,9 +372,15 @@ decode_fused_kernel(const __grid_constant__ FusedArgs a) {
             v[i + 1] = valid ? (d1 > 0.f ? a.scale : (d1 < 0.f ? -a.scale : 0.f)) : 0.f;
           }
         }
+        if (c > 0) {  // the previous chunk's product has read the dy buffer
+          ok = ok && tc::mbar_wait(dyfree, (c - 1) & 1, kLimit);
+          tc::fence_after();
+        }
         put_row<32>(sm + SM_DY, r, 32 * qq, 128, v);
         arrive();
       }
+      ok = ok && tc::mbar_wait(dyfree, 1, kLimit);  // the last chunk's phase
+      tc::fence_after();
       // E5: d3 = dh3 * gelu'(pre3)
       wait_acc();
 #pragma unroll 1

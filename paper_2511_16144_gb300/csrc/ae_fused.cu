@@ -322,7 +322,12 @@ decode_fused_kernel(const __grid_constant__ FusedArgs a) {
         const int c0 = 16 * qq;
         tc::tmem_ld16(tb + c0, v);
 #pragma unroll
-        for (int i = 0; i < 16; i++) v[i] = gelu_tanh(v[i] + sb4[c0 + i]);
+        for (int i = 0; i < 16; i += 2) {
+          const float2 g = gelu_tanh2(__fadd2_rn(f2(v[i], v[i + 1]),
+                                                 *reinterpret_cast<const float2*>(sb4 + c0 + i)));
+          v[i] = g.x;
+          v[i + 1] = g.y;
+        }
         put_row<16>(sm + SM_H1, r, c0, 64, v);
       }
       arrive();
@@ -331,7 +336,12 @@ decode_fused_kernel(const __grid_constant__ FusedArgs a) {
         const int c0 = 32 * qq;
         tc::tmem_ld32(tb + c0, v);
 #pragma unroll
-        for (int i = 0; i < 32; i++) v[i] = gelu_tanh(v[i] + sb5[c0 + i]);
+        for (int i = 0; i < 32; i += 2) {
+          const float2 g = gelu_tanh2(__fadd2_rn(f2(v[i], v[i + 1]),
+                                                 *reinterpret_cast<const float2*>(sb5 + c0 + i)));
+          v[i] = g.x;
+          v[i + 1] = g.y;
+        }
         put_row<32>(sm + SM_H2, r, c0, 128, v);
       }
       arrive();
@@ -341,7 +351,12 @@ decode_fused_kernel(const __grid_constant__ FusedArgs a) {
         const int c0 = 64 * qq + 32 * s2;
         tc::tmem_ld32(tb + c0, v);
 #pragma unroll
-        for (int i = 0; i < 32; i++) v[i] = gelu_tanh(v[i] + sb6[c0 + i]);
+        for (int i = 0; i < 32; i += 2) {
+          const float2 g = gelu_tanh2(__fadd2_rn(f2(v[i], v[i + 1]),
+                                                 *reinterpret_cast<const float2*>(sb6 + c0 + i)));
+          v[i] = g.x;
+          v[i + 1] = g.y;
+        }
         put_row<32>(sm + SM_H3, r, c0, 256, v);
       }
       arrive();
@@ -365,8 +380,10 @@ decode_fused_kernel(const __grid_constant__ FusedArgs a) {
           for (int e = 0; e < 4; e++) {
             const float2 tt = valid ? __bfloat1622float2(h2[e]) : make_float2(0.f, 0.f);
             const int i = 8 * k + 2 * e;
-            const float d0 = v[i] + sb7[n0 + i] - tt.x;
-            const float d1 = v[i + 1] + sb7[n0 + i + 1] - tt.y;
+            const float2 dd = __fadd2_rn(
+                __fadd2_rn(f2(v[i], v[i + 1]), *reinterpret_cast<const float2*>(sb7 + n0 + i)),
+                f2(-tt.x, -tt.y));
+            const float d0 = dd.x, d1 = dd.y;
             if (valid) lsum += fabsf(d0) + fabsf(d1);
             v[i] = valid ? (d0 > 0.f ? a.scale : (d0 < 0.f ? -a.scale : 0.f)) : 0.f;
             v[i + 1] = valid ? (d1 > 0.f ? a.scale : (d1 < 0.f ? -a.scale : 0.f)) : 0.f;
@@ -389,7 +406,13 @@ decode_fused_kernel(const __grid_constant__ FusedArgs a) {
         tc::tmem_ld32(tb + c0, v);
         tc::tmem_ld32(tb + 256 + c0, pre);
 #pragma unroll
-        for (int i = 0; i < 32; i++) v[i] *= gelu_tanh_grad(pre[i] + sb6[c0 + i]);
+        for (int i = 0; i < 32; i += 2) {
+          const float2 g = gelu_tanh_grad2(__fadd2_rn(
+              f2(pre[i], pre[i + 1]), *reinterpret_cast<const float2*>(sb6 + c0 + i)));
+          const float2 d = __fmul2_rn(f2(v[i], v[i + 1]), g);
+          v[i] = d.x;
+          v[i + 1] = d.y;
+        }
         put_row<32>(sm + SM_H3, r, c0, 256, v);
       }
       arrive();
@@ -400,7 +423,13 @@ decode_fused_kernel(const __grid_constant__ FusedArgs a) {
         tc::tmem_ld32(tb + c0, v);
         tc::tmem_ld32(tb + 128 + c0, pre);
 #pragma unroll
-        for (int i = 0; i < 32; i++) v[i] *= gelu_tanh_grad(pre[i] + sb5[c0 + i]);
+        for (int i = 0; i < 32; i += 2) {
+          const float2 g = gelu_tanh_grad2(__fadd2_rn(
+              f2(pre[i], pre[i + 1]), *reinterpret_cast<const float2*>(sb5 + c0 + i)));
+          const float2 d = __fmul2_rn(f2(v[i], v[i + 1]), g);
+          v[i] = d.x;
+          v[i + 1] = d.y;
+        }
         put_row<32>(sm + SM_H2, r, c0, 128, v);
       }
       arrive();
@@ -411,7 +440,13 @@ decode_fused_kernel(const __grid_constant__ FusedArgs a) {
         tc::tmem_ld16(tb + c0, v);
         tc::tmem_ld16(tb + 64 + c0, pre);
 #pragma unroll
-        for (int i = 0; i < 16; i++) v[i] *= gelu_tanh_grad(pre[i] + sb4[c0 + i]);
+        for (int i = 0; i < 16; i += 2) {
+          const float2 g = gelu_tanh_grad2(__fadd2_rn(
+              f2(pre[i], pre[i + 1]), *reinterpret_cast<const float2*>(sb4 + c0 + i)));
+          const float2 d = __fmul2_rn(f2(v[i], v[i + 1]), g);
+          v[i] = d.x;
+          v[i + 1] = d.y;
+        }
         put_row<16>(sm + SM_H1, r, c0, 64, v);
       }
       arrive();

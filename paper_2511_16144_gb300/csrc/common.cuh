@@ -89,6 +89,31 @@ __device__ __forceinline__ float gelu_tanh_grad(float x) {
               0.5f * x * (1.f - t * t) * 0.7978845608028654f * fmaf(0.134145f, x2, 1.f));
 }
 
+// The same two functions on a pair of values with the packed FP32 pipe
+// (FFMA2 / FMUL2 / FADD2: per component identical to the scalar
+// round-to-nearest operations), two tanh per pair.
+__device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
+__device__ __forceinline__ float2 tanh_approx2(float2 u) {
+  return f2(tanh_approx(u.x), tanh_approx(u.y));
+}
+__device__ __forceinline__ float2 gelu_tanh2(float2 x) {
+  constexpr float K = 0.7978845608028654f, KC = 0.7978845608028654f * 0.044715f;
+  const float2 x2 = __fmul2_rn(x, x);
+  const float2 t = tanh_approx2(__fmul2_rn(x, __ffma2_rn(x2, f2(KC, KC), f2(K, K))));
+  const float2 h = __fmul2_rn(x, f2(0.5f, 0.5f));
+  return __ffma2_rn(h, t, h);
+}
+__device__ __forceinline__ float2 gelu_tanh_grad2(float2 x) {
+  constexpr float K = 0.7978845608028654f, KC = 0.7978845608028654f * 0.044715f,
+                  K3 = 0.7978845608028654f * 0.134145f;
+  const float2 x2 = __fmul2_rn(x, x);
+  const float2 t = tanh_approx2(__fmul2_rn(x, __ffma2_rn(x2, f2(KC, KC), f2(K, K))));
+  const float2 q = __ffma2_rn(x2, f2(K3, K3), f2(K, K));               // K (1 + 3c x^2)
+  const float2 s = __ffma2_rn(t, f2(-t.x, -t.y), f2(1.f, 1.f));        // 1 - t^2
+  const float2 r = __fmul2_rn(__fmul2_rn(x, f2(0.5f, 0.5f)), s);       // x (1 - t^2) / 2
+  return __ffma2_rn(r, q, __ffma2_rn(t, f2(0.5f, 0.5f), f2(0.5f, 0.5f)));
+}
+
 __device__ __forceinline__ float to_float(float x) { return x; }
 __device__ __forceinline__ float to_float(__nv_bfloat16 x) { return __bfloat162float(x); }
 

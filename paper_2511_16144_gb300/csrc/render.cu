@@ -187,13 +187,16 @@ __global__ void __launch_bounds__(kThreads) render_fwd_kernel(RasterArgs A, int 
         }
         const float w = __fmul_rn(alpha, T);
         const float4* c4 = reinterpret_cast<const float4*>(s_ch + j * NCH);
+        const float2 ww = f2(w, w);
 #pragma unroll
-        for (int q = 0; q < NCH / 4; q++) {
+        for (int q = 0; q < NCH / 4; q++) {  // packed FP32 pairs (FFMA2)
           const float4 v = c4[q];
-          acc[4 * q + 0] = fmaf(w, v.x, acc[4 * q + 0]);
-          acc[4 * q + 1] = fmaf(w, v.y, acc[4 * q + 1]);
-          acc[4 * q + 2] = fmaf(w, v.z, acc[4 * q + 2]);
-          acc[4 * q + 3] = fmaf(w, v.w, acc[4 * q + 3]);
+          const float2 a0 = __ffma2_rn(ww, f2(v.x, v.y), f2(acc[4 * q], acc[4 * q + 1]));
+          const float2 a1 = __ffma2_rn(ww, f2(v.z, v.w), f2(acc[4 * q + 2], acc[4 * q + 3]));
+          acc[4 * q + 0] = a0.x;
+          acc[4 * q + 1] = a0.y;
+          acc[4 * q + 2] = a1.x;
+          acc[4 * q + 3] = a1.y;
         }
         T = Tn;
         lastpos = b0 - range.x + j + 1;
@@ -338,15 +341,15 @@ render_bwd_kernel(RasterArgs A, int chunk_base) {
             const float Tj = T * inv;
             w = alpha * Tj;
             const float4* c4 = reinterpret_cast<const float4*>(s_ch + j * NCH);
-            float xg = 0.f;
+            float2 x2 = f2(0.f, 0.f), y2 = f2(0.f, 0.f);  // two packed partial sums
 #pragma unroll
             for (int q = 0; q < NCH / 4; q++) {
               const float4 v = c4[q];
-              xg = fmaf(v.x, g[4 * q], xg);
-              xg = fmaf(v.y, g[4 * q + 1], xg);
-              xg = fmaf(v.z, g[4 * q + 2], xg);
-              xg = fmaf(v.w, g[4 * q + 3], xg);
+              x2 = __ffma2_rn(f2(v.x, v.y), f2(g[4 * q], g[4 * q + 1]), x2);
+              y2 = __ffma2_rn(f2(v.z, v.w), f2(g[4 * q + 2], g[4 * q + 3]), y2);
             }
+            const float2 xy2 = __fadd2_rn(x2, y2);
+            const float xg = xy2.x + xy2.y;
             const float dal = Tj * xg - S * inv;
             S = fmaf(w, xg, S);
             T = Tj;
@@ -373,13 +376,16 @@ render_bwd_kernel(RasterArgs A, int chunk_base) {
       for (int k = 0; k < 16; k++) {
         const float wv = wr[k], pv = pr[k];
         const float4* g4 = reinterpret_cast<const float4*>(gr + k * NCH);
+        const float2 w2 = f2(wv, wv);
 #pragma unroll
-        for (int q = 0; q < NCH / 4; q++) {
+        for (int q = 0; q < NCH / 4; q++) {  // packed FP32 pairs (FFMA2)
           const float4 v = g4[q];
-          cs[4 * q + 0] = fmaf(wv, v.x, cs[4 * q + 0]);
-          cs[4 * q + 1] = fmaf(wv, v.y, cs[4 * q + 1]);
-          cs[4 * q + 2] = fmaf(wv, v.z, cs[4 * q + 2]);
-          cs[4 * q + 3] = fmaf(wv, v.w, cs[4 * q + 3]);
+          const float2 a0 = __ffma2_rn(w2, f2(v.x, v.y), f2(cs[4 * q], cs[4 * q + 1]));
+          const float2 a1 = __ffma2_rn(w2, f2(v.z, v.w), f2(cs[4 * q + 2], cs[4 * q + 3]));
+          cs[4 * q + 0] = a0.x;
+          cs[4 * q + 1] = a0.y;
+          cs[4 * q + 2] = a1.x;
+          cs[4 * q + 3] = a1.y;
         }
         const float xl = (float)k + 0.5f;
         S0 += pv;

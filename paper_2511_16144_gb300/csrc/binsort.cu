@@ -194,6 +194,44 @@ __global__ void __launch_bounds__(256) hist_kernel(const uint32_t* __restrict__ 
   }
 }
 
+// Digit histograms of up to four passes of the key sequence produced by a
+// kernel, accumulated in that kernel while it writes the keys: every lane of
+// the warp calls hist_add the same number of times (valid marks real keys),
+// then the block adds its counts to the global histograms.
+__device__ __forceinline__ void hist_add(uint32_t (*h)[kRadix], const HistPasses& hp, uint32_t k,
+                                         bool valid) {
+  const int lane = threadIdx.x & 31;
+  for (int p = 0; p < hp.n; p++) {
+    const uint32_t d = valid ? (k >> hp.shift[p]) & hp.mask[p] : (uint32_t)(kRadix + lane);
+    const uint32_t peers = __match_any_sync(0xffffffffu, d);
+    if (valid && lane == __ffs(peers) - 1) atomicAdd(&h[p][d], (uint32_t)__popc(peers));
+  }
+}
+
+__device__ __forceinline__ void hist_flush(const uint32_t (*h)[kRadix], const HistPasses& hp,
+                                           uint32_t* __restrict__ ghist) {
+  __syncthreads();
+  for (int i = threadIdx.x; i < hp.n * kRadix; i += blockDim.x) {
+    const uint32_t c = (&h[0][0])[i];
+    if (c) atomicAdd(ghist + i, c);
+  }
+}
+
+__device__ __forceinline__ void hist_clear(uint32_t (*h)[kRadix]) {
+  for (int i = threadIdx.x; i < 4 * kRadix; i += blockDim.x) (&h[0][0])[i] = 0;
+  __syncthreads();
+}
+
+static HistPasses hist_passes(int nbits) {
+  HistPasses hp{(nbits + 7) / 8, {0, 0, 0, 0}, {0, 0, 0, 0}};
+  for (int p = 0; p < hp.n; p++) {
+    hp.shift[p] = 8 * p;
+    const int bits = nbits - 8 * p < 8 ? nbits - 8 * p : 8;
+    hp.mask[p] = (1u << bits) - 1u;
+  }
+  return hp;
+}
+
 // ------------------------------------------------------------------ onesweep pass
 
 __global__ void __launch_bounds__(kOsThreads)
@@ -284,16 +322,29 @@ onesweep_kernel(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ v
 
 // ------------------------------------------------------------------ binning kernels
 
-__global__ void depth_keys_kernel(const float4* __restrict__ proj, const ushort4* __restrict__ rect,
-                                  int64_t m, uint32_t* __restrict__ keys,
-                                  uint32_t* __restrict__ vals) {
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    ushort4 r = rect[i];
-    bool vis = r.z > r.x && r.w > r.y;
-    keys[i] = vis ? __float_as_uint(proj[2 * i + 1].z) : 0xffffffffu;
-    vals[i] = (uint32_t)i;
+// Depth keys of the (camera, Gaussian) items (all ones when invisible), and
+// the digit histograms of the depth sort's passes.
+__global__ void __launch_bounds__(256)
+depth_keys_kernel(const float4* __restrict__ proj, const ushort4* __restrict__ rect, int64_t m,
+                  uint32_t* __restrict__ keys, uint32_t* __restrict__ vals, HistPasses hp,
+                  uint32_t* __restrict__ ghist) {
+  __shared__ uint32_t h[4][kRadix];
+  hist_clear(h);
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t b = (int64_t)blockIdx.x * blockDim.x; b < m; b += stride) {
+    const int64_t i = b + threadIdx.x;
+    const bool valid = i < m;
+    uint32_t k = 0;
+    if (valid) {
+      const ushort4 r = rect[i];
+      const bool vis = r.z > r.x && r.w > r.y;
+      k = vis ? __float_as_uint(proj[2 * i + 1].z) : 0xffffffffu;
+      keys[i] = k;
+      vals[i] = (uint32_t)i;
+    }
+    hist_add(h, hp, k, valid);
   }
+  hist_flush(h, hp, ghist);
 }
 
 __global__ void camera_keys_kernel(const uint32_t* __restrict__ vals, int64_t m, uint32_t n,
@@ -397,11 +448,13 @@ emit_kernel(const uint32_t* __restrict__ order, const ushort4* __restrict__ rect
             const uint64_t* __restrict__ offs, const uint32_t* __restrict__ bstart, int64_t m,
             uint32_t n, int tiles_x, uint32_t tiles, uint32_t n_tiles_all,
             const int64_t* __restrict__ sort_n, uint32_t* __restrict__ tkey,
-            uint32_t* __restrict__ tval) {
+            uint32_t* __restrict__ tval, HistPasses hp, uint32_t* __restrict__ ghist) {
   __shared__ uint64_t s_off[kEmitSlots + 2];
+  __shared__ uint32_t hst[4][kRadix];
   const int64_t K = *sort_n;
   const int64_t o0 = (int64_t)blockIdx.x * kEmitSlots;
   if (o0 >= K) return;
+  hist_clear(hst);
   const int64_t o1 = o0 + kEmitSlots < K ? o0 + kEmitSlots : K;
   const int64_t lo = bstart[blockIdx.x];
   const int64_t hi = o1 < K ? (int64_t)bstart[blockIdx.x + 1] : m - 1;  // holds slot o1 - 1
@@ -412,23 +465,34 @@ emit_kernel(const uint32_t* __restrict__ order, const ushort4* __restrict__ rect
   __syncthreads();
   auto g = [&](int64_t i) { return offs[i]; };
   auto sm = [&](int64_t i) { return s_off[i]; };
-  for (int r = 0; r < kEmitPer; r++) {
+  for (int r = 0; r < kEmitPer; r++) {  // every lane runs every round (histograms)
     const int64_t o = o0 + (int64_t)r * kEmitThreads + threadIdx.x;
-    if (o >= o1) break;
-    const int64_t i = staged ? lo + last_le(sm, 0, span, (uint64_t)o)
-                             : last_le(g, lo, hi + 1, (uint64_t)o);
-    const uint32_t item = order[i];
-    const ushort4 rc = rect[item];
-    const uint32_t w = (uint32_t)(rc.z - rc.x), h = (uint32_t)(rc.w - rc.y);
-    const uint64_t local = (uint64_t)o - offs[i];
-    if (rc.z <= rc.x || rc.w <= rc.y || local >= (uint64_t)w * h) continue;  // cannot happen
-    const uint32_t ty = rc.y + (uint32_t)local / w, tx = rc.x + (uint32_t)local % w;
-    const uint32_t c = item / n;
-    const uint32_t key = c * tiles + ty * (uint32_t)tiles_x + tx;
-    if (key >= n_tiles_all) continue;  // cannot happen
-    tkey[o] = key;
-    tval[o] = item - c * n;
+    bool valid = o < o1;
+    uint32_t key = 0;
+    if (valid) {
+      const int64_t i = staged ? lo + last_le(sm, 0, span, (uint64_t)o)
+                               : last_le(g, lo, hi + 1, (uint64_t)o);
+      const uint32_t item = order[i];
+      const ushort4 rc = rect[item];
+      const uint32_t w = (uint32_t)(rc.z - rc.x), h = (uint32_t)(rc.w - rc.y);
+      const uint64_t local = (uint64_t)o - offs[i];
+      if (rc.z <= rc.x || rc.w <= rc.y || local >= (uint64_t)w * h) {
+        valid = false;  // cannot happen
+      } else {
+        const uint32_t ty = rc.y + (uint32_t)local / w, tx = rc.x + (uint32_t)local % w;
+        const uint32_t c = item / n;
+        key = c * tiles + ty * (uint32_t)tiles_x + tx;
+        if (key >= n_tiles_all) {
+          valid = false;  // cannot happen
+        } else {
+          tkey[o] = key;
+          tval[o] = item - c * n;
+        }
+      }
+    }
+    hist_add(hst, hp, key, valid);
   }
+  hist_flush(hst, hp, ghist);
 }
 
 __global__ void ranges_kernel(const uint32_t* __restrict__ tkey, const int64_t* __restrict__ sort_n,
@@ -498,17 +562,14 @@ static int grid_for(int64_t m) {
 // by the caller.  Returns true when the result ended in (k1, v1).
 static bool onesweep_passes(uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t* v1,
                             const int64_t* n_dev, int64_t n_max, int nbits, uint32_t* ghist,
-                            uint32_t* counters, uint32_t* const* status, cudaStream_t s) {
+                            uint32_t* counters, uint32_t* const* status, cudaStream_t s,
+                            bool hist_done = false) {
   const int npass = (nbits + 7) / 8;
-  HistPasses hp{npass, {0, 0, 0, 0}, {0, 0, 0, 0}};
-  for (int p = 0; p < npass; p++) {
-    hp.shift[p] = 8 * p;
-    const int bits = std::min(8, nbits - 8 * p);
-    hp.mask[p] = (1u << bits) - 1u;
-  }
+  const HistPasses hp = hist_passes(nbits);
   const int64_t ntile = std::max<int64_t>(1, tiles_of(n_max));
-  hist_kernel<<<(unsigned)std::min<int64_t>(ntile * 2, 152 * 4), 256, 0, s>>>(k0, n_dev, n_max, hp,
-                                                                           ghist);
+  if (!hist_done)  // else the producer of the keys has filled ghist
+    hist_kernel<<<(unsigned)std::min<int64_t>(ntile * 2, 152 * 4), 256, 0, s>>>(k0, n_dev, n_max,
+                                                                             hp, ghist);
   bool flipped = false;
   for (int p = 0; p < npass; p++) {
     onesweep_kernel<<<(unsigned)ntile, kOsThreads, 0, s>>>(
@@ -523,13 +584,13 @@ static bool onesweep_passes(uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t* 
 
 static bool onesweep_sort(uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t* v1,
                           const int64_t* n_dev, int64_t n_max, int nbits, int pass0,
-                          const Layout& L, char* ws, cudaStream_t s) {
+                          const Layout& L, char* ws, cudaStream_t s, bool hist_done = false) {
   uint32_t* status[4] = {nullptr, nullptr, nullptr, nullptr};
   for (int p = 0; p < 4 && pass0 + p < kPassesMax; p++)
     status[p] = (uint32_t*)(ws + L.status[pass0 + p]);
   return onesweep_passes(k0, v0, k1, v1, n_dev, n_max, nbits,
                          (uint32_t*)(ws + L.ghist) + pass0 * kRadix,
-                         (uint32_t*)(ws + L.counters) + pass0, status, s);
+                         (uint32_t*)(ws + L.counters) + pass0, status, s, hist_done);
 }
 
 size_t sort_pairs_scratch(int64_t n) {
@@ -600,8 +661,8 @@ extern "C" lgs_status gs_bin_sort(const float* proj, const uint16_t* rect, int64
   // 1. (camera, Gaussian) items by depth, then stably by camera
   uint32_t *dk0 = U32(L.dk0), *dk1 = U32(L.dk1), *dv0 = U32(L.dv0), *dv1 = U32(L.dv1);
   depth_keys_kernel<<<grid_for(m), 256, 0, s>>>((const float4*)proj, (const ushort4*)rect, m,
-                                                dk0, dv0);
-  if (onesweep_sort(dk0, dv0, dk1, dv1, nullptr, m, 32, 0, L, ws, s)) {
+                                                dk0, dv0, hist_passes(32), U32(L.ghist));
+  if (onesweep_sort(dk0, dv0, dk1, dv1, nullptr, m, 32, 0, L, ws, s, true)) {
     std::swap(dk0, dk1);
     std::swap(dv0, dv1);
   }
@@ -631,8 +692,10 @@ extern "C" lgs_status gs_bin_sort(const float* proj, const uint16_t* rect, int64
   emit_kernel<<<(unsigned)std::max<int64_t>(1, (capacity + kEmitSlots - 1) / kEmitSlots),
                 kEmitThreads, 0, s>>>(order, (const ushort4*)rect, offs, U32(L.bstart), m,
                                       (uint32_t)n, tiles_x, tiles, (uint32_t)n_cams * tiles,
-                                      sort_n, tk0, tv0);
-  const bool flipped = onesweep_sort(tk0, tv0, tk1, tv1, sort_n, capacity, tbits, 5, L, ws, s);
+                                      sort_n, tk0, tv0, hist_passes(tbits),
+                                      U32(L.ghist) + 5 * kRadix);
+  const bool flipped =
+      onesweep_sort(tk0, tv0, tk1, tv1, sort_n, capacity, tbits, 5, L, ws, s, true);
   const uint32_t* tkey = flipped ? tk1 : tk0;
   // 4. per-tile ranges and (optionally) the 64-bit keys
   ranges_kernel<<<grid_for(capacity), 256, 0, s>>>(tkey, sort_n, (uint32_t)n_cams * tiles,

@@ -30,6 +30,9 @@ namespace lgs {
 constexpr int kOsThreads = 256;
 constexpr int kOsItems = 16;
 constexpr int kOsTile = kOsThreads * kOsItems;  // keys per onesweep tile
+// smaller tiles for short key sequences, so that a pass spreads over all SMs
+constexpr int kOsItemsSmall = 4;
+constexpr int64_t kOsSmallMax = 1 << 20;
 constexpr int kRadix = 256;
 constexpr uint32_t kFlagAgg = 1u << 30, kFlagInc = 2u << 30, kValMask = (1u << 30) - 1;
 constexpr uint64_t kFlag64Agg = 1ull << 62, kFlag64Inc = 2ull << 62,
@@ -234,6 +237,7 @@ static HistPasses hist_passes(int nbits) {
 
 // ------------------------------------------------------------------ onesweep pass
 
+template <int ITEMS>
 __global__ void __launch_bounds__(kOsThreads)
 onesweep_kernel(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin,
                 uint32_t* __restrict__ kout, uint32_t* __restrict__ vout, const int64_t* n_dev,
@@ -243,7 +247,7 @@ onesweep_kernel(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ v
   __shared__ uint32_t dstart[kRadix];
   __shared__ uint32_t goff[kRadix];
   __shared__ uint32_t wt[32];
-  __shared__ uint32_t sk[kOsTile], sv[kOsTile];
+  __shared__ uint32_t sk[(kOsThreads * ITEMS)], sv[(kOsThreads * ITEMS)];
   __shared__ uint32_t s_tile;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int i = threadIdx.x; i < (kOsThreads / 32) * kRadix; i += kOsThreads)
@@ -252,19 +256,19 @@ onesweep_kernel(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ v
   __syncthreads();
   const uint32_t tile = s_tile;
   const int64_t n = item_count(n_dev, n_host);
-  const int64_t blk0 = (int64_t)tile * kOsTile;
+  const int64_t blk0 = (int64_t)tile * (kOsThreads * ITEMS);
   if (blk0 >= n) return;
-  const int64_t base = blk0 + warp * (32 * kOsItems);
-  uint32_t key[kOsItems], val[kOsItems], rank[kOsItems];
+  const int64_t base = blk0 + warp * (32 * ITEMS);
+  uint32_t key[ITEMS], val[ITEMS], rank[ITEMS];
   const uint32_t lt = lanemask_lt();
 #pragma unroll
-  for (int r = 0; r < kOsItems; r++) {  // all loads in flight before any ranking
+  for (int r = 0; r < ITEMS; r++) {  // all loads in flight before any ranking
     const int64_t idx = base + r * 32 + lane;
     key[r] = idx < n ? kin[idx] : 0u;
     val[r] = idx < n ? vin[idx] : 0u;
   }
 #pragma unroll
-  for (int r = 0; r < kOsItems; r++) {
+  for (int r = 0; r < ITEMS; r++) {
     const int64_t idx = base + r * 32 + lane;
     const bool valid = idx < n;
     const uint32_t d = valid ? (key[r] >> shift) & mask : (uint32_t)(kRadix + lane);
@@ -300,7 +304,7 @@ onesweep_kernel(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ v
   goff[d] = gbase + prefix;
   __syncthreads();
 #pragma unroll
-  for (int r = 0; r < kOsItems; r++) {
+  for (int r = 0; r < ITEMS; r++) {
     const int64_t idx = base + r * 32 + lane;
     if (idx < n) {
       const uint32_t dd = (key[r] >> shift) & mask;
@@ -310,7 +314,7 @@ onesweep_kernel(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ v
     }
   }
   __syncthreads();
-  const int m = (int)((n - blk0) < (int64_t)kOsTile ? (n - blk0) : (int64_t)kOsTile);
+  const int m = (int)((n - blk0) < (int64_t)(kOsThreads * ITEMS) ? (n - blk0) : (int64_t)(kOsThreads * ITEMS));
   for (int j = threadIdx.x; j < m; j += kOsThreads) {
     const uint32_t k = sk[j];
     const uint32_t dd = (k >> shift) & mask;
@@ -524,6 +528,12 @@ __global__ void keys_kernel(const uint32_t* __restrict__ tkey, const uint32_t* _
 
 static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 static int64_t tiles_of(int64_t n) { return (n + kOsTile - 1) / kOsTile; }
+// keys per onesweep tile for a sort of at most n_max keys, and the tile count
+static int os_items(int64_t n_max) { return n_max <= kOsSmallMax ? kOsItemsSmall : kOsItems; }
+static int64_t os_tiles(int64_t n_max) {
+  const int64_t t = (int64_t)kOsThreads * os_items(n_max);
+  return std::max<int64_t>(1, (n_max + t - 1) / t);
+}
 
 struct Layout {
   size_t dk0, dk1, dv0, dv1, offs, bstart, tk0, tk1, tv;
@@ -544,7 +554,7 @@ static Layout layout(int64_t n, int n_cams, int64_t capacity) {
   L.ghist = take(4 * kPassesMax * kRadix);
   L.counters = take(4 * (kPassesMax + 1));
   for (int p = 0; p < kPassesMax; p++)
-    L.status[p] = take(4 * (size_t)kRadix * std::max<int64_t>(1, tiles_of(p < 5 ? m : capacity)));
+    L.status[p] = take(4 * (size_t)kRadix * os_tiles(p < 5 ? m : capacity));
   L.scan_status = take(8 * std::max<int64_t>(1, tiles_of(m)));
   L.scal = take(8 * 4);
   L.zero_end = o;
@@ -566,15 +576,21 @@ static bool onesweep_passes(uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t* 
                             bool hist_done = false) {
   const int npass = (nbits + 7) / 8;
   const HistPasses hp = hist_passes(nbits);
-  const int64_t ntile = std::max<int64_t>(1, tiles_of(n_max));
+  const int64_t ntile = os_tiles(n_max);
   if (!hist_done)  // else the producer of the keys has filled ghist
     hist_kernel<<<(unsigned)std::min<int64_t>(ntile * 2, 152 * 4), 256, 0, s>>>(k0, n_dev, n_max,
                                                                              hp, ghist);
+  const bool small = os_items(n_max) == kOsItemsSmall;
   bool flipped = false;
   for (int p = 0; p < npass; p++) {
-    onesweep_kernel<<<(unsigned)ntile, kOsThreads, 0, s>>>(
-        k0, v0, k1, v1, n_dev, n_max, hp.shift[p], hp.mask[p], ghist + p * kRadix, status[p],
-        counters + p);
+    if (small)
+      onesweep_kernel<kOsItemsSmall><<<(unsigned)ntile, kOsThreads, 0, s>>>(
+          k0, v0, k1, v1, n_dev, n_max, hp.shift[p], hp.mask[p], ghist + p * kRadix, status[p],
+          counters + p);
+    else
+      onesweep_kernel<kOsItems><<<(unsigned)ntile, kOsThreads, 0, s>>>(
+          k0, v0, k1, v1, n_dev, n_max, hp.shift[p], hp.mask[p], ghist + p * kRadix, status[p],
+          counters + p);
     std::swap(k0, k1);
     std::swap(v0, v1);
     flipped = !flipped;
@@ -594,14 +610,14 @@ static bool onesweep_sort(uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t* v1
 }
 
 size_t sort_pairs_scratch(int64_t n) {
-  const size_t per = align256(4 * (size_t)kRadix * std::max<int64_t>(1, tiles_of(n)));
+  const size_t per = align256(4 * (size_t)kRadix * os_tiles(n));
   return align256(4 * 4 * kRadix) + align256(4 * 4) + 4 * per;
 }
 
 bool sort_pairs(uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t* v1, int64_t n, int nbits,
                 void* scratch, cudaStream_t s) {
   char* ws = (char*)scratch;
-  const size_t per = align256(4 * (size_t)kRadix * std::max<int64_t>(1, tiles_of(n)));
+  const size_t per = align256(4 * (size_t)kRadix * os_tiles(n));
   uint32_t* ghist = (uint32_t*)ws;
   uint32_t* counters = (uint32_t*)(ws + align256(4 * 4 * kRadix));
   char* st0 = ws + align256(4 * 4 * kRadix) + align256(4 * 4);

@@ -16,6 +16,8 @@ Contents
   Eq. 4) with the geometric criteria, by brute-force neighbour search; its
   mask decisions are taken in FP32 with a fixed operation order (they turn
   float comparisons into bits), everything else here is float64.
+* ``ssim.py``: the D-SSIM term of the photometric loss (Sec. III-B.3) in
+  numpy float64.
 * ``ae.py``: the scene-adaptive autoencoder (Sec. III-B.3 Eq. 2, Sec. III-B.4
   Eq. 3, Sec. IV-A.2 pretraining) in numpy float64.
 * ``losses``: the L1 terms of Eq. 1.
@@ -70,6 +72,7 @@ def _load():
     lib.lgso_bin_count.restype = I64
     lib.lgso_bin_sort.argtypes = [I64, I32, I32, I32, P, P, P, P, P]
     lib.lgso_num_threads.restype = I32
+    lib.lgso_pose_grad.argtypes = [I64, P, P, P, P, P, P, P]
     F32 = ctypes.c_float
     lib.lgso_prune.argtypes = [I64, I32, P, P, P, P, I32, F32, F32, F32, F32, P]
     lib.lgso_prune_sample.argtypes = [I64, I32, P, P, P, P, I32, F32, F32, F32, F32, P, I64, P]
@@ -169,6 +172,20 @@ def render_backward(scene, cam, g_rgb, g_depth, g_feat, bg=(0.0, 0.0, 0.0), crop
                         _ptr(gr), _ptr(gd), _ptr(gf), _ptr(out["means"]), _ptr(out["quats"]),
                         _ptr(out["log_scales"]), _ptr(out["opacity_logits"]),
                         _ptr(out["colors"]), _ptr(out["feats"]), _ptr(out["proj"]))
+    return out
+
+
+def pose_grad(scene, cam, dproj) -> np.ndarray:
+    """Gradient (6,) of the loss w.r.t. a left perturbation exp(xi^) of the
+    camera's world->camera transform, xi = (rho, phi), from the per-Gaussian
+    2D gradients ``dproj`` [N,7] of this camera (render_backward's ``proj``)."""
+    lib = _load()
+    n = scene.means.shape[0]
+    out = np.zeros(6)
+    dp = _f64(dproj)
+    lib.lgso_pose_grad(n, _ptr(_f64(scene.means)), _ptr(_f64(scene.quats)),
+                       _ptr(_f64(scene.log_scales)), _ptr(_f64(scene.opacity_logits)),
+                       _ptr(camera_array(cam)), _ptr(dp), _ptr(out))
     return out
 
 

@@ -328,17 +328,15 @@ static void atomic_add(double* p, double v) {
   *p += v;
 }
 
-/* Projection backward of one Gaussian for one camera.  dp7 = gradient w.r.t.
- * (u, v, conic a, conic b, conic c, opacity, depth t_z).  Accumulates into
- * the parameter gradients. */
-static void project_backward(const oproj* P, const ocam* cam, const double* dp7,
-                             double* dmean, double* dquat, double* dls, double* dlogit) {
-  double du = dp7[0], dv = dp7[1], da = dp7[2], db = dp7[3], dc = dp7[4], dop = dp7[5],
-         dz = dp7[6];
+/* The camera-space part of the projection backward of one Gaussian:
+ * dp7 = gradient w.r.t. (u, v, conic a, conic b, conic c, opacity, depth t_z)
+ * gives dS3 (world 3D covariance), dJ (the 2x3 Jacobian J of the EWA
+ * linearisation) and dt (the camera-space mean t). */
+static void camera_backward(const oproj* P, const ocam* cam, const double* dp7, double* dS3,
+                            double* dJ, double* dt) {
+  double du = dp7[0], dv = dp7[1], da = dp7[2], db = dp7[3], dc = dp7[4], dz = dp7[6];
   double tx = P->t[0], ty = P->t[1], tz = P->t[2];
   double fx = cam->fx, fy = cam->fy;
-  /* opacity = sigmoid(logit) */
-  *dlogit += dop * P->o * (1.0 - P->o);
   /* conic = Sigma2^-1: dSigma2 = -Q dQ Q with dQ symmetric (b shared by 01/10) */
   double Q[4] = {P->conic[0], P->conic[1], P->conic[1], P->conic[2]};
   double G[4] = {da, 0.5 * db, 0.5 * db, dc};
@@ -349,7 +347,7 @@ static void project_backward(const oproj* P, const ocam* cam, const double* dp7,
     for (int j = 0; j < 2; j++)
       dS2[2 * i + j] = -(QG[2 * i] * Q[j] + QG[2 * i + 1] * Q[2 + j]);
   /* Sigma2 = T Sigma3 T^T (+ const): dSigma3 = T^T dS2 T, dT = 2 dS2 T Sigma3 */
-  double dS3[9], dT[6], TS3[6];
+  double dT[6], TS3[6];
   for (int i = 0; i < 3; i++)
     for (int j = 0; j < 3; j++) {
       double acc = 0;
@@ -366,14 +364,13 @@ static void project_backward(const oproj* P, const ocam* cam, const double* dp7,
   for (int i = 0; i < 2; i++)
     for (int j = 0; j < 3; j++) dT[3 * i + j] = 2.0 * (dS2[2 * i] * TS3[j] + dS2[2 * i + 1] * TS3[3 + j]);
   /* T = J Rc: dJ = dT Rc^T */
-  double dJ[6];
   for (int i = 0; i < 2; i++)
     for (int j = 0; j < 3; j++) {
       double acc = 0;
       for (int k = 0; k < 3; k++) acc += dT[3 * i + k] * cam->R[3 * j + k];
       dJ[3 * i + j] = acc;
     }
-  double dt[3] = {0, 0, 0};
+  dt[0] = dt[1] = dt[2] = 0;
   /* J00 = fx/tz, J02 = -fx txc/tz^2 with txc = tx (inside) or lim*tz (clamped) */
   dt[2] += dJ[0] * (-fx / (tz * tz));
   dt[2] += dJ[2] * (2.0 * fx * P->txc / (tz * tz * tz));
@@ -389,6 +386,17 @@ static void project_backward(const oproj* P, const ocam* cam, const double* dp7,
   dt[1] += dv * fy / tz;
   dt[2] += -dv * fy * ty / (tz * tz);
   dt[2] += dz;
+}
+
+/* Projection backward of one Gaussian for one camera.  dp7 = gradient w.r.t.
+ * (u, v, conic a, conic b, conic c, opacity, depth t_z).  Accumulates into
+ * the parameter gradients. */
+static void project_backward(const oproj* P, const ocam* cam, const double* dp7,
+                             double* dmean, double* dquat, double* dls, double* dlogit) {
+  double dS3[9], dJ[6], dt[3];
+  camera_backward(P, cam, dp7, dS3, dJ, dt);
+  /* opacity = sigmoid(logit) */
+  *dlogit += dp7[5] * P->o * (1.0 - P->o);
   /* t = Rc p + tc */
   for (int j = 0; j < 3; j++)
     dmean[j] += cam->R[j] * dt[0] + cam->R[3 + j] * dt[1] + cam->R[6 + j] * dt[2];
@@ -579,4 +587,47 @@ int lgso_num_threads(void) {
 #else
   return 1;
 #endif
+}
+
+/* ---------------------------------------------------------------------- */
+/* camera pose gradient                                                     */
+
+/* Gradient of the loss with respect to a left perturbation of the camera's
+ * world->camera transform, T <- exp(xi^) T with xi = (rho, phi): the camera
+ * frame moves by rho and rotates by phi (the keyframe pose refinement of
+ * Sec. III-B.2 optimises this).  Under it t' = t + phi x t + rho and the
+ * rotation in T = J Rc becomes (I + phi^) Rc, so per Gaussian
+ *   dL/drho += dL/dt,   dL/dphi += t x dL/dt + vee(A^T - A),
+ * A = J^T dJ... written out: with dT the gradient of T = J Rc,
+ * dL = tr(dT^T J phi^ Rc) gives dL/dphi_k = -sum_ab A_ab eps_abk for
+ * A = J^T dT Rc^T (= J^T dJ).  dproj [n,7] holds each Gaussian's gradient
+ * w.r.t. (u, v, a, b, c, opacity, t_z) for this camera (as returned by
+ * lgso_render_bwd).  out[6] = (dL/drho, dL/dphi). */
+int lgso_pose_grad(int64_t n, const double* means, const double* quats, const double* log_scales,
+                   const double* op_logits, const double* camv, const double* dproj,
+                   double* out) {
+  ocam cam = read_cam(camv);
+  for (int k = 0; k < 6; k++) out[k] = 0;
+  for (int64_t i = 0; i < n; i++) {
+    oproj P;
+    project_one(means + 3 * i, quats + 4 * i, log_scales + 3 * i, op_logits[i], &cam, &P);
+    if (!P.valid) continue;
+    const double* g = dproj + 7 * i;
+    int nz = 0;
+    for (int k = 0; k < 7; k++) nz |= g[k] != 0.0;
+    if (!nz) continue;
+    double dS3[9], dJ[6], dt[3];
+    camera_backward(&P, &cam, g, dS3, dJ, dt);
+    double A[9];
+    for (int a = 0; a < 3; a++)
+      for (int b = 0; b < 3; b++) A[3 * a + b] = P.J[a] * dJ[b] + P.J[3 + a] * dJ[3 + b];
+    const double* t = P.t;
+    out[0] += dt[0];
+    out[1] += dt[1];
+    out[2] += dt[2];
+    out[3] += t[1] * dt[2] - t[2] * dt[1] + A[7] - A[5];
+    out[4] += t[2] * dt[0] - t[0] * dt[2] + A[2] - A[6];
+    out[5] += t[0] * dt[1] - t[1] * dt[0] + A[3] - A[1];
+  }
+  return 0;
 }

@@ -377,6 +377,38 @@ lgs_status gs_compact_index(const uint8_t* mask, int64_t n, uint32_t* new_index,
 lgs_status gs_gather_rows(const void* src, int64_t n, int row_bytes, const uint32_t* new_index,
                           void* dst, void* stream);
 
+/* ------------------------------------------------------------------------
+ * lgs_dssim_loss -- the D-SSIM term of the photometric loss L_rgb
+ * (Sec. III-B.3, Eq. 1: L_rgb combines an L1 and a D-SSIM term).  The paper
+ * gives no SSIM parameters; these are the standard ones: per colour channel,
+ * an 11 x 11 Gaussian window of sigma 1.5 (normalised), images zero outside
+ * their borders, C1 = 0.01^2, C2 = 0.03^2.
+ * loss_dev (device float) += weight * (1 - mean SSIM(pred, target)) over all
+ * pixels and channels; grad += its gradient w.r.t. pred (accumulated, so an
+ * L1 term can share the buffer).  pred, target, grad: [n_img, H, W, 3] fp32.
+ * workspace: lgs_dssim_workspace(...) bytes of device scratch (4-byte
+ * aligned).  The standard L_rgb = 0.8 L1 + 0.2 D-SSIM is lgs_l1_loss with
+ * weight 0.8 and this call with weight 0.2 on the same grad.
+ * ---------------------------------------------------------------------- */
+size_t lgs_dssim_workspace(int n_img, int height, int width);
+lgs_status lgs_dssim_loss(const float* pred, const float* target, int n_img, int height,
+                          int width, float weight, float* grad, float* loss_dev, void* workspace,
+                          size_t workspace_bytes, void* stream);
+
+/* ------------------------------------------------------------------------
+ * gs_pose_grad -- camera pose gradient for the keyframe pose refinement of
+ * Sec. III-B.2 (the pose is refined by minimising the render loss).
+ * d_pose [n_cams, 6] fp32 out (overwritten): the gradient w.r.t. a left
+ * perturbation T <- exp(xi^) T of each camera's world->camera transform,
+ * xi = (rho, phi): rho translates the camera frame, phi rotates it (so a
+ * camera-space mean t moves to t + phi x t + rho).  grad2d: the
+ * per-(camera, Gaussian) 2D gradient records that gs_render_bwd wrote
+ * ([n_cams*n, 8] fp32, 16-byte aligned); the other inputs as for gs_project.
+ * ---------------------------------------------------------------------- */
+lgs_status gs_pose_grad(const float* means, const float* quats, const float* log_scales,
+                        const float* opacity_logits, int64_t n, const lgs_camera* cams_host,
+                        int n_cams, const float* grad2d, float* d_pose, void* stream);
+
 /* Reads and clears the device error word that kernels with bounded waits
  * set when a wait gives up (0 = none).  Synchronises the device. */
 lgs_status lgs_device_error(int* code);

@@ -147,13 +147,17 @@ __global__ void project_kernel(const float* __restrict__ means, const float4* __
 
 // Chain rule from the 2D gradients g7 = d(u, v, a, b, c, o, tz) of one
 // (camera, Gaussian) to the parameters (accumulated into the outputs).
-__device__ void project_backward(const ProjState& P, const lgs_camera& cam, const float* g7,
-                                 float* dmean, float* dquat, float* dls, float& dlogit) {
-  float du = g7[0], dv = g7[1], da = g7[2], db = g7[3], dc = g7[4], dop = g7[5], dz = g7[6];
+// The camera-space part of the projection backward: from the 2D gradient
+// record g7 = d(u, v, a, b, c, o, t_z) to dS3 (world 3D covariance), dJ (the
+// full 2x3 gradient of the EWA Jacobian J, row-major) and dt (camera-space
+// mean).
+__device__ __forceinline__ void camera_backward(const ProjState& P, const lgs_camera& cam,
+                                                const float* g7, float* dS3, float* dJ,
+                                                float& dt0, float& dt1, float& dt2) {
+  float du = g7[0], dv = g7[1], da = g7[2], db = g7[3], dc = g7[4], dz = g7[6];
   float tx = P.t[0], ty = P.t[1], tz = P.t[2];
   float fx = cam.fx, fy = cam.fy;
   const float* V = cam.viewmat;
-  dlogit += dop * P.o * (1.f - P.o);
   // conic = Sigma2^-1: dSigma2 = -Q G Q, G = [[da, db/2], [db/2, dc]]
   float Q00 = P.conic[0], Q01 = P.conic[1], Q11 = P.conic[2];
   float G01 = 0.5f * db;
@@ -164,7 +168,6 @@ __device__ void project_backward(const ProjState& P, const lgs_camera& cam, cons
   float dS11 = -(QG10 * Q01 + QG11 * Q11);
   // Sigma2 = T Sigma3 T^T: dSigma3 = T^T dS T, dT = 2 dS T Sigma3
   const float* T = P.T2;
-  float dS3[9];
 #pragma unroll
   for (int i = 0; i < 3; i++)
 #pragma unroll
@@ -183,13 +186,18 @@ __device__ void project_backward(const ProjState& P, const lgs_camera& cam, cons
     dT[j] = 2.f * (dS00 * TS[j] + dS01 * TS[3 + j]);
     dT[3 + j] = 2.f * (dS01 * TS[j] + dS11 * TS[3 + j]);
   }
-  // T = J R_c: dJ = dT R_c^T (only the non-zero entries of J matter)
-  float dJ00 = dT[0] * V[0] + dT[1] * V[1] + dT[2] * V[2];
-  float dJ02 = dT[0] * V[8] + dT[1] * V[9] + dT[2] * V[10];
-  float dJ11 = dT[3] * V[4] + dT[4] * V[5] + dT[5] * V[6];
-  float dJ12 = dT[3] * V[8] + dT[4] * V[9] + dT[5] * V[10];
+  // T = J R_c: dJ = dT R_c^T
+#pragma unroll
+  for (int k = 0; k < 2; k++)
+#pragma unroll
+    for (int b = 0; b < 3; b++)
+      dJ[3 * k + b] = dT[3 * k] * V[4 * b] + dT[3 * k + 1] * V[4 * b + 1] +
+                      dT[3 * k + 2] * V[4 * b + 2];
+  const float dJ00 = dJ[0], dJ02 = dJ[2], dJ11 = dJ[4], dJ12 = dJ[5];
   float itz = 1.f / tz, itz2 = itz * itz;
-  float dt0 = 0.f, dt1 = 0.f, dt2 = 0.f;
+  dt0 = 0.f;
+  dt1 = 0.f;
+  dt2 = 0.f;
   dt2 += -dJ00 * fx * itz2 + dJ02 * 2.f * fx * P.txc * itz2 * itz;
   if (P.clampx) dt2 += -dJ02 * fx * P.limx * itz2;
   else dt0 += -dJ02 * fx * itz2;
@@ -200,6 +208,14 @@ __device__ void project_backward(const ProjState& P, const lgs_camera& cam, cons
   dt0 += du * fx * itz;
   dt1 += dv * fy * itz;
   dt2 += -(du * fx * tx + dv * fy * ty) * itz2 + dz;
+}
+
+__device__ void project_backward(const ProjState& P, const lgs_camera& cam, const float* g7,
+                                 float* dmean, float* dquat, float* dls, float& dlogit) {
+  const float* V = cam.viewmat;
+  float dS3[9], dJ[6], dt0, dt1, dt2;
+  camera_backward(P, cam, g7, dS3, dJ, dt0, dt1, dt2);
+  dlogit += g7[5] * P.o * (1.f - P.o);
   // t = R_c p + t_c
 #pragma unroll
   for (int j = 0; j < 3; j++) dmean[j] += V[j] * dt0 + V[4 + j] * dt1 + V[8 + j] * dt2;
@@ -287,6 +303,66 @@ lgs_status launch_project_bwd(const float* means, const float* quats, const floa
   return LGS_OK;
 }
 
+// Camera pose gradient: a left perturbation T <- exp(xi^) T of camera c's
+// world->camera transform, xi = (rho, phi), moves each camera-space mean to
+// t + phi x t + rho and turns J R_c into J (I + phi^) R_c, so per Gaussian
+// dL/drho += dL/dt and dL/dphi += t x dL/dt + (A21 - A12, A02 - A20, A10 - A01)
+// with A = J^T dJ.  One thread per (Gaussian, camera); a block sums its six
+// values and adds them to d_pose[c] once.
+__global__ void __launch_bounds__(256)
+pose_grad_kernel(const float* __restrict__ means, const float4* __restrict__ quats,
+                 const float* __restrict__ log_scales, const float* __restrict__ logits,
+                 int64_t n, CamBlock cams, const float4* __restrict__ grad2d,
+                 float* __restrict__ d_pose) {
+  __shared__ float red[8][6];
+  const int c = blockIdx.y;
+  const lgs_camera& cam = cams.cam[c];
+  float acc[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t k = (int64_t)c * n + i;
+    const float4 g0 = grad2d[2 * k], g1 = grad2d[2 * k + 1];
+    if (g0.x == 0.f && g0.y == 0.f && g0.z == 0.f && g0.w == 0.f && g1.x == 0.f &&
+        g1.y == 0.f && g1.z == 0.f)
+      continue;
+    const float p[3] = {means[3 * i], means[3 * i + 1], means[3 * i + 2]};
+    const float ls[3] = {log_scales[3 * i], log_scales[3 * i + 1], log_scales[3 * i + 2]};
+    ProjState P;
+    project_state(p, quats[i], ls, logits[i], cam, P);
+    if (!P.valid) continue;
+    const float g7[7] = {g0.x, g0.y, g0.z, g0.w, g1.x, g1.y, g1.z};
+    float dS3[9], dJ[6], dt0, dt1, dt2;
+    camera_backward(P, cam, g7, dS3, dJ, dt0, dt1, dt2);
+    const float tz = P.t[2], itz = 1.f / tz;
+    const float J00 = cam.fx * itz, J02 = -cam.fx * P.txc * itz * itz;
+    const float J11 = cam.fy * itz, J12 = -cam.fy * P.tyc * itz * itz;
+    const float A01 = J00 * dJ[1], A02 = J00 * dJ[2];
+    const float A10 = J11 * dJ[3], A12 = J11 * dJ[5];
+    const float A20 = J02 * dJ[0] + J12 * dJ[3], A21 = J02 * dJ[1] + J12 * dJ[4];
+    const float tx = P.t[0], ty = P.t[1];
+    acc[0] += dt0;
+    acc[1] += dt1;
+    acc[2] += dt2;
+    acc[3] += ty * dt2 - tz * dt1 + A21 - A12;
+    acc[4] += tz * dt0 - tx * dt2 + A02 - A20;
+    acc[5] += tx * dt1 - ty * dt0 + A10 - A01;
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int j = 0; j < 6; j++) {
+    float v = acc[j];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) red[warp][j] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < 6) {
+    float v = 0.f;
+    for (int w = 0; w < 8; w++) v += red[w][threadIdx.x];
+    if (v != 0.f) atomicAdd(d_pose + 6 * c + threadIdx.x, v);
+  }
+}
+
 lgs_status fill_cams(const lgs_camera* cams_host, int n_cams, CamBlock& cb) {
   LGS_CHECK_ARG(cams_host != nullptr, "cams_host is null");
   LGS_CHECK_ARG(n_cams >= 1 && n_cams <= LGS_MAX_CAMS, "n_cams out of range");
@@ -321,6 +397,28 @@ extern "C" lgs_status gs_project(const float* means, const float* quats, const f
   project_kernel<<<grid, 256, 0, as_stream(stream)>>>(means, (const float4*)quats, log_scales,
                                                       opacity_logits, n, cb, (float4*)proj,
                                                       (ushort4*)rect);
+  LGS_CHECK_LAUNCH();
+  return LGS_OK;
+}
+
+extern "C" lgs_status gs_pose_grad(const float* means, const float* quats, const float* log_scales,
+                                   const float* opacity_logits, int64_t n,
+                                   const lgs_camera* cams_host, int n_cams, const float* grad2d,
+                                   float* d_pose, void* stream) {
+  clear_error();
+  LGS_CHECK_ARG(n >= 0 && n < (int64_t)1 << 32, "n out of range");
+  CamBlock cb;
+  lgs_status st = fill_cams(cams_host, n_cams, cb);
+  if (st != LGS_OK) return st;
+  LGS_CHECK_ARG(d_pose, "d_pose is null");
+  cudaStream_t s = as_stream(stream);
+  LGS_CHECK_CUDA(cudaMemsetAsync(d_pose, 0, sizeof(float) * 6 * (size_t)n_cams, s));
+  if (n == 0) return LGS_OK;
+  LGS_CHECK_ARG(means && quats && log_scales && opacity_logits && grad2d, "null pointer");
+  LGS_CHECK_ARG(aligned(quats, 16) && aligned(grad2d, 16), "misaligned pointer");
+  dim3 grid((unsigned)std::min<int64_t>((n + 255) / 256, 152 * 4), n_cams);
+  pose_grad_kernel<<<grid, 256, 0, s>>>(means, (const float4*)quats, log_scales, opacity_logits,
+                                        n, cb, (const float4*)grad2d, d_pose);
   LGS_CHECK_LAUNCH();
   return LGS_OK;
 }

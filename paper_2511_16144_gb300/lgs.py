@@ -94,6 +94,9 @@ def load():
         "gs_compact_workspace": ([I64], SZ),
         "gs_compact_index": ([P, I64, P, P, P, SZ, P], I32),
         "gs_gather_rows": ([P, I64, I32, P, P, P], I32),
+        "lgs_dssim_workspace": ([I32, I32, I32], SZ),
+        "lgs_dssim_loss": ([P, P, I32, I32, I32, F, P, P, P, SZ, P], I32),
+        "gs_pose_grad": ([P, P, P, P, I64, P, I32, P, P, P], I32),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -109,7 +112,8 @@ def exported_symbols():
             "gs_render_fwd", "gs_render_bwd", "lgs_l1_loss", "ae_workspace_bytes", "ae_encode",
             "ae_decode", "ae_train_step", "ae_pack", "lgs_device_error", "lgs_graph_kernel_nodes", "lgs_zero",
             "gs_render_bwd_static_capacity", "gs_render_bwd_static", "gs_prune_workspace",
-            "gs_prune", "gs_compact_workspace", "gs_compact_index", "gs_gather_rows"]
+            "gs_prune", "gs_compact_workspace", "gs_compact_index", "gs_gather_rows",
+            "lgs_dssim_workspace", "lgs_dssim_loss", "gs_pose_grad"]
 
 
 def _check(status, what):
@@ -384,3 +388,27 @@ def gs_compact(mask, tensors):
         _check(L.gs_gather_rows(_p(t), n, row, _p(new_index), _p(dst), _stream()),
                "gs_gather_rows")
     return out, new_index
+
+
+def lgs_dssim_loss(pred, target, weight, grad, loss_dev, ws=None):
+    """loss_dev += weight (1 - mean SSIM(pred, target)); grad += its gradient.
+    pred / target / grad: [C, H, W, 3] float32 on the device."""
+    L = load()
+    c, h, w = int(pred.shape[0]), int(pred.shape[1]), int(pred.shape[2])
+    if ws is None:
+        ws = torch.empty(max(int(L.lgs_dssim_workspace(c, h, w)), 4), dtype=torch.uint8,
+                         device=pred.device)
+    _check(L.lgs_dssim_loss(_p(pred), _p(target), c, h, w, float(weight), _p(grad), _p(loss_dev),
+                            _p(ws), ws.numel(), _stream()), "lgs_dssim_loss")
+
+
+def gs_pose_grad(means, quats, log_scales, opacity_logits, cams, grad2d, d_pose=None):
+    """[n_cams, 6] gradient w.r.t. left se(3) perturbations (rho, phi) of each
+    camera's world->camera transform, from gs_render_bwd's 2D records."""
+    n = means.shape[0]
+    d_pose = (torch.empty((len(cams), 6), dtype=torch.float32, device=means.device)
+              if d_pose is None else d_pose)
+    _check(load().gs_pose_grad(_p(means), _p(quats), _p(log_scales), _p(opacity_logits), n,
+                               cameras(cams), len(cams), _p(grad2d), _p(d_pose), _stream()),
+           "gs_pose_grad")
+    return d_pose

@@ -305,6 +305,8 @@ def run_gpu(args, rank, world):
     # targets (RGB, depth, F_gt) go host -> device from pinned memory and the
     # loss comes back
     prune = measure_prune(s16_bf, flush)
+    extras = measure_loss_pose(step16, flush)
+    extras.update(measure_loop_query(step16, f_gt, flush))
 
     rgb_b, dep_b, fgt_b = rgb_t.clone(), dep_t.clone(), f_gt.clone()
     step16b = MappingStep(s16_bf, cams, rgb_b, dep_b, fgt_b, model=model,
@@ -332,7 +334,7 @@ def run_gpu(args, rank, world):
             "e2e": e2e,
             "clocks": clocks.summary(),
             "plain_512": plain, "decoded_cosine_error": cos_err, "variants": extra,
-            "prune": prune, "feature_dim_sweep": sweep,
+            "prune": prune, "feature_dim_sweep": sweep, "dssim_and_pose": extras,
             "per_call_ms": calls,
             "ae_pretrain": {"steps": args.ae_steps, "loss_first": ae_losses[0],
                             "loss_last": ae_losses[-1], "seconds": ae_train_s},
@@ -526,6 +528,116 @@ def measure_prune(scene, flush, reps=20):
                          "unit": "GB/s", "frac": achieved / float(peaks["hbm_gbs"]),
                          "traffic": None, "peak_source": kind + " copy",
                          "note": "61 B per Gaussian: the inputs the rule reads once, the mask byte"}}
+
+
+def measure_loss_pose(step, flush, reps=20):
+    """The D-SSIM term of L_rgb (Sec. III-B.3) on the step's 640x480 render
+    and the camera pose gradient (Sec. III-B.2) from its backward's 2D
+    records, each alone in a CUDA graph between CUDA events (L2 flushed)."""
+    import torch
+    from paper_2511_16144_gb300 import lgs
+    step.run()
+    torch.cuda.synchronize()
+    rgb = step.out["rgb"]
+    grad = torch.zeros_like(rgb)
+    loss = torch.zeros(1, device=rgb.device)
+    ws = torch.empty(int(lgs.load().lgs_dssim_workspace(*rgb.shape[:3])), dtype=torch.uint8,
+                     device=rgb.device)
+    sc = step.scene
+    d_pose = torch.empty((len(step.cams), 6), device=rgb.device)
+
+    def dssim():
+        lgs.lgs_dssim_loss(rgb, step.rgb_t, 0.2, grad, loss, ws)
+
+    def pose():
+        lgs.gs_pose_grad(sc.means, sc.quats, sc.log_scales, sc.opacity_logits, step.cams,
+                         step.grad2d, d_pose)
+
+    out = {}
+    for name, fn in (("dssim_ms", dssim), ("pose_grad_ms", pose)):
+        fn()
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            fn()
+        ts = []
+        for _ in range(reps):
+            flush.fill_(1.0)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            g.replay()
+            b.record()
+            torch.cuda.synchronize()
+            ts.append(a.elapsed_time(b))
+        out[name] = float(np.median(ts))
+    px = rgb.shape[0] * rgb.shape[1] * rgb.shape[2]
+    # algorithmic bytes of D-SSIM: read pred and target, write and re-read the
+    # three gradient maps, read-modify-write the gradient (12 B per value each)
+    byts = px * 3 * 4 * (2 + 3 + 3 + 2)
+    peaks, kind = measured_peaks()
+    out["dssim_roofline"] = {"bound": "hbm", "achieved": byts / (out["dssim_ms"] / 1e3) / 1e9,
+                             "peak": float(peaks["hbm_gbs"]), "unit": "GB/s",
+                             "frac": byts / (out["dssim_ms"] / 1e3) / 1e9 / float(peaks["hbm_gbs"]),
+                             "peak_source": kind + " copy"}
+    return out
+
+
+def measure_loop_query(step, f_gt, flush, reps=20, K=256, Q=8):
+    """The keyframe's loop signature (Sec. III-D: closest of K codewords for
+    every 512-d F_gt pixel on the tensor cores, histogram) and the relevance
+    of Q compact-space queries (Sec. I) over the rendered 16-d map, each
+    alone in a CUDA graph between CUDA events (L2 flushed).  The codebook is
+    synthetic (unit codewords): the paper's comes from external datasets."""
+    import torch
+    from paper_2511_16144_gb300 import lgs
+    dev = f_gt.device
+    gen = torch.Generator(device=dev).manual_seed(4100)
+    cb = torch.randn((K, 512), device=dev, generator=gen)
+    cb = (cb / cb.norm(dim=1, keepdim=True)).bfloat16().contiguous()
+    hist = torch.zeros(K, dtype=torch.int32, device=dev)
+    ws = torch.empty(int(lgs.load().lgs_codebook_workspace(K)), dtype=torch.uint8, device=dev)
+    feat = step.out["feat"].reshape(-1, step.D)
+    q = torch.randn((Q, step.D), device=dev, generator=gen)
+    rel = torch.empty((feat.shape[0], Q), device=dev)
+
+    def assign():
+        lgs.lgs_codebook_assign(f_gt, cb, hist=hist, ws=ws)
+
+    def query():
+        lgs.gs_query_relevance(feat, q, rel)
+
+    out = {}
+    for name, fn in (("codebook_assign_ms", assign), ("query_relevance_ms", query)):
+        fn()
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            fn()
+        ts = []
+        for _ in range(reps):
+            flush.fill_(1.0)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            g.replay()
+            b.record()
+            torch.cuda.synchronize()
+            ts.append(a.elapsed_time(b))
+        out[name] = float(np.median(ts))
+    peaks, kind = measured_peaks()
+    P = f_gt.shape[0]
+    fl = 2.0 * P * 512 * K
+    out["codebook_assign_roofline"] = {
+        "bound": "tensor", "achieved": fl / (out["codebook_assign_ms"] / 1e3) / 1e12,
+        "peak": float(peaks["bf16_tflops"]), "unit": "TFLOP/s",
+        "frac": fl / (out["codebook_assign_ms"] / 1e3) / 1e12 / float(peaks["bf16_tflops"]),
+        "peak_source": kind + " bf16 burst", "codebook": K}
+    byts = float(feat.numel() * 4 + P * Q * 4)
+    out["query_relevance_roofline"] = {
+        "bound": "hbm", "achieved": byts / (out["query_relevance_ms"] / 1e3) / 1e9,
+        "peak": float(peaks["hbm_gbs"]), "unit": "GB/s",
+        "frac": byts / (out["query_relevance_ms"] / 1e3) / 1e9 / float(peaks["hbm_gbs"]),
+        "peak_source": kind + " copy", "queries": Q}
+    return out
 
 
 def measure_e2e(steps, graphs, k, warm):

@@ -409,6 +409,41 @@ lgs_status gs_pose_grad(const float* means, const float* quats, const float* log
                         const float* opacity_logits, int64_t n, const lgs_camera* cams_host,
                         int n_cams, const float* grad2d, float* d_pose, void* stream);
 
+/* ------------------------------------------------------------------------
+ * Language loop signature (Sec. III-D) and compact-space queries (Sec. I).
+ *
+ * lgs_codebook_assign: every row of x (bf16 [P, D], the keyframe's language
+ * features; D = 16 or a multiple of 64) goes to its closest codeword of
+ * codebook (bf16 [K, D], K in {16, 64, 128, 256, 512}) in Euclidean distance,
+ * decided as argmin_k (|c_k|^2 - 2 x.c_k) with FP32 accumulation of the BF16
+ * products on the tensor cores (ties to the lower index; two codewords whose
+ * scores differ by less than that arithmetic's rounding may swap).
+ * assign_opt [P] uint32 out or NULL; hist [K] uint32 += the counts (the
+ * keyframe signature before normalisation).  workspace:
+ * lgs_codebook_workspace(K) bytes, 4-byte aligned.
+ * lgs_hist_cosine: out[m] = cos(hist, hists[m]) for M stored histograms
+ * ([M, K] uint32); 0 for an empty histogram.
+ * lgs_loop_candidates: out[0..top) = the indices m of past keyframes with
+ * sim[m] > tau_hist and |centres[m] - cur| < radius (centres [M, 3] fp32,
+ * cur on the host), most similar first, ties to the lower index, -1 padding;
+ * top in [1, 8] (the paper verifies the top two).
+ * gs_query_relevance: out [M, Q] fp32 = cos(feats[m], queries[q]) for
+ * features [M, D] (fp32 or bf16, D <= 64: a rendered compact feature map or
+ * the Gaussians' features) and queries [Q, D] fp32 already projected into the
+ * compact space (ae_encode of the text embedding), Q <= 64; 0 for a zero norm.
+ * ---------------------------------------------------------------------- */
+size_t lgs_codebook_workspace(int K);
+lgs_status lgs_codebook_assign(const uint16_t* x, int64_t P, int D, const uint16_t* codebook,
+                               int K, uint32_t* assign_opt, uint32_t* hist, void* workspace,
+                               size_t workspace_bytes, void* stream);
+lgs_status lgs_hist_cosine(const uint32_t* hist, const uint32_t* hists, int M, int K, float* out,
+                           void* stream);
+lgs_status lgs_loop_candidates(const float* sim, const float* centres, int M,
+                               const float* cur_centre_host, float tau_hist, float radius, int top,
+                               int* out, void* stream);
+lgs_status gs_query_relevance(const void* feats, int feat_dtype, int64_t M, int D,
+                              const float* queries, int Q, float* out, void* stream);
+
 /* Reads and clears the device error word that kernels with bounded waits
  * set when a wait gives up (0 = none).  Synchronises the device. */
 lgs_status lgs_device_error(int* code);

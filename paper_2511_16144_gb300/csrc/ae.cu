@@ -45,7 +45,8 @@ enum Epi : int {
   EPI_DX_BF16 = 5,   // out = acc (bf16)
   EPI_L1_BF16T = 6,  // y = acc + b; loss += s|y - t|; out = s sign(y - t) (bf16); t bf16
   EPI_L1_F32T = 7,   // same with an f32 target
-  EPI_RECON = 8      // y = acc + b vs x: loss += s (mean (y-x)^2 + 1 - cos); out = dL/dy
+  EPI_RECON = 8,     // y = acc + b vs x: loss += s (mean (y-x)^2 + 1 - cos); out = dL/dy
+  EPI_ARGMIN = 9     // closest codeword: argmin_n (b_n - 2 acc_n) -> out_u32, hist[n] += 1
 };
 
 struct LayerArgs {
@@ -63,6 +64,8 @@ struct LayerArgs {
   const void* target;
   float scale;
   float* loss;
+  uint32_t* out_u32;
+  uint32_t* hist;
 };
 
 __device__ __forceinline__ float gelu_f(float x) { return gelu_tanh(x); }
@@ -206,7 +209,28 @@ __global__ void __launch_bounds__(128, 1) layer_kernel(LayerArgs a) {
     const uint32_t tb = tmem + ((uint32_t)(warp * 32) << 16);
     constexpr int CW = NT < 32 ? 16 : 32;
     float lsum = 0.f;
-    if (a.epi == EPI_RECON) {
+    if (a.epi == EPI_ARGMIN) {
+      // |x - c_n|^2 - |x|^2 = |c_n|^2 - 2 x.c_n with |c_n|^2 in the bias;
+      // columns in increasing order, strict < keeps the lower index on ties
+      float best = INFINITY;
+      uint32_t bi = 0;
+      for (int c0 = 0; c0 < NT; c0 += CW) {
+        float v[32];
+        if (CW == 32) tc::tmem_ld32(tb + c0, v);
+        else tc::tmem_ld16(tb + c0, v);
+#pragma unroll
+        for (int i = 0; i < CW; i++) {
+          const float sc = fmaf(-2.f, v[i], a.bias[n0 + c0 + i]);
+          if (sc < best) {
+            best = sc;
+            bi = (uint32_t)(n0 + c0 + i);
+          }
+        }
+      }
+      if (valid && a.out_u32) a.out_u32[p] = bi;
+      const uint32_t peers = __match_any_sync(0xffffffffu, valid ? bi : (0x80000000u | lane));
+      if (valid && a.hist && lane == __ffs(peers) - 1) atomicAdd(a.hist + bi, (uint32_t)__popc(peers));
+    } else if (a.epi == EPI_RECON) {
       // pass 1: row statistics of y against x = target
       float sdd = 0.f, syx = 0.f, syy = 0.f, sxx = 0.f;
       for (int c0 = 0; c0 < NT; c0 += CW) {
@@ -817,6 +841,56 @@ extern "C" lgs_status ae_train_step(lgs_ae_state* st_, const uint16_t* x, const 
     LGS_CHECK_LAUNCH();
   }
   return ae_pack(st_, 0, last, stream);
+}
+
+namespace lgs {
+namespace {
+// |c_n|^2 of every BF16 codeword, summed left to right in FP32.
+__global__ void codeword_norms_kernel(const __nv_bfloat16* __restrict__ cb, int K, int D,
+                                      float* __restrict__ out) {
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < K; k += gridDim.x * blockDim.x) {
+    float s = 0.f;
+    for (int j = 0; j < D; j++) {
+      const float v = __bfloat162float(cb[(int64_t)k * D + j]);
+      s = fmaf(v, v, s);
+    }
+    out[k] = s;
+  }
+}
+}  // namespace
+}  // namespace lgs
+
+extern "C" size_t lgs_codebook_workspace(int K) { return K > 0 ? 4 * (size_t)K : 0; }
+
+extern "C" lgs_status lgs_codebook_assign(const uint16_t* x, int64_t P, int D,
+                                          const uint16_t* codebook, int K, uint32_t* assign_opt,
+                                          uint32_t* hist, void* workspace, size_t workspace_bytes,
+                                          void* stream) {
+  clear_error();
+  LGS_CHECK_ARG(P >= 0 && P < ((int64_t)1 << 31), "P out of range");
+  LGS_CHECK_ARG(D == 16 || (D >= 64 && D % 64 == 0 && D <= 4096), "D must be 16 or a multiple of 64");
+  LGS_CHECK_ARG(K == 16 || K == 64 || K == 128 || K == 256 || K == 512,
+                "codebook size must be 16, 64, 128, 256 or 512");
+  LGS_CHECK_ARG(codebook && hist && workspace, "null pointer");
+  LGS_CHECK_ARG(P == 0 || x, "null pointer");
+  LGS_CHECK_ARG(aligned(x, 16) && aligned(codebook, 16) && aligned(workspace, 4),
+                "misaligned pointer");
+  LGS_CHECK_ARG(workspace_bytes >= lgs_codebook_workspace(K), "workspace too small");
+  if (P == 0) return LGS_OK;
+  cudaStream_t s = as_stream(stream);
+  float* cnorm = (float*)workspace;
+  codeword_norms_kernel<<<(K + 127) / 128, 128, 0, s>>>((const __nv_bfloat16*)codebook, K, D, cnorm);
+  LayerArgs a = {};
+  a.A = x;
+  a.W = (const __nv_bfloat16*)codebook;
+  a.bias = cnorm;
+  a.P = P;
+  a.K = D;
+  a.N = K;
+  a.epi = EPI_ARGMIN;
+  a.out_u32 = assign_opt;
+  a.hist = hist;
+  return launch_layer(a, s);
 }
 
 extern "C" lgs_status lgs_device_error(int* code) {

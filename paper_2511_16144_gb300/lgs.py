@@ -97,6 +97,11 @@ def load():
         "lgs_dssim_workspace": ([I32, I32, I32], SZ),
         "lgs_dssim_loss": ([P, P, I32, I32, I32, F, P, P, P, SZ, P], I32),
         "gs_pose_grad": ([P, P, P, P, I64, P, I32, P, P, P], I32),
+        "lgs_codebook_workspace": ([I32], SZ),
+        "lgs_codebook_assign": ([P, I64, I32, P, I32, P, P, P, SZ, P], I32),
+        "lgs_hist_cosine": ([P, P, I32, I32, P, P], I32),
+        "lgs_loop_candidates": ([P, P, I32, P, F, F, I32, P, P], I32),
+        "gs_query_relevance": ([P, I32, I64, I32, P, I32, P, P], I32),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -113,7 +118,9 @@ def exported_symbols():
             "ae_decode", "ae_train_step", "ae_pack", "lgs_device_error", "lgs_graph_kernel_nodes", "lgs_zero",
             "gs_render_bwd_static_capacity", "gs_render_bwd_static", "gs_prune_workspace",
             "gs_prune", "gs_compact_workspace", "gs_compact_index", "gs_gather_rows",
-            "lgs_dssim_workspace", "lgs_dssim_loss", "gs_pose_grad"]
+            "lgs_dssim_workspace", "lgs_dssim_loss", "gs_pose_grad", "lgs_codebook_workspace",
+            "lgs_codebook_assign", "lgs_hist_cosine", "lgs_loop_candidates",
+            "gs_query_relevance"]
 
 
 def _check(status, what):
@@ -412,3 +419,46 @@ def gs_pose_grad(means, quats, log_scales, opacity_logits, cams, grad2d, d_pose=
                                cameras(cams), len(cams), _p(grad2d), _p(d_pose), _stream()),
            "gs_pose_grad")
     return d_pose
+
+
+def lgs_codebook_assign(x, codebook, hist=None, assign=None, ws=None):
+    """Closest codeword per row of x (bf16 [P, D]); hist [K] uint32 += counts.
+    Returns (assign int32 [P] or None, hist)."""
+    L = load()
+    P, D = x.shape
+    K = codebook.shape[0]
+    dev = x.device
+    hist = torch.zeros(K, dtype=torch.int32, device=dev) if hist is None else hist
+    if ws is None:
+        ws = torch.empty(max(int(L.lgs_codebook_workspace(K)), 4), dtype=torch.uint8, device=dev)
+    _check(L.lgs_codebook_assign(_p(x), P, D, _p(codebook), K, _p(assign), _p(hist), _p(ws),
+                                 ws.numel(), _stream()), "lgs_codebook_assign")
+    return assign, hist
+
+
+def lgs_hist_cosine(hist, hists, out=None):
+    M, K = hists.shape
+    out = torch.empty(M, dtype=torch.float32, device=hists.device) if out is None else out
+    _check(load().lgs_hist_cosine(_p(hist), _p(hists), M, K, _p(out), _stream()),
+           "lgs_hist_cosine")
+    return out
+
+
+def lgs_loop_candidates(sim, centres, cur_centre, tau_hist, radius, top=2, out=None):
+    out = torch.empty(top, dtype=torch.int32, device=sim.device) if out is None else out
+    cur = (ctypes.c_float * 3)(*[float(v) for v in cur_centre])
+    _check(load().lgs_loop_candidates(_p(sim), _p(centres), sim.shape[0], cur, float(tau_hist),
+                                      float(radius), top, _p(out), _stream()),
+           "lgs_loop_candidates")
+    return out
+
+
+def gs_query_relevance(feats, queries, out=None):
+    """[M, Q] cosine of every feature row (fp32/bf16 [M, D]) with every
+    compact-space query (fp32 [Q, D])."""
+    M, D = feats.shape
+    Q = queries.shape[0]
+    out = torch.empty((M, Q), dtype=torch.float32, device=feats.device) if out is None else out
+    _check(load().gs_query_relevance(_p(feats), _dtype_code(feats), M, D, _p(queries), Q, _p(out),
+                                     _stream()), "gs_query_relevance")
+    return out

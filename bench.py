@@ -402,8 +402,8 @@ def per_call_times(step, flush, reps=5):
 # ncu DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) per launch
 # of each call group at this workload, from the capture summarised under
 # profiles/; None once the kernel has changed since the capture.
-TRAFFIC = {"gs_project": 13217024, "gs_bin_sort": 71693568, "gs_render_fwd": 3313152,
-           "l1_losses": 9844992, "ae_decode": 350261248, "gs_render_bwd": 41910528}
+TRAFFIC = {"gs_project": 13217024, "gs_bin_sort": 64159488, "gs_render_fwd": 3313664,
+           "l1_losses": 9845504, "ae_decode": 350672384, "gs_render_bwd": 41831680}
 
 
 def rooflines(step, calls):

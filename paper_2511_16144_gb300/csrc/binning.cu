@@ -1,0 +1,490 @@
+// 16x16 tile binning: every (camera, Gaussian) item emits one instance per
+// tile its support rect covers, and each tile's instances are ordered by
+// depth, ties by Gaussian index -- the front-to-back order alpha compositing
+// needs (LEGO-SLAM Sec. III-B.1, the standard 3DGS pipeline).  The result is
+// the same as a stable sort of the keys ((camera * tiles + tile) << 32) |
+// bits(depth) in emission order.
+//
+// Because every tile's segment can be sorted on its own, there is no global
+// sort:
+//   1. count the instances of every tile (shared-memory histograms per
+//      block of contiguous items when the tiles fit, else global atomics)
+//      and the total K;
+//   2. one block scans the counts into segment starts, writes the ranges and
+//      the write cursors (all ranges stay (0, 0) when K > capacity);
+//   3. every item appends (depth bits, index) to each of its tiles' segments
+//      (a block reserves one range per tile, then fills it with shared-
+//      memory atomics; the order inside a segment is arbitrary);
+//   4. one block per tile sorts its segment's 64-bit (depth bits, index)
+//      keys with a bitonic network -- in shared memory up to kSegMax keys,
+//      in a global scratch copy beyond -- and writes the Gaussian indices.
+// Depths are positive floats, so their bit patterns order like the values.
+#include <algorithm>
+
+#include "common.cuh"
+#include "kernels.cuh"
+
+namespace lgs {
+
+namespace {
+
+constexpr int kSegMax = 4096;          // keys a block sorts in shared memory
+constexpr int kSegThreads = 512;
+constexpr int kSmemTiles = 24576;      // per-block tile tables up to this many tiles
+constexpr int kItemBlocks = 2 * 152;   // blocks of the count and emit passes
+constexpr int kScanThreads = 1024;
+
+__device__ __forceinline__ bool rect_empty(const ushort4& r) { return r.z <= r.x || r.w <= r.y; }
+
+// Items of block b: a contiguous chunk, so a block's per-tile tables cover
+// few tiles densely.
+__device__ __forceinline__ void item_chunk(int64_t m, int64_t& i0, int64_t& i1) {
+  const int64_t per = (m + gridDim.x - 1) / gridDim.x;
+  i0 = (int64_t)blockIdx.x * per;
+  i1 = i0 + per < m ? i0 + per : m;
+}
+
+// 1. per-tile instance counts and K.
+__global__ void __launch_bounds__(256)
+tile_count_kernel(const ushort4* __restrict__ rect, int64_t m, uint32_t n, int tiles_x,
+                  uint32_t tiles, uint32_t n_tiles_all, uint32_t* __restrict__ counts,
+                  uint32_t* __restrict__ block_counts, unsigned long long* __restrict__ total) {
+  extern __shared__ uint32_t s_cnt[];  // n_tiles_all entries when they fit
+  const bool local = n_tiles_all <= (uint32_t)kSmemTiles;
+  if (local) {
+    for (uint32_t t = threadIdx.x; t < n_tiles_all; t += blockDim.x) s_cnt[t] = 0;
+    __syncthreads();
+  }
+  unsigned long long k = 0;
+  int64_t i0, i1;
+  item_chunk(m, i0, i1);
+  for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
+    const ushort4 r = rect[i];
+    if (rect_empty(r)) continue;
+    const uint32_t base = (uint32_t)(i / n) * tiles;
+    for (uint32_t y = r.y; y < r.w; y++)
+      for (uint32_t x = r.x; x < r.z; x++) {
+        const uint32_t t = base + y * (uint32_t)tiles_x + x;
+        if (local) atomicAdd(&s_cnt[t], 1u);
+        else atomicAdd(&counts[t], 1u);
+      }
+    k += (unsigned long long)(r.z - r.x) * (r.w - r.y);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) k += __shfl_xor_sync(0xffffffffu, k, o);
+  if ((threadIdx.x & 31) == 0 && k) atomicAdd(total, k);
+  if (local) {  // this block's column of the [tile][block] counts, and the totals
+    __syncthreads();
+    for (uint32_t t = threadIdx.x; t < n_tiles_all; t += blockDim.x) {
+      const uint32_t c = s_cnt[t];
+      block_counts[(size_t)t * gridDim.x + blockIdx.x] = c;
+      if (c) atomicAdd(&counts[t], c);
+    }
+  }
+}
+
+// 2. exclusive scan of the counts (one block): ranges, cursors, K.
+__global__ void __launch_bounds__(kScanThreads)
+tile_scan_kernel(const uint32_t* __restrict__ counts, uint32_t n_tiles_all,
+                 const unsigned long long* __restrict__ total, int64_t capacity,
+                 uint2* __restrict__ ranges, uint32_t* __restrict__ cursor,
+                 int64_t* __restrict__ n_instances, int64_t* __restrict__ sort_n) {
+  __shared__ uint32_t ws[32];
+  __shared__ uint32_t carry;
+  const int64_t K = (int64_t)*total;
+  const bool fits = K <= capacity;
+  if (threadIdx.x == 0) {
+    carry = 0;
+    *n_instances = K;
+    *sort_n = fits ? K : 0;
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (uint32_t c0 = 0; c0 < n_tiles_all; c0 += kScanThreads) {
+    const uint32_t t = c0 + threadIdx.x;
+    const uint32_t v = t < n_tiles_all ? counts[t] : 0u;
+    uint32_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane == 31) ws[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+      uint32_t w = ws[lane];
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, w, o);
+        if (lane >= o) w += y;
+      }
+      ws[lane] = w;
+    }
+    __syncthreads();
+    const uint32_t incl = carry + (warp > 0 ? ws[warp - 1] : 0u) + x;
+    if (t < n_tiles_all) {
+      const uint32_t start = incl - v;
+      ranges[t] = fits && v ? make_uint2(start, incl) : make_uint2(0u, 0u);
+      cursor[t] = start;
+    }
+    __syncthreads();
+    if (threadIdx.x == kScanThreads - 1) carry = incl;
+    __syncthreads();
+  }
+}
+
+// 2b. where each block's instances of each tile start: the tile's start plus
+// the counts of the blocks before it (one warp per tile, a warp scan over
+// the blocks in order).
+__global__ void __launch_bounds__(256)
+block_base_kernel(const uint32_t* __restrict__ block_counts, int nblocks, uint32_t n_tiles_all,
+                  const uint32_t* __restrict__ cursor, const int64_t* __restrict__ sort_n,
+                  uint32_t* __restrict__ block_base) {
+  if (*sort_n == 0) return;
+  const int lane = threadIdx.x & 31;
+  const uint32_t t = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (t >= n_tiles_all) return;
+  const uint32_t* col = block_counts + (size_t)t * nblocks;
+  uint32_t* out = block_base + (size_t)t * nblocks;
+  uint32_t run = cursor[t];
+  for (int b0 = 0; b0 < nblocks; b0 += 32) {
+    const int b = b0 + lane;
+    const uint32_t c = b < nblocks ? col[b] : 0u;
+    uint32_t x = c;
+#pragma unroll
+    for (int q = 1; q < 32; q <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, x, q);
+      if (lane >= q) x += y;
+    }
+    if (b < nblocks) out[b] = run + x - c;
+    run += __shfl_sync(0xffffffffu, x, 31);
+  }
+}
+
+// 3. append (depth bits, Gaussian index) to every covered tile's segment.
+// With the tile tables in shared memory a block starts from its own bases
+// (block_base row) and places its instances with shared-memory atomics;
+// otherwise every instance reserves its slot with a global atomic.
+__global__ void __launch_bounds__(256)
+tile_emit_kernel(const float4* __restrict__ proj, const ushort4* __restrict__ rect, int64_t m,
+                 uint32_t n, int tiles_x, uint32_t tiles, uint32_t n_tiles_all,
+                 const int64_t* __restrict__ sort_n, const uint32_t* __restrict__ block_base,
+                 uint32_t* __restrict__ cursor, unsigned long long* __restrict__ seg) {
+  extern __shared__ uint32_t s_cur[];  // [n_tiles_all] next slot of this block
+  if (*sort_n == 0) return;  // nothing fits (or nothing visible)
+  const bool local = n_tiles_all <= (uint32_t)kSmemTiles;
+  int64_t i0, i1;
+  item_chunk(m, i0, i1);
+  if (local) {
+    for (uint32_t t = threadIdx.x; t < n_tiles_all; t += blockDim.x)
+      s_cur[t] = block_base[(size_t)t * gridDim.x + blockIdx.x];
+    __syncthreads();
+  }
+  for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
+    const ushort4 r = rect[i];
+    if (rect_empty(r)) continue;
+    const uint32_t c = (uint32_t)(i / n);
+    const uint32_t base = c * tiles;
+    const unsigned long long key =
+        ((unsigned long long)__float_as_uint(proj[2 * i + 1].z) << 32) | (uint32_t)(i - (int64_t)c * n);
+    for (uint32_t y = r.y; y < r.w; y++)
+      for (uint32_t x = r.x; x < r.z; x++) {
+        const uint32_t t = base + y * (uint32_t)tiles_x + x;
+        const uint32_t pos = local ? atomicAdd(&s_cur[t], 1u) : atomicAdd(&cursor[t], 1u);
+        seg[pos] = key;
+      }
+  }
+}
+
+// Ascending bitonic network over np (a power of two) keys of s.
+template <int THREADS>
+__device__ __forceinline__ void bitonic(unsigned long long* s, uint32_t np) {
+  for (uint32_t k = 2; k <= np; k <<= 1)
+    for (uint32_t j = k >> 1; j > 0; j >>= 1) {
+      for (uint32_t i = threadIdx.x; i < np; i += THREADS) {
+        const uint32_t l = i ^ j;
+        if (l > i) {
+          const unsigned long long a = s[i], b = s[l];
+          if ((a > b) == ((i & k) == 0)) {
+            s[i] = b;
+            s[l] = a;
+          }
+        }
+      }
+      __syncthreads();
+    }
+}
+
+__device__ __forceinline__ uint32_t lane_lt() {
+  uint32_t m;
+  asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+  return m;
+}
+
+// 4. one block per tile sorts its segment of 64-bit (depth bits, index)
+// keys.  Up to kSegMax keys: a stable LSD radix sort in shared memory, 8 bits
+// a pass, skipping the digits all keys share; each warp holds R consecutive
+// runs of 32 keys (R = keys / 512 rounded up), ranks them per digit with
+// match-any in position order, and a per-digit scan over the warps places
+// them.  Longer segments: a bitonic network on a padded copy in global
+// scratch (the tile's own region [2 start, 2 start + 2 count)), padded with
+// all-ones keys (above any real key: depth bits of a positive float are
+// below 0x7f800000).
+constexpr int kSegWarps = kSegThreads / 32;
+constexpr int kSegItems = kSegMax / kSegThreads;
+
+__global__ void __launch_bounds__(kSegThreads, 3)
+tile_sort_kernel(const uint2* __restrict__ ranges, const unsigned long long* __restrict__ seg,
+                 unsigned long long* __restrict__ scratch, uint32_t* __restrict__ ids,
+                 uint64_t* __restrict__ keys_opt) {
+  __shared__ unsigned long long sk[kSegMax];
+  __shared__ uint16_t wcnt[kSegWarps][256];  // counts, then offsets (<= kSegMax)
+  __shared__ uint32_t dstart[256];
+  __shared__ uint32_t wsum[8];
+  __shared__ unsigned long long s_or[kSegWarps], s_and[kSegWarps], s_max[kSegWarps];
+  const uint32_t tile = blockIdx.x;
+  const uint2 rg = ranges[tile];
+  const uint32_t cnt = rg.y - rg.x;
+  if (cnt == 0) return;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (cnt > (uint32_t)kSegMax) {
+    uint32_t np = 32;
+    while (np < cnt) np <<= 1;  // np < 2 cnt
+    unsigned long long* s = scratch + 2 * (uint64_t)rg.x;
+    for (uint32_t i = threadIdx.x; i < np; i += kSegThreads) s[i] = i < cnt ? seg[rg.x + i] : ~0ull;
+    __syncthreads();
+    bitonic<kSegThreads>(s, np);
+    for (uint32_t i = threadIdx.x; i < cnt; i += kSegThreads) {
+      const unsigned long long key = s[i];
+      ids[rg.x + i] = (uint32_t)key;
+      if (keys_opt) keys_opt[rg.x + i] = ((uint64_t)tile << 32) | (key >> 32);
+    }
+    return;
+  }
+  const int R = (int)((cnt + kSegThreads - 1) / kSegThreads);
+  const uint32_t base = (uint32_t)warp * 32u * (uint32_t)R;  // this warp's first position
+  unsigned long long key[kSegItems];
+  unsigned long long o = 0, a = ~0ull, mx = 0;
+#pragma unroll
+  for (int r = 0; r < kSegItems; r++) {
+    const uint32_t p = base + r * 32 + lane;
+    key[r] = 0;
+    if (r < R && p < cnt) {
+      key[r] = seg[rg.x + p];
+      o |= key[r];
+      a &= key[r];
+      mx = key[r] > mx ? key[r] : mx;
+    }
+  }
+  // bits that differ between the keys: only those digits need a pass
+#pragma unroll
+  for (int d = 16; d > 0; d >>= 1) {
+    o |= __shfl_xor_sync(0xffffffffu, o, d);
+    a &= __shfl_xor_sync(0xffffffffu, a, d);
+    const unsigned long long m2 = __shfl_xor_sync(0xffffffffu, mx, d);
+    mx = m2 > mx ? m2 : mx;
+  }
+  if (lane == 0) {
+    s_or[warp] = o;
+    s_and[warp] = a;
+    s_max[warp] = mx;
+  }
+  __syncthreads();
+  unsigned long long diff = 0, kmax = 0;
+  {
+    unsigned long long oo = 0, aa = ~0ull;
+    for (int w = 0; w < kSegWarps; w++) {
+      oo |= s_or[w];
+      aa &= s_and[w];
+      kmax = s_max[w] > kmax ? s_max[w] : kmax;
+    }
+    diff = oo ^ aa;
+  }
+  // slots past the segment hold copies of the largest key: they share every
+  // skipped digit with the real keys and, being later in position, stay
+  // behind the real copy in a stable sort
+#pragma unroll
+  for (int r = 0; r < kSegItems; r++)
+    if (!(r < R && base + r * 32 + lane < cnt)) key[r] = kmax;
+  // one stable pass on the 8-bit digit at `shift` (skipped when every key
+  // has the same digit there)
+  auto pass = [&](int shift) {
+    if (((diff >> shift) & 0xffull) == 0) return;  // uniform over the block
+    for (int i = threadIdx.x; i < kSegWarps * 256; i += kSegThreads) (&wcnt[0][0])[i] = 0;
+    __syncthreads();
+    uint32_t rank[kSegItems];
+#pragma unroll
+    for (int r = 0; r < kSegItems; r++) {
+      if (r < R) {  // uniform over the block
+        const uint32_t d = (uint32_t)(key[r] >> shift) & 0xffu;
+        const uint32_t peers = __match_any_sync(0xffffffffu, d);
+        const uint32_t prior = wcnt[warp][d];
+        rank[r] = prior + __popc(peers & lane_lt());
+        __syncwarp();
+        if (lane == __ffs(peers) - 1) wcnt[warp][d] = (uint16_t)(prior + __popc(peers));
+        __syncwarp();
+      }
+    }
+    __syncthreads();
+    if (threadIdx.x < 256) {  // per digit: warps in order, then digits in order
+      const int d = threadIdx.x;
+      uint32_t tot = 0;
+      for (int w = 0; w < kSegWarps; w++) {
+        const uint32_t c = wcnt[w][d];
+        wcnt[w][d] = (uint16_t)tot;
+        tot += c;
+      }
+      uint32_t x = tot;
+#pragma unroll
+      for (int q = 1; q < 32; q <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, x, q);
+        if (lane >= q) x += y;
+      }
+      if (lane == 31) wsum[warp] = x;
+      dstart[d] = x - tot;  // exclusive within this warp's 32 digits
+    }
+    __syncthreads();
+    if (threadIdx.x < 256) {
+      uint32_t add = 0;
+      for (int w = 0; w < warp; w++) add += wsum[w];
+      dstart[threadIdx.x] += add;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < kSegItems; r++)
+      if (r < R) {
+        const uint32_t d = (uint32_t)(key[r] >> shift) & 0xffu;
+        sk[dstart[d] + wcnt[warp][d] + rank[r]] = key[r];
+      }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < kSegItems; r++)
+      if (r < R) key[r] = sk[base + r * 32 + lane];
+    __syncthreads();
+  };
+  // the depth digits alone order the keys unless two share a depth; only
+  // then is the segment sorted again on all eight digits (index ones first)
+  for (int sh = 32; sh < 64; sh += 8) pass(sh);
+#pragma unroll
+  for (int r = 0; r < kSegItems; r++)  // the current order (also when no pass ran)
+    if (r < R) sk[base + r * 32 + lane] = key[r];
+  __syncthreads();
+  bool tie = false;
+#pragma unroll
+  for (int r = 0; r < kSegItems; r++) {
+    const uint32_t p = base + r * 32 + lane;
+    if (r < R && p > 0 && p < cnt) tie |= (key[r] >> 32) == (sk[p - 1] >> 32);
+  }
+  if (__syncthreads_or(tie)) {
+    for (int sh = 0; sh < 64; sh += 8) pass(sh);
+  }
+#pragma unroll
+  for (int r = 0; r < kSegItems; r++) {
+    const uint32_t p = base + r * 32 + lane;
+    if (r < R && p < cnt) {
+      ids[rg.x + p] = (uint32_t)key[r];
+      if (keys_opt) keys_opt[rg.x + p] = ((uint64_t)tile << 32) | (key[r] >> 32);
+    }
+  }
+}
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+struct BinLayout {
+  size_t counts, cursor, total, sort_n, zero_end, block_counts, block_base, seg, scratch, size;
+};
+
+BinLayout bin_layout(uint64_t n_tiles_all, int64_t capacity) {
+  BinLayout L;
+  size_t o = 0;
+  auto take = [&](size_t b) { size_t at = o; o += align256(b > 0 ? b : 1); return at; };
+  L.counts = take(4 * n_tiles_all);
+  L.total = take(8);
+  L.zero_end = o;  // counts and total start at zero
+  L.sort_n = take(8);
+  L.cursor = take(4 * n_tiles_all);
+  const bool local = n_tiles_all <= (uint64_t)kSmemTiles;
+  L.block_counts = take(local ? 4 * (size_t)kItemBlocks * n_tiles_all : 0);
+  L.block_base = take(local ? 4 * (size_t)kItemBlocks * n_tiles_all : 0);
+  L.seg = take(8 * (size_t)capacity);
+  L.scratch = take(16 * (size_t)capacity);
+  L.size = o;
+  return L;
+}
+
+int grid_items(int64_t m) {
+  return (int)std::max<int64_t>(1, std::min<int64_t>((m + 1023) / 1024, kItemBlocks));
+}
+
+}  // namespace
+}  // namespace lgs
+
+using namespace lgs;
+
+extern "C" size_t gs_bin_sort_workspace(int64_t n, int n_cams, int tiles_x, int tiles_y,
+                                        int64_t capacity) {
+  if (n < 0 || n_cams < 1 || capacity < 0 || tiles_x < 1 || tiles_y < 1) return 0;
+  return bin_layout((uint64_t)n_cams * tiles_x * tiles_y, capacity).size;
+}
+
+extern "C" lgs_status gs_bin_sort(const float* proj, const uint16_t* rect, int64_t n, int n_cams,
+                                  int tiles_x, int tiles_y, int64_t capacity, uint32_t* ids,
+                                  uint32_t* ranges, uint64_t* keys_opt, int64_t* n_instances_dev,
+                                  void* workspace, size_t workspace_bytes, void* stream) {
+  clear_error();
+  LGS_CHECK_ARG(n >= 0 && n < ((int64_t)1 << 31), "n out of range");
+  LGS_CHECK_ARG(n_cams >= 1 && n_cams <= LGS_MAX_CAMS, "n_cams out of range");
+  LGS_CHECK_ARG(tiles_x >= 1 && tiles_y >= 1 && tiles_x <= 65535 && tiles_y <= 65535,
+                "bad tile grid");
+  LGS_CHECK_ARG(capacity >= 0 && capacity < ((int64_t)1 << 30), "capacity out of range");
+  LGS_CHECK_ARG((int64_t)n_cams * n < ((int64_t)1 << 30), "n_cams * n out of range");
+  LGS_CHECK_ARG(ranges && n_instances_dev && workspace, "null pointer");
+  LGS_CHECK_ARG(n == 0 || (proj && rect), "null pointer");
+  LGS_CHECK_ARG(capacity == 0 || ids, "ids is null");
+  LGS_CHECK_ARG(aligned(workspace, 256), "workspace must be 256-byte aligned");
+  LGS_CHECK_ARG(n == 0 || (aligned(proj, 16) && aligned(rect, 8)), "misaligned pointer");
+  const int64_t m = (int64_t)n_cams * n;
+  const uint32_t tiles = (uint32_t)tiles_x * (uint32_t)tiles_y;
+  LGS_CHECK_ARG((uint64_t)tiles * (uint64_t)n_cams <= (1ull << 24), "too many tiles");
+  const uint32_t n_tiles_all = (uint32_t)n_cams * tiles;
+  const BinLayout L = bin_layout(n_tiles_all, capacity);
+  LGS_CHECK_ARG(workspace_bytes >= L.size, "workspace too small");
+  cudaStream_t s = as_stream(stream);
+  char* ws = (char*)workspace;
+  LGS_CHECK_CUDA(cudaMemsetAsync(ws, 0, L.zero_end, s));
+  if (m == 0) {
+    LGS_CHECK_CUDA(cudaMemsetAsync(ranges, 0, sizeof(uint32_t) * 2 * (size_t)n_tiles_all, s));
+    LGS_CHECK_CUDA(cudaMemsetAsync(n_instances_dev, 0, sizeof(int64_t), s));
+    return LGS_OK;
+  }
+  uint32_t* counts = (uint32_t*)(ws + L.counts);
+  uint32_t* cursor = (uint32_t*)(ws + L.cursor);
+  unsigned long long* total = (unsigned long long*)(ws + L.total);
+  int64_t* sort_n = (int64_t*)(ws + L.sort_n);
+  unsigned long long* seg = (unsigned long long*)(ws + L.seg);
+  const bool local = n_tiles_all <= (uint32_t)kSmemTiles;
+  const size_t cnt_smem = local ? 4 * (size_t)n_tiles_all : 0;
+  LGS_CHECK_CUDA(set_smem_limit(reinterpret_cast<const void*>(tile_count_kernel), 4 * kSmemTiles));
+  LGS_CHECK_CUDA(set_smem_limit(reinterpret_cast<const void*>(tile_emit_kernel), 4 * kSmemTiles));
+  uint32_t* block_counts = (uint32_t*)(ws + L.block_counts);
+  uint32_t* block_base = (uint32_t*)(ws + L.block_base);
+  const int nblk = grid_items(m);
+  tile_count_kernel<<<nblk, 256, cnt_smem, s>>>((const ushort4*)rect, m, (uint32_t)n, tiles_x,
+                                                tiles, n_tiles_all, counts, block_counts, total);
+  tile_scan_kernel<<<1, kScanThreads, 0, s>>>(counts, n_tiles_all, total, capacity,
+                                              (uint2*)ranges, cursor, n_instances_dev, sort_n);
+  if (capacity == 0) {
+    LGS_CHECK_LAUNCH();
+    return LGS_OK;
+  }
+  if (local)
+    block_base_kernel<<<(n_tiles_all + 7) / 8, 256, 0, s>>>(block_counts, nblk, n_tiles_all,
+                                                          cursor, sort_n, block_base);
+  tile_emit_kernel<<<nblk, 256, cnt_smem, s>>>((const float4*)proj, (const ushort4*)rect, m,
+                                               (uint32_t)n, tiles_x, tiles, n_tiles_all, sort_n,
+                                               block_base, cursor, seg);
+  tile_sort_kernel<<<n_tiles_all, kSegThreads, 0, s>>>(
+      (const uint2*)ranges, seg, (unsigned long long*)(ws + L.scratch), ids, keys_opt);
+  LGS_CHECK_LAUNCH();
+  return LGS_OK;
+}

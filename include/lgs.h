@@ -110,7 +110,7 @@ lgs_status gs_project(const float* means, const float* quats, const float* log_s
                       int n_cams, float* proj, uint16_t* rect, void* stream);
 
 /* ------------------------------------------------------------------------
- * gs_bin_sort -- 16x16 tile binning with a depth-keyed stable radix sort.
+ * gs_bin_sort -- 16x16 tile binning, instances ordered by depth within each tile.
  *
  * Each (camera c, Gaussian i) emits one instance per covered tile; the
  * instances are ordered by the 64-bit key ((c * tiles + tile) << 32) |

@@ -337,7 +337,8 @@ render_bwd_kernel(RasterArgs A, int chunk_base) {
           const float araw = raw_alpha(co.w, power);
           const float alpha = fminf(kAlphaMax, araw);
           if (alpha >= kAlphaMin) {
-            const float inv = 1.f / __fsub_rn(1.f, alpha);
+            // fast reciprocal: T only enters gradient values here, never a decision
+            const float inv = __fdividef(1.f, __fsub_rn(1.f, alpha));
             const float Tj = T * inv;
             w = alpha * Tj;
             const float4* c4 = reinterpret_cast<const float4*>(s_ch + j * NCH);

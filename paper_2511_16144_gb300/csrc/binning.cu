@@ -29,7 +29,7 @@ namespace lgs {
 namespace {
 
 constexpr int kSegMax = 4096;          // keys a block sorts in shared memory
-constexpr int kSegThreads = 512;
+constexpr int kSegThreads = 256;
 constexpr int kSmemTiles = 24576;      // per-block tile tables up to this many tiles
 constexpr int kItemBlocks = 2 * 152;   // blocks of the count and emit passes
 constexpr int kScanThreads = 1024;

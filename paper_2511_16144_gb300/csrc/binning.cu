@@ -16,8 +16,9 @@
 //      (a block reserves one range per tile, then fills it with shared-
 //      memory atomics; the order inside a segment is arbitrary);
 //   4. one block per tile sorts its segment's 64-bit (depth bits, index)
-//      keys with a bitonic network -- in shared memory up to kSegMax keys,
-//      in a global scratch copy beyond -- and writes the Gaussian indices.
+//      keys with a stable LSD radix sort -- in shared memory up to kSegMax
+//      keys, chunk by chunk from global memory beyond -- and writes the
+//      Gaussian indices.
 // Depths are positive floats, so their bit patterns order like the values.
 #include <algorithm>
 
@@ -30,7 +31,7 @@ namespace {
 
 constexpr int kSegMax = 4096;          // keys a block sorts in shared memory
 constexpr int kSegThreads = 256;
-constexpr int kSmemTiles = 24576;      // per-block tile tables up to this many tiles
+constexpr int kSmemTiles = 32768;      // per-block tile tables (4 B each) up to this many tiles
 constexpr int kItemBlocks = 2 * 152;   // blocks of the count and emit passes
 constexpr int kScanThreads = 1024;
 
@@ -196,25 +197,6 @@ tile_emit_kernel(const float4* __restrict__ proj, const ushort4* __restrict__ re
   }
 }
 
-// Ascending bitonic network over np (a power of two) keys of s.
-template <int THREADS>
-__device__ __forceinline__ void bitonic(unsigned long long* s, uint32_t np) {
-  for (uint32_t k = 2; k <= np; k <<= 1)
-    for (uint32_t j = k >> 1; j > 0; j >>= 1) {
-      for (uint32_t i = threadIdx.x; i < np; i += THREADS) {
-        const uint32_t l = i ^ j;
-        if (l > i) {
-          const unsigned long long a = s[i], b = s[l];
-          if ((a > b) == ((i & k) == 0)) {
-            s[i] = b;
-            s[l] = a;
-          }
-        }
-      }
-      __syncthreads();
-    }
-}
-
 __device__ __forceinline__ uint32_t lane_lt() {
   uint32_t m;
   asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
@@ -226,15 +208,133 @@ __device__ __forceinline__ uint32_t lane_lt() {
 // a pass, skipping the digits all keys share; each warp holds R consecutive
 // runs of 32 keys (R = keys / 512 rounded up), ranks them per digit with
 // match-any in position order, and a per-digit scan over the warps places
-// them.  Longer segments: a bitonic network on a padded copy in global
-// scratch (the tile's own region [2 start, 2 start + 2 count)), padded with
-// all-ones keys (above any real key: depth bits of a positive float are
-// below 0x7f800000).
+// them.  Longer segments are sorted the same way from global memory (below).
 constexpr int kSegWarps = kSegThreads / 32;
 constexpr int kSegItems = kSegMax / kSegThreads;
 
+// Segments over kSegMax keys: the same stable LSD radix sort with the keys in
+// global memory (ping-pong between the segment and its scratch copy, both
+// L2-resident).  Each pass counts the digit over the whole segment, then
+// scatters it kSegMax keys at a time in position order: within a chunk the
+// warps rank their keys as above, and running per-digit offsets carry over
+// from chunk to chunk, which keeps the pass stable.
+__device__ __noinline__ void big_segment_sort(unsigned long long* src, unsigned long long* dst, uint32_t cnt,
+                                 uint32_t tile, uint32_t* __restrict__ ids,
+                                 uint64_t* __restrict__ keys_opt, uint16_t (*wcnt)[256],
+                                 uint32_t* dstart, uint32_t* wsum, unsigned long long* s_or,
+                                 unsigned long long* s_and, uint32_t* tab) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint32_t* hist = tab;        // [256] digit counts of the segment
+  uint32_t* run = tab + 256;   // [256] next output slot of each digit
+  unsigned long long o = 0, a = ~0ull;
+  for (uint32_t i = threadIdx.x; i < cnt; i += kSegThreads) {
+    o |= src[i];
+    a &= src[i];
+  }
+#pragma unroll
+  for (int d = 16; d > 0; d >>= 1) {
+    o |= __shfl_xor_sync(0xffffffffu, o, d);
+    a &= __shfl_xor_sync(0xffffffffu, a, d);
+  }
+  if (lane == 0) {
+    s_or[warp] = o;
+    s_and[warp] = a;
+  }
+  __syncthreads();
+  unsigned long long oo = 0, aa = ~0ull;
+  for (int w = 0; w < kSegWarps; w++) {
+    oo |= s_or[w];
+    aa &= s_and[w];
+  }
+  const unsigned long long diff = oo ^ aa;
+  auto pass = [&](int shift) {
+    if (((diff >> shift) & 0xffull) == 0) return;  // uniform over the block
+    for (int d = threadIdx.x; d < 256; d += kSegThreads) hist[d] = 0;
+    __syncthreads();
+    for (uint32_t i = threadIdx.x; i < cnt; i += kSegThreads)
+      atomicAdd(&hist[(uint32_t)(src[i] >> shift) & 0xffu], 1u);
+    __syncthreads();
+    if (threadIdx.x < 256) {  // exclusive scan of the digit counts
+      const uint32_t v = hist[threadIdx.x];
+      uint32_t x = v;
+#pragma unroll
+      for (int q = 1; q < 32; q <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, x, q);
+        if (lane >= q) x += y;
+      }
+      if (lane == 31) wsum[warp] = x;
+      run[threadIdx.x] = x - v;
+    }
+    __syncthreads();
+    if (threadIdx.x < 256) {
+      uint32_t add = 0;
+      for (int w = 0; w < warp; w++) add += wsum[w];
+      run[threadIdx.x] += add;
+    }
+    __syncthreads();
+    for (uint32_t c0 = 0; c0 < cnt; c0 += kSegMax) {
+      for (int i = threadIdx.x; i < kSegWarps * 256; i += kSegThreads) (&wcnt[0][0])[i] = 0;
+      __syncthreads();
+      const uint32_t base = c0 + (uint32_t)warp * 32u * kSegItems;
+      unsigned long long key[kSegItems];
+      uint32_t rank[kSegItems];
+#pragma unroll
+      for (int r = 0; r < kSegItems; r++) {
+        const uint32_t p = base + r * 32 + lane;
+        const bool valid = p < cnt;
+        key[r] = valid ? src[p] : 0ull;
+        const uint32_t d = valid ? (uint32_t)(key[r] >> shift) & 0xffu : 256u + lane;
+        const uint32_t peers = __match_any_sync(0xffffffffu, d);
+        const uint32_t prior = valid ? wcnt[warp][d] : 0u;
+        rank[r] = prior + __popc(peers & lane_lt());
+        __syncwarp();
+        if (valid && lane == __ffs(peers) - 1) wcnt[warp][d] = (uint16_t)(prior + __popc(peers));
+        __syncwarp();
+      }
+      __syncthreads();
+      if (threadIdx.x < 256) {  // per digit: this chunk's warps in order
+        const int d = threadIdx.x;
+        uint32_t tot = 0;
+        for (int w = 0; w < kSegWarps; w++) {
+          const uint32_t c = wcnt[w][d];
+          wcnt[w][d] = (uint16_t)tot;
+          tot += c;
+        }
+        dstart[d] = tot;
+      }
+      __syncthreads();
+#pragma unroll
+      for (int r = 0; r < kSegItems; r++) {
+        const uint32_t p = base + r * 32 + lane;
+        if (p < cnt) {
+          const uint32_t d = (uint32_t)(key[r] >> shift) & 0xffu;
+          dst[run[d] + wcnt[warp][d] + rank[r]] = key[r];
+        }
+      }
+      __syncthreads();
+      if (threadIdx.x < 256) run[threadIdx.x] += dstart[threadIdx.x];
+      __syncthreads();
+    }
+    unsigned long long* t = src;
+    src = dst;
+    dst = t;
+    __syncthreads();
+  };
+  for (int sh = 32; sh < 64; sh += 8) pass(sh);  // depth digits
+  bool tie = false;
+  for (uint32_t i = threadIdx.x + 1; i < cnt; i += kSegThreads)
+    tie |= (src[i] >> 32) == (src[i - 1] >> 32);
+  if (__syncthreads_or(tie))
+    for (int sh = 0; sh < 64; sh += 8) pass(sh);  // equal depths: order by index too
+  for (uint32_t i = threadIdx.x; i < cnt; i += kSegThreads) {
+    const unsigned long long key = src[i];
+    ids[i] = (uint32_t)key;
+    if (keys_opt) keys_opt[i] = ((uint64_t)tile << 32) | (key >> 32);
+  }
+}
+
 __global__ void __launch_bounds__(kSegThreads, 3)
-tile_sort_kernel(const uint2* __restrict__ ranges, const unsigned long long* __restrict__ seg,
+tile_sort_kernel(const uint2* __restrict__ ranges, unsigned long long* __restrict__ seg,
                  unsigned long long* __restrict__ scratch, uint32_t* __restrict__ ids,
                  uint64_t* __restrict__ keys_opt) {
   __shared__ unsigned long long sk[kSegMax];
@@ -248,17 +348,9 @@ tile_sort_kernel(const uint2* __restrict__ ranges, const unsigned long long* __r
   if (cnt == 0) return;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   if (cnt > (uint32_t)kSegMax) {
-    uint32_t np = 32;
-    while (np < cnt) np <<= 1;  // np < 2 cnt
-    unsigned long long* s = scratch + 2 * (uint64_t)rg.x;
-    for (uint32_t i = threadIdx.x; i < np; i += kSegThreads) s[i] = i < cnt ? seg[rg.x + i] : ~0ull;
-    __syncthreads();
-    bitonic<kSegThreads>(s, np);
-    for (uint32_t i = threadIdx.x; i < cnt; i += kSegThreads) {
-      const unsigned long long key = s[i];
-      ids[rg.x + i] = (uint32_t)key;
-      if (keys_opt) keys_opt[rg.x + i] = ((uint64_t)tile << 32) | (key >> 32);
-    }
+    big_segment_sort(seg + rg.x, scratch + rg.x, cnt, tile, ids + rg.x,
+                     keys_opt ? keys_opt + rg.x : nullptr, wcnt, dstart, wsum, s_or, s_and,
+                     reinterpret_cast<uint32_t*>(sk));
     return;
   }
   const int R = (int)((cnt + kSegThreads - 1) / kSegThreads);
@@ -407,7 +499,7 @@ BinLayout bin_layout(uint64_t n_tiles_all, int64_t capacity) {
   L.block_counts = take(local ? 4 * (size_t)kItemBlocks * n_tiles_all : 0);
   L.block_base = take(local ? 4 * (size_t)kItemBlocks * n_tiles_all : 0);
   L.seg = take(8 * (size_t)capacity);
-  L.scratch = take(16 * (size_t)capacity);
+  L.scratch = take(8 * (size_t)capacity);
   L.size = o;
   return L;
 }

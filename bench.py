@@ -57,9 +57,32 @@ def build_workload(rank):
     from paper_2511_16144_gb300 import synth
     scene, cams = synth.indoor(n_cams=8)
     g512 = synth.semantic_features(scene.means, synth.ROOM_LO, synth.ROOM_HI, seed=1005)
-    cam = cams[rank % 8]
+    cam = cams[keyframe_of_rank(rank)]
     (rgb_t, dep_t, _), = synth.targets([cam], feat_dim=16, seed=2001 + rank)
     return dict(scene=scene, cams=cams, cam=cam, g512=g512, rgb_t=rgb_t, dep_t=dep_t)
+
+
+def keyframe_of_rank(rank, n_keyframes=8):
+    """Replicas: rank r renders keyframe r mod 8 of the window against its
+    own copy of the map (no exchange between ranks)."""
+    return rank % n_keyframes
+
+
+def max_over_ranks(x, world, device="cpu"):
+    """The largest x over all ranks of the process group (x when alone): the
+    job's time is its slowest rank's."""
+    if world == 1:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(pixels_per_rank, steps, world, total_ms):
+    """Whole-job Mpix/s: every rank's pixels of every timed step over the
+    slowest rank's time."""
+    return world * pixels_per_rank * steps / 1e6 / (total_ms / 1e3)
 
 
 class Clocks:
@@ -163,7 +186,7 @@ def run_gpu(args, rank, world):
     # the extractor's per-frame 512-d maps: the semantic field rendered by the
     # plain path for every keyframe of the window (BF16), F_gt = this rank's
     frames = [Frame(s512, [c]).out["feat"][0].reshape(-1, 512).bfloat16() for c in W["cams"]]
-    f_gt = frames[rank % 8].contiguous()
+    f_gt = frames[keyframe_of_rank(rank)].contiguous()
 
     # scene-adaptive autoencoder pretrained online on those maps (Sec. IV-A.2);
     # the encoder prior gives the Gaussians' 16-d features (Sec. III-B.2)
@@ -240,14 +263,9 @@ def run_gpu(args, rank, world):
     t16, g16, nodes16 = timed(step16, args.steps, args.warmup, clocks)
     k_inst = int(step16.k_dev.item())
     ms16 = float(np.mean(t16))
-    if world > 1:
-        tt = torch.tensor([sum(t16)], device=dev)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(tt.item())
-    else:
-        total_ms = float(sum(t16))
+    total_ms = max_over_ranks(float(sum(t16)), world, dev)
     pixels = step16.pixels
-    value = world * pixels * args.steps / 1e6 / (total_ms / 1e3)
+    value = job_throughput(pixels, args.steps, world, total_ms)
 
     # per-call durations of one eager step (events on the launching stream)
     calls = per_call_times(step16, flush, reps=5)

@@ -172,7 +172,7 @@ decode_fused_kernel(const __grid_constant__ FusedArgs a) {
       tc::mbar_init(&empty[s], 1);
     }
     tc::mbar_init(accbar, 1);
-    tc::mbar_init(opbar, kEpiWarps * 32);
+    tc::mbar_init(opbar, kEpiWarps);
     tc::mbar_init(&ybar[0], 1);
     tc::mbar_init(&ybar[1], 1);
     tc::mbar_init(dyfree, 1);
@@ -291,10 +291,13 @@ decode_fused_kernel(const __grid_constant__ FusedArgs a) {
       accs++;
       tc::fence_after();
     };
+    // every thread publishes its shared-memory writes to the async proxy and
+    // orders its TMEM loads; one lane per warp then arrives for the warp
     auto arrive = [&]() {
       tc::fence_async_smem();
       tc::fence_before();
-      tc::mbar_arrive(opbar);
+      __syncwarp();
+      if (lane == 0) tc::mbar_arrive(opbar);
     };
     for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
       const int64_t p = t * 128 + r;

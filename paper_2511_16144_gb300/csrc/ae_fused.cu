@@ -10,15 +10,20 @@
 //           epilogue forms dy = w sign(y - F_gt) / (P 512) and immediately
 //           feeds dh3 += dy_chunk W7_chunk, so y and dy never reach memory;
 //   R3..R1  the pre-activations are recomputed instead of stored (this keeps
-//           the working set in 212 KB of shared memory);
+//           the working set in shared memory);
 //   B2..B4  dh2 = (dh3 * gelu'(pre3)) W6, dh1 = (dh2 * gelu'(pre2)) W5,
 //           dz = (dh1 * gelu'(pre1)) W4.
+// Consecutive tiles of a CTA overlap: the backward hidden layers of tile t
+// (R3, B2..B4, accumulators in TMEM columns 0-255) interleave with the
+// forward hidden layers of tile t+1 (F1..F3, columns 256-511), so the tensor
+// core works on one tile while the epilogue warps work on the other.  z is
+// double-buffered for this; the shared buffer of the z not in use doubles as
+// the F_gt transpose buffer of the output epilogue.
 // Warps 0-15 are the epilogue (TMEM -> registers -> shared memory; warps w,
 // w + 4, w + 8, w + 12 share TMEM lane quadrant w % 4 and split the columns in
-// quarters), warp 16 streams
-// the weights as 51 pre-packed units (<= 16 KB each, already in the
-// tensor-core's canonical layout) through a 4-stage ring with bulk TMA
-// copies, warp 17 issues the MMAs.  Every wait is bounded.
+// quarters), warp 16 streams the weights as 51 pre-packed units (<= 16 KB
+// each, already in the tensor-core's canonical layout) through a 4-stage ring
+// with bulk TMA copies, warp 17 issues the MMAs.  Every wait is bounded.
 #include <mutex>
 #include <vector>
 
@@ -36,12 +41,13 @@ constexpr uint32_t kStageBytes = 16384;
 constexpr uint32_t kLimit = 1u << 22;
 
 // shared-memory map (bytes)
-constexpr uint32_t SM_Z = 0;         // 128 x 16 bf16
-constexpr uint32_t SM_H1 = 4096;     // 128 x 64   (h1, later d1)
-constexpr uint32_t SM_H2 = 20480;    // 128 x 128  (h2, later d2)
-constexpr uint32_t SM_H3 = 53248;    // 128 x 256  (h3, later d3)
-constexpr uint32_t SM_DY = 118784;   // 128 x 128  (one dy chunk)
-constexpr uint32_t SM_ST = 151552;   // kStages x 16 KB weight ring
+constexpr uint32_t SM_Z = 0;         // 2 x (128 x 16 bf16): z of this tile and the next
+constexpr uint32_t SM_H1 = 8192;     // 128 x 64   (h1)
+constexpr uint32_t SM_H2 = 24576;    // 128 x 128  (h2, later d2)
+constexpr uint32_t SM_H3 = 57344;    // 128 x 256  (h3, later d3)
+constexpr uint32_t SM_DY = 122880;   // 128 x 128  (one dy chunk, later d1)
+constexpr uint32_t SM_FGX = 155648;  // F_gt transpose buffers of epilogue warps 8-15
+constexpr uint32_t SM_ST = 159744;   // kStages x 16 KB weight ring
 constexpr uint32_t SM_BAR = SM_ST + kStages * kStageBytes;
 
 // weight matrices of the decoder: forward W (out x in) and transposed Wt
@@ -138,23 +144,51 @@ __device__ unsigned g_fused_error;
 
 constexpr int kEpiWarps = 16;
 constexpr int kFusedThreads = (kEpiWarps + 2) * 32;   // + producer warp + MMA warp
-// barriers: full[kStages], empty[kStages], accbar, opbar, ybar[2], dyfree,
-// then the TMEM slot
-constexpr uint32_t kBarBytes = (2 * kStages + 5) * 8 + 4;
+// barriers: full[kStages], empty[kStages], accH, accT, opH, opT, ybar[2],
+// dyfree, then the TMEM slot
+constexpr uint32_t kBarBytes = (2 * kStages + 7) * 8 + 4;
 constexpr uint32_t SM_BIAS = SM_BAR + 128;             // b4 | b5 | b6 | b7 (960 floats)
 constexpr uint32_t SM_ALL = SM_BIAS + 960 * 4;
 static_assert(kBarBytes <= SM_BIAS - SM_BAR, "barrier block overlaps the biases");
 static_assert(SM_ALL <= 232448, "shared-memory map exceeds 227 KB");
+static_assert(SM_FGX + 8 * 512 <= SM_ST && SM_Z + 2 * 4096 <= SM_H1, "transpose buffers overlap");
+
+// Weight units per tile in stream order.  Units 0-5 are the forward hidden
+// layers (F1, F2, F3), 6-37 the output layer and its backward (F4/B1), 38-41
+// R3, 42-46 B2 and R2, 47-49 B3 and R1, 50 B4.  The first tile of a CTA
+// starts with 0-5; every tile then streams 6-46, 47-49, 50, with the next
+// tile's F1 (0), F2 (1) and F3 (2-5) slotted in after 46, 49 and 50.
+__device__ __forceinline__ int stream_count(bool first, bool next) {
+  return (first ? 6 : 0) + 45 + (next ? 6 : 0);
+}
+__device__ __forceinline__ int stream_unit(bool first, bool next, int j) {
+  if (first) {
+    if (j < 6) return j;
+    j -= 6;
+  }
+  if (j < 41) return 6 + j;                 // 6..46
+  j -= 41;
+  if (next) {
+    if (j == 0) return 0;                   // F1 of the next tile
+    if (j <= 3) return 46 + j;              // 47..49
+    if (j == 4) return 1;                   // F2 of the next tile
+    if (j == 5) return 50;
+    return j - 4;                           // 2..5: F3 of the next tile
+  }
+  return j < 3 ? 47 + j : 50;
+}
 
 __global__ void __launch_bounds__(kFusedThreads, 1)
 decode_fused_kernel(const __grid_constant__ FusedArgs a) {
   extern __shared__ __align__(1024) uint8_t sm[];
   uint64_t* full = reinterpret_cast<uint64_t*>(sm + SM_BAR);
   uint64_t* empty = full + kStages;
-  uint64_t* accbar = full + 2 * kStages;
-  uint64_t* opbar = accbar + 1;
-  uint64_t* ybar = opbar + 1;    // [2] output chunk ready in TMEM buffer c & 1
-  uint64_t* dyfree = ybar + 2;   // the backward product of the last dy chunk is done
+  uint64_t* accH = full + 2 * kStages;  // MMA -> epilogue: a forward hidden layer is done
+  uint64_t* accT = accH + 1;            // MMA -> epilogue: a backward group is done
+  uint64_t* opH = accT + 1;             // epilogue -> MMA: z / h1 / h2 / h3 staged
+  uint64_t* opT = opH + 1;              // epilogue -> MMA: a dy chunk / d3 / d2 / d1 / dz done
+  uint64_t* ybar = opT + 1;             // [2] output chunk ready in TMEM buffer c & 1
+  uint64_t* dyfree = ybar + 2;          // the backward product of the last dy chunk is done
   uint32_t* tslot = reinterpret_cast<uint32_t*>(dyfree + 1);
   float* sb = reinterpret_cast<float*>(sm + SM_BIAS);
   const float* sb4 = sb;
@@ -171,8 +205,10 @@ decode_fused_kernel(const __grid_constant__ FusedArgs a) {
       tc::mbar_init(&full[s], 1);
       tc::mbar_init(&empty[s], 1);
     }
-    tc::mbar_init(accbar, 1);
-    tc::mbar_init(opbar, kEpiWarps);
+    tc::mbar_init(accH, 1);
+    tc::mbar_init(accT, 1);
+    tc::mbar_init(opH, kEpiWarps);
+    tc::mbar_init(opT, kEpiWarps);
     tc::mbar_init(&ybar[0], 1);
     tc::mbar_init(&ybar[1], 1);
     tc::mbar_init(dyfree, 1);
@@ -190,7 +226,10 @@ decode_fused_kernel(const __grid_constant__ FusedArgs a) {
       uint32_t u = 0;
       bool ok = true;
       for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
-        for (int i = 0; i < kUnits; i++, u++) {
+        const bool first = t == blockIdx.x, next = t + gridDim.x < ntiles;
+        const int n = stream_count(first, next);
+        for (int j = 0; j < n; j++, u++) {
+          const int i = stream_unit(first, next, j);
           const uint32_t s = u % kStages, round = u / kStages;
           if (round > 0 && !tc::mbar_wait(&empty[s], (round - 1) & 1, kLimit)) {
             ok = false;
@@ -204,78 +243,104 @@ decode_fused_kernel(const __grid_constant__ FusedArgs a) {
     }
   } else if (warp == kEpiWarps + 1) {
     // ---------------------------------------------------------------- MMA issuer
-    if (lane == 0) {
-      uint32_t u = 0, ops = 0;
-      bool ok = true;
-      auto wait_op = [&]() {
-        ok = ok && tc::mbar_wait(opbar, ops & 1, kLimit);
-        ops++;
-        tc::fence_after();
-      };
-      // one weight unit: B = ring stage, A = activation tile at a_off (width
-      // a_kw) from column k0, D = TMEM column dcol, N = n, K = kc
-      auto unit = [&](uint32_t a_off, int a_kw, int k0, int kc, int n, uint32_t dcol, bool fresh) {
-        if (!ok) return;
-        const uint32_t s = u % kStages, round = u / kStages;
-        if (!tc::mbar_wait(&full[s], round & 1, kLimit)) {
-          ok = false;
-          return;
-        }
-        tc::fence_after();
-        const uint32_t b = sbase + SM_ST + s * kStageBytes;
-        const uint32_t idesc = tc::idesc_bf16(128, n);
-        for (int j = 0; j < kc / 16; j++) {
-          const uint64_t ad = tc::sdesc(sbase + a_off + ((k0 + 16 * j) >> 3) * 128, 128, a_kw * 16);
-          const uint64_t bd = tc::sdesc(b + j * 256, 128, kc * 16);
-          tc::mma_bf16(tmem + dcol, ad, bd, idesc, (fresh && j == 0) ? 0u : 1u);
-        }
+    // The whole warp walks the schedule (so descriptors and loop state stay
+    // warp-uniform) and votes on every wait; one elected lane issues the MMAs
+    // and commits.  Descriptors are a base plus compile-time offsets.
+    uint32_t u = 0, nopH = 0, nopT = 0;
+    bool ok = true;
+    const uint64_t dbase = tc::sdesc_base(sbase);
+    auto wait_on = [&](uint64_t* bar, uint32_t& n) {
+      ok = ok && __all_sync(0xffffffffu, tc::mbar_wait(bar, n & 1, kLimit));
+      n++;
+      tc::fence_after();
+    };
+    auto commit = [&](uint64_t* bar) {
+      if (ok && tc::elect_one()) tc::commit(bar);
+      __syncwarp();
+    };
+    // one weight unit: B = ring stage, A = activation tile at a_off (width
+    // a_kw) from column k0, D = TMEM column dcol, N = n, K = kc
+    auto unit = [&](uint32_t a_off, int a_kw, int k0, int kc, int n, uint32_t dcol, bool fresh) {
+      if (!ok) return;
+      const uint32_t s = u % kStages, round = u / kStages;
+      ok = __all_sync(0xffffffffu, tc::mbar_wait(&full[s], round & 1, kLimit));
+      if (!ok) return;
+      tc::fence_after();
+      const uint64_t ad = dbase + tc::sdesc_off(a_off + (uint32_t)k0 * 16, (uint32_t)a_kw * 16);
+      const uint64_t bd = dbase + tc::sdesc_off(SM_ST + s * kStageBytes, (uint32_t)kc * 16);
+      const uint32_t idesc = tc::idesc_bf16(128, n);
+      if (tc::elect_one()) {
+        for (int j = 0; j < kc / 16; j++)
+          tc::mma_bf16(tmem + dcol, ad + 16 * j, bd + 16 * j, idesc, (fresh && j == 0) ? 0u : 1u);
         tc::commit(&empty[s]);
-        u++;
-      };
-      auto done = [&]() { if (ok) tc::commit(accbar); };
-      for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
-        wait_op();                                                     // z staged
-        unit(SM_Z, 16, 0, 16, 64, 0, true);                            // F1
-        done();
-        wait_op();
-        unit(SM_H1, 64, 0, 64, 128, 0, true);                          // F2
-        done();
-        wait_op();
-        for (int k = 0; k < 4; k++) unit(SM_H2, 128, 32 * k, 32, 256, 0, k == 0);         // F3
-        done();
-        wait_op();
-        // output chunk c -> TMEM buffer c & 1, announced on ybar[c & 1]; each
-        // dy chunk's product is announced on dyfree (its buffer is free again)
-        auto f4 = [&](int c) {
-          for (int k = 0; k < 4; k++)
-            unit(SM_H3, 256, 64 * k, 64, 128, 256 + 128 * (c & 1), k == 0);
-          if (ok) tc::commit(&ybar[c & 1]);
-        };
-        f4(0);
-        f4(1);
-        for (int c = 0; c < 4; c++) {
-          wait_op();                                                   // dy chunk c written
-          for (int k = 0; k < 4; k++)
-            unit(SM_DY, 128, 32 * k, 32, 256, 0, c == 0 && k == 0);                         // B1 c
-          if (ok) tc::commit(dyfree);
-          if (c < 2) f4(c + 2);
-        }
-        for (int k = 0; k < 4; k++) unit(SM_H2, 128, 32 * k, 32, 256, 256, k == 0);       // R3
-        done();
-        wait_op();                                                     // d3 written
-        for (int k = 0; k < 4; k++) unit(SM_H3, 256, 64 * k, 64, 128, 0, k == 0);         // B2
-        unit(SM_H1, 64, 0, 64, 128, 128, true);                        // R2
-        done();
-        wait_op();                                                     // d2 written
-        for (int k = 0; k < 2; k++) unit(SM_H2, 128, 64 * k, 64, 64, 0, k == 0);           // B3
-        unit(SM_Z, 16, 0, 16, 64, 64, true);                           // R1
-        done();
-        wait_op();                                                     // d1 written
-        unit(SM_H1, 64, 0, 64, 16, 0, true);                           // B4
-        done();
       }
-      if (!ok) atomicOr(&g_fused_error, 2u);
+      __syncwarp();
+      u++;
+    };
+    // forward hidden layers into TMEM columns 256-511 (z in buffer zb)
+    auto f1 = [&](uint32_t zb) { unit(zb, 16, 0, 16, 64, 256, true); commit(accH); };
+    auto f2 = [&]() { unit(SM_H1, 64, 0, 64, 128, 256, true); commit(accH); };
+    auto f3 = [&]() {
+      for (int k = 0; k < 4; k++) unit(SM_H2, 128, 32 * k, 32, 256, 256, k == 0);
+      commit(accH);
+    };
+    if (blockIdx.x < ntiles) {
+      wait_on(opH, nopH);                                            // z staged
+      f1(SM_Z);
+      wait_on(opH, nopH);                                            // h1 staged
+      f2();
+      wait_on(opH, nopH);                                            // h2 staged
+      f3();
     }
+    int64_t k = 0;
+    for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x, k++) {
+      const bool next = t + gridDim.x < ntiles;
+      const uint32_t zc = SM_Z + (uint32_t)(k & 1) * 4096, zn = SM_Z + (uint32_t)((k + 1) & 1) * 4096;
+      wait_on(opH, nopH);                                            // h3 staged
+      if (k > 0) wait_on(opT, nopT);                                 // dz of the last tile read
+      // output chunk c -> TMEM buffer c & 1, announced on ybar[c & 1]; each
+      // dy chunk's product is announced on dyfree (its buffer is free again)
+      auto f4 = [&](int c) {
+        for (int kk = 0; kk < 4; kk++)
+          unit(SM_H3, 256, 64 * kk, 64, 128, 256 + 128 * (c & 1), kk == 0);
+        commit(&ybar[c & 1]);
+      };
+      f4(0);
+      f4(1);
+      for (int c = 0; c < 4; c++) {
+        wait_on(opT, nopT);                                          // dy chunk c written
+        for (int kk = 0; kk < 4; kk++)
+          unit(SM_DY, 128, 32 * kk, 32, 256, 0, c == 0 && kk == 0);                       // B1 c
+        commit(dyfree);
+        if (c < 2) f4(c + 2);
+      }
+      for (int kk = 0; kk < 4; kk++) unit(SM_H2, 128, 32 * kk, 32, 256, 256, kk == 0);  // R3
+      commit(accT);
+      wait_on(opT, nopT);                                            // d3 written
+      for (int kk = 0; kk < 4; kk++) unit(SM_H3, 256, 64 * kk, 64, 128, 0, kk == 0);    // B2
+      unit(SM_H1, 64, 0, 64, 128, 128, true);                        // R2
+      commit(accT);
+      if (next) {
+        wait_on(opH, nopH);                                          // next z staged
+        f1(zn);
+      }
+      wait_on(opT, nopT);                                            // d2 written
+      for (int kk = 0; kk < 2; kk++) unit(SM_H2, 128, 64 * kk, 64, 64, 0, kk == 0);      // B3
+      unit(zc, 16, 0, 16, 64, 64, true);                             // R1
+      commit(accT);
+      if (next) {
+        wait_on(opH, nopH);                                          // next h1 staged
+        f2();
+      }
+      wait_on(opT, nopT);                                            // d1 written
+      unit(SM_DY, 64, 0, 64, 16, 0, true);                           // B4
+      commit(accT);
+      if (next) {
+        wait_on(opH, nopH);                                          // next h2 staged
+        f3();
+      }
+    }
+    if (!ok && lane == 0) atomicOr(&g_fused_error, 2u);
   } else {
     // ---------------------------------------------------------------- epilogue
     // warp w reads TMEM lane quadrant w % 4 (rows 32 (w % 4) ..) and the
@@ -283,28 +348,28 @@ decode_fused_kernel(const __grid_constant__ FusedArgs a) {
     const int q = warp & 3, qq = warp >> 2;
     const int r = 32 * q + lane;
     const uint32_t tb = tmem + ((uint32_t)(32 * q) << 16);
-    uint32_t accs = 0;
+    uint32_t nH = 0, nT = 0;
     bool ok = true;
     float lsum = 0.f;
-    auto wait_acc = [&]() {
-      ok = ok && tc::mbar_wait(accbar, accs & 1, kLimit);
-      accs++;
+    auto wait_acc = [&](uint64_t* bar, uint32_t& n) {
+      ok = ok && tc::mbar_wait(bar, n & 1, kLimit);
+      n++;
       tc::fence_after();
     };
     // every thread publishes its shared-memory writes to the async proxy and
     // orders its TMEM loads; one lane per warp then arrives for the warp
-    auto arrive = [&]() {
+    auto arrive = [&](uint64_t* bar) {
       tc::fence_async_smem();
       tc::fence_before();
       __syncwarp();
-      if (lane == 0) tc::mbar_arrive(opbar);
+      if (lane == 0) tc::mbar_arrive(bar);
     };
-    for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
-      const int64_t p = t * 128 + r;
-      const bool valid = p < a.P;
-      if (qq < 2) {  // E0: z (f32) -> bf16 A operand, columns [8 qq, 8 qq + 8)
+    // E0: z (f32) of tile t -> bf16 A operand in buffer zb, columns [8 qq, 8 qq + 8)
+    auto stage_z = [&](int64_t t, uint32_t zb) {
+      if (qq < 2) {
+        const int64_t p = t * 128 + r;
         float4 f0 = make_float4(0.f, 0.f, 0.f, 0.f), f1 = f0;
-        if (valid) {
+        if (p < a.P) {
           const float4* src = reinterpret_cast<const float4*>(a.z + p * 16 + 8 * qq);
           f0 = src[0];
           f1 = src[1];
@@ -315,44 +380,47 @@ decode_fused_kernel(const __grid_constant__ FusedArgs a) {
         h[1] = __floats2bfloat162_rn(f0.z, f0.w);
         h[2] = __floats2bfloat162_rn(f1.x, f1.y);
         h[3] = __floats2bfloat162_rn(f1.z, f1.w);
-        *reinterpret_cast<uint4*>(sm + SM_Z + tc::core_offset(r, qq, 16)) = u;
+        *reinterpret_cast<uint4*>(sm + zb + tc::core_offset(r, qq, 16)) = u;
       }
-      arrive();
-      float v[32], pre[32];
-      // E1..E3: hidden forward layers (columns of this warp's quarter)
-      wait_acc();
-      {
-        const int c0 = 16 * qq;
-        tc::tmem_ld16(tb + c0, v);
+      arrive(opH);
+    };
+    float v[32], pre[32];
+    // E1..E3: forward hidden layers from TMEM columns 256-511 (this warp's
+    // column quarter), GELU, BF16 activations into shared memory
+    auto e1 = [&]() {
+      wait_acc(accH, nH);
+      const int c0 = 16 * qq;
+      tc::tmem_ld16(tb + 256 + c0, v);
 #pragma unroll
-        for (int i = 0; i < 16; i += 2) {
-          const float2 g = gelu_tanh2(__fadd2_rn(f2(v[i], v[i + 1]),
-                                                 *reinterpret_cast<const float2*>(sb4 + c0 + i)));
-          v[i] = g.x;
-          v[i + 1] = g.y;
-        }
-        put_row<16>(sm + SM_H1, r, c0, 64, v);
+      for (int i = 0; i < 16; i += 2) {
+        const float2 g = gelu_tanh2(__fadd2_rn(f2(v[i], v[i + 1]),
+                                               *reinterpret_cast<const float2*>(sb4 + c0 + i)));
+        v[i] = g.x;
+        v[i + 1] = g.y;
       }
-      arrive();
-      wait_acc();
-      {
-        const int c0 = 32 * qq;
-        tc::tmem_ld32(tb + c0, v);
+      put_row<16>(sm + SM_H1, r, c0, 64, v);
+      arrive(opH);
+    };
+    auto e2 = [&]() {
+      wait_acc(accH, nH);
+      const int c0 = 32 * qq;
+      tc::tmem_ld32(tb + 256 + c0, v);
 #pragma unroll
-        for (int i = 0; i < 32; i += 2) {
-          const float2 g = gelu_tanh2(__fadd2_rn(f2(v[i], v[i + 1]),
-                                                 *reinterpret_cast<const float2*>(sb5 + c0 + i)));
-          v[i] = g.x;
-          v[i + 1] = g.y;
-        }
-        put_row<32>(sm + SM_H2, r, c0, 128, v);
+      for (int i = 0; i < 32; i += 2) {
+        const float2 g = gelu_tanh2(__fadd2_rn(f2(v[i], v[i + 1]),
+                                               *reinterpret_cast<const float2*>(sb5 + c0 + i)));
+        v[i] = g.x;
+        v[i + 1] = g.y;
       }
-      arrive();
-      wait_acc();
+      put_row<32>(sm + SM_H2, r, c0, 128, v);
+      arrive(opH);
+    };
+    auto e3 = [&]() {
+      wait_acc(accH, nH);
 #pragma unroll 1
       for (int s2 = 0; s2 < 2; s2++) {
         const int c0 = 64 * qq + 32 * s2;
-        tc::tmem_ld32(tb + c0, v);
+        tc::tmem_ld32(tb + 256 + c0, v);
 #pragma unroll
         for (int i = 0; i < 32; i += 2) {
           const float2 g = gelu_tanh2(__fadd2_rn(f2(v[i], v[i + 1]),
@@ -362,86 +430,137 @@ decode_fused_kernel(const __grid_constant__ FusedArgs a) {
         }
         put_row<32>(sm + SM_H3, r, c0, 256, v);
       }
-      arrive();
+      arrive(opH);
+    };
+    // F_gt of output chunk c of tile t, loaded coalesced: slot i holds row
+    // 8 i + lane / 4 of this warp's 32 rows, 16-byte piece lane % 4 of its
+    // 32 columns (each load covers 8 rows x 64 contiguous bytes)
+    uint4 ld[4];
+    auto load_fgt = [&](int64_t t, int c) {
+      const int n0 = 128 * c + 32 * qq;
+#pragma unroll
+      for (int i = 0; i < 4; i++) {
+        const int64_t pr = t * 128 + 32 * q + 8 * i + (lane >> 2);
+        ld[i] = pr < a.P ? *reinterpret_cast<const uint4*>(a.target + pr * 512 + n0 + 8 * (lane & 3))
+                         : make_uint4(0u, 0u, 0u, 0u);
+      }
+    };
+    if (blockIdx.x < ntiles) {
+      const int64_t t = blockIdx.x;
+      stage_z(t, SM_Z);
+      e1();
+      e2();
+      load_fgt(t, 0);
+      e3();
+    }
+    int64_t k = 0;
+    for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x, k++) {
+      const bool next = t + gridDim.x < ntiles;
+      const int64_t p = t * 128 + r;
+      const bool valid = p < a.P;
+      // this warp's transpose buffer: the z buffer of the next tile (not
+      // written before E5 of this tile) for warps 0-7, a buffer of its own
+      // for warps 8-15
+      uint8_t* fg = sm + (warp < 8 ? SM_Z + (uint32_t)((k + 1) & 1) * 4096 + warp * 512
+                                   : SM_FGX + (warp - 8) * 512);
       // E4: output chunks, L1 against F_gt, dy into the chunk buffer
 #pragma unroll 1
       for (int c = 0; c < 4; c++) {
+        // round j: the 8 lanes holding piece j store it for all 32 rows, then
+        // every lane reads piece j of its own row
         uint4 tg[4];
-        const int n0 = 128 * c + 32 * qq;
-        if (valid) {
-          const uint4* src = reinterpret_cast<const uint4*>(a.target + p * 512 + n0);
 #pragma unroll
-          for (int k = 0; k < 4; k++) tg[k] = src[k];
+        for (int j = 0; j < 4; j++) {
+          __syncwarp();
+          if ((lane & 3) == j) {
+#pragma unroll
+            for (int i = 0; i < 4; i++)
+              *reinterpret_cast<uint4*>(fg + (8 * i + (lane >> 2)) * 16) = ld[i];
+          }
+          __syncwarp();
+          tg[j] = *reinterpret_cast<const uint4*>(fg + lane * 16);
         }
+        if (c < 3) load_fgt(t, c + 1);
+        const int n0 = 128 * c + 32 * qq;
         ok = ok && tc::mbar_wait(&ybar[c & 1], (c >> 1) & 1, kLimit);
         tc::fence_after();
-        tc::tmem_ld32(tb + 256 + 128 * (c & 1) + 32 * qq, v);
+        // two halves of 16 columns; dy = +-scale or 0, packed to BF16 at once
+        uint4 dy[4];
 #pragma unroll
-        for (int k = 0; k < 4; k++) {
-          const __nv_bfloat162* h2 = reinterpret_cast<const __nv_bfloat162*>(&tg[k]);
+        for (int h = 0; h < 2; h++) {
+          tc::tmem_ld16(tb + 256 + 128 * (c & 1) + 32 * qq + 16 * h, v);
 #pragma unroll
-          for (int e = 0; e < 4; e++) {
-            const float2 tt = valid ? __bfloat1622float2(h2[e]) : make_float2(0.f, 0.f);
-            const int i = 8 * k + 2 * e;
-            const float2 dd = __fadd2_rn(
-                __fadd2_rn(f2(v[i], v[i + 1]), *reinterpret_cast<const float2*>(sb7 + n0 + i)),
-                f2(-tt.x, -tt.y));
-            const float d0 = dd.x, d1 = dd.y;
-            if (valid) lsum += fabsf(d0) + fabsf(d1);
-            v[i] = valid ? (d0 > 0.f ? a.scale : (d0 < 0.f ? -a.scale : 0.f)) : 0.f;
-            v[i + 1] = valid ? (d1 > 0.f ? a.scale : (d1 < 0.f ? -a.scale : 0.f)) : 0.f;
+          for (int kk = 0; kk < 2; kk++) {
+            const __nv_bfloat162* h2 = reinterpret_cast<const __nv_bfloat162*>(&tg[2 * h + kk]);
+            __nv_bfloat162* o2 = reinterpret_cast<__nv_bfloat162*>(&dy[2 * h + kk]);
+#pragma unroll
+            for (int e = 0; e < 4; e++) {
+              const float2 tt = __bfloat1622float2(h2[e]);
+              const int i = 8 * kk + 2 * e;
+              const float2 dd = __fadd2_rn(
+                  __fadd2_rn(f2(v[i], v[i + 1]),
+                             *reinterpret_cast<const float2*>(sb7 + n0 + 16 * h + i)),
+                  f2(-tt.x, -tt.y));
+              const float d0 = dd.x, d1 = dd.y;
+              if (valid) lsum += fabsf(d0) + fabsf(d1);
+              o2[e] = __floats2bfloat162_rn(
+                  valid ? (d0 > 0.f ? a.scale : (d0 < 0.f ? -a.scale : 0.f)) : 0.f,
+                  valid ? (d1 > 0.f ? a.scale : (d1 < 0.f ? -a.scale : 0.f)) : 0.f);
+            }
           }
         }
         if (c > 0) {  // the previous chunk's product has read the dy buffer
           ok = ok && tc::mbar_wait(dyfree, (c - 1) & 1, kLimit);
           tc::fence_after();
         }
-        put_row<32>(sm + SM_DY, r, 32 * qq, 128, v);
-        arrive();
+#pragma unroll
+        for (int kk = 0; kk < 4; kk++)
+          *reinterpret_cast<uint4*>(sm + SM_DY + tc::core_offset(r, 4 * qq + kk, 128)) = dy[kk];
+        arrive(opT);
       }
       ok = ok && tc::mbar_wait(dyfree, 1, kLimit);  // the last chunk's phase
       tc::fence_after();
       // E5: d3 = dh3 * gelu'(pre3)
-      wait_acc();
+      wait_acc(accT, nT);
 #pragma unroll 1
-      for (int s2 = 0; s2 < 2; s2++) {
-        const int c0 = 64 * qq + 32 * s2;
-        tc::tmem_ld32(tb + c0, v);
-        tc::tmem_ld32(tb + 256 + c0, pre);
+      for (int s2 = 0; s2 < 4; s2++) {
+        const int c0 = 64 * qq + 16 * s2;
+        tc::tmem_ld16x2(tb + c0, v, tb + 256 + c0, pre);
 #pragma unroll
-        for (int i = 0; i < 32; i += 2) {
+        for (int i = 0; i < 16; i += 2) {
           const float2 g = gelu_tanh_grad2(__fadd2_rn(
               f2(pre[i], pre[i + 1]), *reinterpret_cast<const float2*>(sb6 + c0 + i)));
           const float2 d = __fmul2_rn(f2(v[i], v[i + 1]), g);
           v[i] = d.x;
           v[i + 1] = d.y;
         }
-        put_row<32>(sm + SM_H3, r, c0, 256, v);
+        put_row<16>(sm + SM_H3, r, c0, 256, v);
       }
-      arrive();
+      arrive(opT);
+      if (next) stage_z(t + gridDim.x, SM_Z + (uint32_t)((k + 1) & 1) * 4096);
       // E6: d2 = dh2 * gelu'(pre2)
-      wait_acc();
-      {
-        const int c0 = 32 * qq;
-        tc::tmem_ld32(tb + c0, v);
-        tc::tmem_ld32(tb + 128 + c0, pre);
+      wait_acc(accT, nT);
+#pragma unroll 1
+      for (int s2 = 0; s2 < 2; s2++) {
+        const int c0 = 32 * qq + 16 * s2;
+        tc::tmem_ld16x2(tb + c0, v, tb + 128 + c0, pre);
 #pragma unroll
-        for (int i = 0; i < 32; i += 2) {
+        for (int i = 0; i < 16; i += 2) {
           const float2 g = gelu_tanh_grad2(__fadd2_rn(
               f2(pre[i], pre[i + 1]), *reinterpret_cast<const float2*>(sb5 + c0 + i)));
           const float2 d = __fmul2_rn(f2(v[i], v[i + 1]), g);
           v[i] = d.x;
           v[i + 1] = d.y;
         }
-        put_row<32>(sm + SM_H2, r, c0, 128, v);
+        put_row<16>(sm + SM_H2, r, c0, 128, v);
       }
-      arrive();
-      // E7: d1 = dh1 * gelu'(pre1)
-      wait_acc();
+      arrive(opT);
+      if (next) e1();
+      // E7: d1 = dh1 * gelu'(pre1), into the dy buffer (free once R3 is done)
+      wait_acc(accT, nT);
       {
         const int c0 = 16 * qq;
-        tc::tmem_ld16(tb + c0, v);
-        tc::tmem_ld16(tb + 64 + c0, pre);
+        tc::tmem_ld16x2(tb + c0, v, tb + 64 + c0, pre);
 #pragma unroll
         for (int i = 0; i < 16; i += 2) {
           const float2 g = gelu_tanh_grad2(__fadd2_rn(
@@ -450,18 +569,25 @@ decode_fused_kernel(const __grid_constant__ FusedArgs a) {
           v[i] = d.x;
           v[i + 1] = d.y;
         }
-        put_row<16>(sm + SM_H1, r, c0, 64, v);
+        put_row<16>(sm + SM_DY, r, c0, 64, v);
       }
-      arrive();
+      arrive(opT);
+      if (next) e2();
       // E8: dz
-      wait_acc();
+      wait_acc(accT, nT);
       if (qq == 0) {
         tc::tmem_ld16(tb, v);
         if (valid) {
           float4* dst = reinterpret_cast<float4*>(a.dz + p * 16);
 #pragma unroll
-          for (int k = 0; k < 4; k++) dst[k] = make_float4(v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3]);
+          for (int kk = 0; kk < 4; kk++)
+            dst[kk] = make_float4(v[4 * kk], v[4 * kk + 1], v[4 * kk + 2], v[4 * kk + 3]);
         }
+      }
+      arrive(opT);
+      if (next) {
+        load_fgt(t + gridDim.x, 0);
+        e3();
       }
     }
     if (!ok) atomicOr(&g_fused_error, 4u);

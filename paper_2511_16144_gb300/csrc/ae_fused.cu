@@ -21,9 +21,9 @@
 // the F_gt transpose buffer of the output epilogue.
 // Warps 0-15 are the epilogue (TMEM -> registers -> shared memory; warps w,
 // w + 4, w + 8, w + 12 share TMEM lane quadrant w % 4 and split the columns in
-// quarters), warp 16 streams the weights as 51 pre-packed units (<= 16 KB
-// each, already in the tensor-core's canonical layout) through a 4-stage ring
-// with bulk TMA copies, warp 17 issues the MMAs.  Every wait is bounded.
+// quarters), warp 16 issues the MMAs, warps 17 and 18 stream the weights as
+// 51 pre-packed units (<= 16 KB each, already in the tensor-core's canonical
+// layout) through a 4-stage ring with bulk TMA copies.  Every wait is bounded.
 #include <mutex>
 #include <vector>
 
@@ -143,7 +143,7 @@ __device__ __forceinline__ void put_row(uint8_t* tile, int r, int col, int kw, c
 __device__ unsigned g_fused_error;
 
 constexpr int kEpiWarps = 16;
-constexpr int kFusedThreads = (kEpiWarps + 2) * 32;   // + producer warp + MMA warp
+constexpr int kFusedThreads = (kEpiWarps + 3) * 32;   // + MMA warp + two producer warps
 // barriers: full[kStages], empty[kStages], accH, accT, opH, opT, ybar[2],
 // dyfree, then the TMEM slot
 constexpr uint32_t kBarBytes = (2 * kStages + 7) * 8 + 4;
@@ -220,8 +220,11 @@ decode_fused_kernel(const __grid_constant__ FusedArgs a) {
   const uint32_t tmem = *tslot;
   const uint32_t sbase = tc::smem_addr(sm);
 
-  if (warp == kEpiWarps) {
-    // ---------------------------------------------------------------- producer
+  if (warp >= kEpiWarps + 1) {
+    // ---------------------------------------------------------------- producers
+    // A bulk copy holds its issuing thread for ~200 cycles, so two warps
+    // share the stream: producer pp copies the units with u % 2 == pp.
+    const uint32_t pp = (uint32_t)(warp - kEpiWarps - 1);
     if (lane == 0) {
       uint32_t u = 0;
       bool ok = true;
@@ -229,6 +232,7 @@ decode_fused_kernel(const __grid_constant__ FusedArgs a) {
         const bool first = t == blockIdx.x, next = t + gridDim.x < ntiles;
         const int n = stream_count(first, next);
         for (int j = 0; j < n; j++, u++) {
+          if ((u & 1) != pp) continue;
           const int i = stream_unit(first, next, j);
           const uint32_t s = u % kStages, round = u / kStages;
           if (round > 0 && !tc::mbar_wait(&empty[s], (round - 1) & 1, kLimit)) {
@@ -241,7 +245,7 @@ decode_fused_kernel(const __grid_constant__ FusedArgs a) {
       }
       if (!ok) atomicOr(&g_fused_error, 1u);
     }
-  } else if (warp == kEpiWarps + 1) {
+  } else if (warp == kEpiWarps) {
     // ---------------------------------------------------------------- MMA issuer
     // The whole warp walks the schedule (so descriptors and loop state stay
     // warp-uniform) and votes on every wait; one elected lane issues the MMAs

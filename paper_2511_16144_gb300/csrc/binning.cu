@@ -203,6 +203,20 @@ __device__ __forceinline__ uint32_t lane_lt() {
   return m;
 }
 
+// The lanes of a converged warp whose NB-bit digit equals this lane's: one
+// ballot per bit (short fixed-latency votes instead of a match instruction).
+template <int NB>
+__device__ __forceinline__ uint32_t digit_peers(uint32_t d) {
+  uint32_t peers = 0xffffffffu;
+#pragma unroll
+  for (int b = 0; b < NB; b++) {
+    const bool on = (d >> b) & 1u;
+    const uint32_t bal = __ballot_sync(0xffffffffu, on);
+    peers &= on ? bal : ~bal;
+  }
+  return peers;
+}
+
 // 4. one block per tile sorts its segment of 64-bit (depth bits, index)
 // keys.  Up to kSegMax keys: a stable LSD radix sort in shared memory, 8 bits
 // a pass, skipping the digits all keys share; each warp holds R consecutive
@@ -284,7 +298,7 @@ __device__ __noinline__ void big_segment_sort(unsigned long long* src, unsigned 
         const bool valid = p < cnt;
         key[r] = valid ? src[p] : 0ull;
         const uint32_t d = valid ? (uint32_t)(key[r] >> shift) & 0xffu : 256u + lane;
-        const uint32_t peers = __match_any_sync(0xffffffffu, d);
+        const uint32_t peers = digit_peers<9>(d);  // lanes past the end stay alone
         const uint32_t prior = valid ? wcnt[warp][d] : 0u;
         rank[r] = prior + __popc(peers & lane_lt());
         __syncwarp();
@@ -409,7 +423,7 @@ tile_sort_kernel(const uint2* __restrict__ ranges, unsigned long long* __restric
     for (int r = 0; r < kSegItems; r++) {
       if (r < R) {  // uniform over the block
         const uint32_t d = (uint32_t)(key[r] >> shift) & 0xffu;
-        const uint32_t peers = __match_any_sync(0xffffffffu, d);
+        const uint32_t peers = digit_peers<8>(d);
         const uint32_t prior = wcnt[warp][d];
         rank[r] = prior + __popc(peers & lane_lt());
         __syncwarp();

@@ -233,12 +233,16 @@ struct BwdSmem {
   static constexpr size_t g_off = 0;
   static constexpr size_t w_off = g_off + sizeof(float) * 16 * GROUP;
   static constexpr size_t p_off = w_off + sizeof(float) * 8 * kBwdBatch * WROW;
-  static constexpr size_t acc_off = p_off + sizeof(float) * 8 * kBwdBatch * WROW;
+  // two batch buffers (sums, channels, conic + opacity, means, ids): the
+  // next batch is staged while the current one is written out
+  static constexpr size_t st_off = p_off + sizeof(float) * 8 * kBwdBatch * WROW;
+  static constexpr size_t acc_off = 0;
   static constexpr size_t ch_off = acc_off + sizeof(float) * kBwdBatch * NV;
   static constexpr size_t co_off = (ch_off + sizeof(float) * kBwdBatch * NCH + 15) / 16 * 16;
   static constexpr size_t xy_off = co_off + sizeof(float4) * kBwdBatch;
   static constexpr size_t gid_off = xy_off + sizeof(float2) * kBwdBatch;
-  static constexpr size_t total = gid_off + sizeof(uint32_t) * kBwdBatch + 16;
+  static constexpr size_t stage = (gid_off + sizeof(uint32_t) * kBwdBatch + 15) / 16 * 16;
+  static constexpr size_t total = st_off + 2 * stage + 16;
 };
 
 template <int FC, typename TC, bool RGB>
@@ -251,11 +255,6 @@ render_bwd_kernel(RasterArgs A, int chunk_base) {
   float* s_g = reinterpret_cast<float*>(sm + L::g_off);
   float* s_w = reinterpret_cast<float*>(sm + L::w_off);
   float* s_p = reinterpret_cast<float*>(sm + L::p_off);
-  float* s_acc = reinterpret_cast<float*>(sm + L::acc_off);
-  float* s_ch = reinterpret_cast<float*>(sm + L::ch_off);
-  float4* s_co = reinterpret_cast<float4*>(sm + L::co_off);
-  float2* s_xy = reinterpret_cast<float2*>(sm + L::xy_off);
-  uint32_t* s_gid = reinterpret_cast<uint32_t*>(sm + L::gid_off);
   __shared__ uint32_t s_maxlast;
 
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -309,17 +308,34 @@ render_bwd_kernel(RasterArgs A, int chunk_base) {
   __syncthreads();
   const int blk_last = (int)s_maxlast;
 
-  for (int hi = blk_last; hi > 0; hi -= B) {
-    const int lo = max(hi - B, 0), nb = hi - lo;
-    __syncthreads();  // the previous batch's reduction has read everything
-    for (int i = threadIdx.x; i < B * NV; i += kThreads) s_acc[i] = 0.f;
-    if ((int)threadIdx.x < nb) {
-      uint32_t gid = A.ids[range.x + lo + threadIdx.x];
-      s_gid[threadIdx.x] = gid;
-      stage_instance<FC, TC, RGB>(A, projbase, gid, f0, s_xy[threadIdx.x], s_co[threadIdx.x],
-                                  s_ch + threadIdx.x * NCH);
+  // batch buffer `buf`: sums, channels, conic + opacity, means, Gaussian ids
+  auto stage_at = [&](int buf) { return sm + L::st_off + (size_t)buf * L::stage; };
+  // zero the sums of buffer `buf` and stage the batch [lo, hi) into it
+  auto stage_batch = [&](int buf, int lo, int hi) {
+    char* st = stage_at(buf);
+    float* acc = reinterpret_cast<float*>(st + L::acc_off);
+    for (int i = threadIdx.x; i < B * NV; i += kThreads) acc[i] = 0.f;
+    if ((int)threadIdx.x < hi - lo) {
+      const uint32_t gid = A.ids[range.x + lo + threadIdx.x];
+      reinterpret_cast<uint32_t*>(st + L::gid_off)[threadIdx.x] = gid;
+      stage_instance<FC, TC, RGB>(A, projbase, gid, f0,
+                                  reinterpret_cast<float2*>(st + L::xy_off)[threadIdx.x],
+                                  reinterpret_cast<float4*>(st + L::co_off)[threadIdx.x],
+                                  reinterpret_cast<float*>(st + L::ch_off) + threadIdx.x * NCH);
     }
-    __syncthreads();
+  };
+  if (blk_last > 0) stage_batch(0, max(blk_last - B, 0), blk_last);
+  __syncthreads();
+
+  int buf = 0;
+  for (int hi = blk_last; hi > 0; hi -= B, buf ^= 1) {
+    const int lo = max(hi - B, 0), nb = hi - lo;
+    char* st = stage_at(buf);
+    float* s_acc = reinterpret_cast<float*>(st + L::acc_off);
+    const float* s_ch = reinterpret_cast<const float*>(st + L::ch_off);
+    const float4* s_co = reinterpret_cast<const float4*>(st + L::co_off);
+    const float2* s_xy = reinterpret_cast<const float2*>(st + L::xy_off);
+    const uint32_t* s_gid = reinterpret_cast<const uint32_t*>(st + L::gid_off);
 
     // phase 1: per pixel, back to front through the batch (a warp whose
     // pixels all end before this batch has nothing to add to it)
@@ -417,7 +433,11 @@ render_bwd_kernel(RasterArgs A, int chunk_base) {
         for (int v = 0; v < NV / 2; v++) atomicAdd(dst + v, keep[v]);
       }
     }
-    __syncthreads();
+    __syncthreads();  // the batch's sums are complete
+
+    // the next batch goes into the other buffer, whose last readers (phase 3
+    // of the batch before this one) finished before the previous barrier
+    if (hi - B > 0) stage_batch(buf ^ 1, max(hi - 2 * B, 0), hi - B);
 
     // phase 3: one global update per (tile, instance)
     if ((int)threadIdx.x < nb) {
@@ -454,6 +474,7 @@ render_bwd_kernel(RasterArgs A, int chunk_base) {
                   make_float4(src[0], src[1], src[2], src[3]));
       }
     }
+    __syncthreads();  // the next batch is staged; this one has been read
   }
 }
 

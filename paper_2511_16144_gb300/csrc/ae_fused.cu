@@ -25,6 +25,7 @@
 // 51 pre-packed units (<= 16 KB each, already in the tensor-core's canonical
 // layout) through a 4-stage ring with bulk TMA copies.  Every wait is bounded.
 #include <mutex>
+#include <type_traits>
 #include <vector>
 
 #include "common.cuh"
@@ -405,35 +406,40 @@ decode_fused_kernel(const __grid_constant__ FusedArgs a) {
       put_row<16>(sm + SM_H1, r, c0, 64, v);
       arrive(opH);
     };
+    // GELU of NS consecutive 16-column slices from column c0 of the forward
+    // accumulator into the BF16 tile (width kw); the next slice's TMEM load
+    // is in flight while a slice is computed
+    auto gelu_slices = [&](auto ns, int c0, const float* bias, uint8_t* tile, int kw) {
+      constexpr int NS = decltype(ns)::value;
+      uint32_t ra[16], rb[16];
+      tc::tmem_ld16_issue(tb + 256 + c0, ra);
+      tc::tmem_wait16(ra);
+#pragma unroll
+      for (int s2 = 0; s2 < NS; s2++) {
+        const int cc = c0 + 16 * s2;
+        uint32_t* cur = (s2 & 1) ? rb : ra;
+        uint32_t* nxt = (s2 & 1) ? ra : rb;
+        if (s2 + 1 < NS) tc::tmem_ld16_issue(tb + 256 + cc + 16, nxt);
+#pragma unroll
+        for (int i = 0; i < 16; i += 2) {
+          const float2 g = gelu_tanh2(
+              __fadd2_rn(f2(__uint_as_float(cur[i]), __uint_as_float(cur[i + 1])),
+                         *reinterpret_cast<const float2*>(bias + cc + i)));
+          v[i] = g.x;
+          v[i + 1] = g.y;
+        }
+        put_row<16>(tile, r, cc, kw, v);
+        if (s2 + 1 < NS) tc::tmem_wait16(nxt);
+      }
+    };
     auto e2 = [&]() {
       wait_acc(accH, nH);
-      const int c0 = 32 * qq;
-      tc::tmem_ld32(tb + 256 + c0, v);
-#pragma unroll
-      for (int i = 0; i < 32; i += 2) {
-        const float2 g = gelu_tanh2(__fadd2_rn(f2(v[i], v[i + 1]),
-                                               *reinterpret_cast<const float2*>(sb5 + c0 + i)));
-        v[i] = g.x;
-        v[i + 1] = g.y;
-      }
-      put_row<32>(sm + SM_H2, r, c0, 128, v);
+      gelu_slices(std::integral_constant<int, 2>(), 32 * qq, sb5, sm + SM_H2, 128);
       arrive(opH);
     };
     auto e3 = [&]() {
       wait_acc(accH, nH);
-#pragma unroll 1
-      for (int s2 = 0; s2 < 2; s2++) {
-        const int c0 = 64 * qq + 32 * s2;
-        tc::tmem_ld32(tb + 256 + c0, v);
-#pragma unroll
-        for (int i = 0; i < 32; i += 2) {
-          const float2 g = gelu_tanh2(__fadd2_rn(f2(v[i], v[i + 1]),
-                                                 *reinterpret_cast<const float2*>(sb6 + c0 + i)));
-          v[i] = g.x;
-          v[i + 1] = g.y;
-        }
-        put_row<32>(sm + SM_H3, r, c0, 256, v);
-      }
+      gelu_slices(std::integral_constant<int, 4>(), 64 * qq, sb6, sm + SM_H3, 256);
       arrive(opH);
     };
     // F_gt of output chunk c of tile t, loaded coalesced: slot i holds row
@@ -488,11 +494,18 @@ decode_fused_kernel(const __grid_constant__ FusedArgs a) {
         const int n0 = 128 * c + 32 * qq;
         ok = ok && tc::mbar_wait(&ybar[c & 1], (c >> 1) & 1, kLimit);
         tc::fence_after();
-        // two halves of 16 columns; dy = +-scale or 0, packed to BF16 at once
+        // two halves of 16 columns (the second's TMEM load in flight while the
+        // first is computed); dy = +-scale or 0, packed to BF16 at once
         uint4 dy[4];
+        uint32_t ya[16], yb[16];
+        const uint32_t ty = tb + 256 + 128 * (c & 1) + 32 * qq;
+        tc::tmem_ld16_issue(ty, ya);
+        tc::tmem_wait16(ya);
+        tc::tmem_ld16_issue(ty + 16, yb);
 #pragma unroll
         for (int h = 0; h < 2; h++) {
-          tc::tmem_ld16(tb + 256 + 128 * (c & 1) + 32 * qq + 16 * h, v);
+          if (h == 1) tc::tmem_wait16(yb);
+          const uint32_t* yv = h ? yb : ya;
 #pragma unroll
           for (int kk = 0; kk < 2; kk++) {
             const __nv_bfloat162* h2 = reinterpret_cast<const __nv_bfloat162*>(&tg[2 * h + kk]);
@@ -502,7 +515,7 @@ decode_fused_kernel(const __grid_constant__ FusedArgs a) {
               const float2 tt = __bfloat1622float2(h2[e]);
               const int i = 8 * kk + 2 * e;
               const float2 dd = __fadd2_rn(
-                  __fadd2_rn(f2(v[i], v[i + 1]),
+                  __fadd2_rn(f2(__uint_as_float(yv[i]), __uint_as_float(yv[i + 1])),
                              *reinterpret_cast<const float2*>(sb7 + n0 + 16 * h + i)),
                   f2(-tt.x, -tt.y));
               const float d0 = dd.x, d1 = dd.y;
@@ -526,37 +539,57 @@ decode_fused_kernel(const __grid_constant__ FusedArgs a) {
       tc::fence_after();
       // E5: d3 = dh3 * gelu'(pre3)
       wait_acc(accT, nT);
-#pragma unroll 1
-      for (int s2 = 0; s2 < 4; s2++) {
-        const int c0 = 64 * qq + 16 * s2;
-        tc::tmem_ld16x2(tb + c0, v, tb + 256 + c0, pre);
+      {  // the next 16 columns' loads are in flight while these are computed
+        uint32_t ra[32], rb[32];
+        tc::tmem_ld16x2_issue(tb + 64 * qq, tb + 256 + 64 * qq, ra);
+        tc::tmem_wait32(ra);
 #pragma unroll
-        for (int i = 0; i < 16; i += 2) {
-          const float2 g = gelu_tanh_grad2(__fadd2_rn(
-              f2(pre[i], pre[i + 1]), *reinterpret_cast<const float2*>(sb6 + c0 + i)));
-          const float2 d = __fmul2_rn(f2(v[i], v[i + 1]), g);
-          v[i] = d.x;
-          v[i + 1] = d.y;
+        for (int s2 = 0; s2 < 4; s2++) {
+          const int c0 = 64 * qq + 16 * s2;
+          uint32_t* cur = (s2 & 1) ? rb : ra;
+          uint32_t* nxt = (s2 & 1) ? ra : rb;
+          if (s2 < 3) tc::tmem_ld16x2_issue(tb + c0 + 16, tb + 256 + c0 + 16, nxt);
+#pragma unroll
+          for (int i = 0; i < 16; i += 2) {
+            const float2 g = gelu_tanh_grad2(__fadd2_rn(
+                f2(__uint_as_float(cur[16 + i]), __uint_as_float(cur[17 + i])),
+                *reinterpret_cast<const float2*>(sb6 + c0 + i)));
+            const float2 d =
+                __fmul2_rn(f2(__uint_as_float(cur[i]), __uint_as_float(cur[i + 1])), g);
+            v[i] = d.x;
+            v[i + 1] = d.y;
+          }
+          put_row<16>(sm + SM_H3, r, c0, 256, v);
+          if (s2 < 3) tc::tmem_wait32(nxt);
         }
-        put_row<16>(sm + SM_H3, r, c0, 256, v);
       }
       arrive(opT);
       if (next) stage_z(t + gridDim.x, SM_Z + (uint32_t)((k + 1) & 1) * 4096);
       // E6: d2 = dh2 * gelu'(pre2)
       wait_acc(accT, nT);
-#pragma unroll 1
-      for (int s2 = 0; s2 < 2; s2++) {
-        const int c0 = 32 * qq + 16 * s2;
-        tc::tmem_ld16x2(tb + c0, v, tb + 128 + c0, pre);
+      {
+        uint32_t ra[32], rb[32];
+        tc::tmem_ld16x2_issue(tb + 32 * qq, tb + 128 + 32 * qq, ra);
+        tc::tmem_wait32(ra);
 #pragma unroll
-        for (int i = 0; i < 16; i += 2) {
-          const float2 g = gelu_tanh_grad2(__fadd2_rn(
-              f2(pre[i], pre[i + 1]), *reinterpret_cast<const float2*>(sb5 + c0 + i)));
-          const float2 d = __fmul2_rn(f2(v[i], v[i + 1]), g);
-          v[i] = d.x;
-          v[i + 1] = d.y;
+        for (int s2 = 0; s2 < 2; s2++) {
+          const int c0 = 32 * qq + 16 * s2;
+          uint32_t* cur = (s2 & 1) ? rb : ra;
+          uint32_t* nxt = (s2 & 1) ? ra : rb;
+          if (s2 < 1) tc::tmem_ld16x2_issue(tb + c0 + 16, tb + 128 + c0 + 16, nxt);
+#pragma unroll
+          for (int i = 0; i < 16; i += 2) {
+            const float2 g = gelu_tanh_grad2(__fadd2_rn(
+                f2(__uint_as_float(cur[16 + i]), __uint_as_float(cur[17 + i])),
+                *reinterpret_cast<const float2*>(sb5 + c0 + i)));
+            const float2 d =
+                __fmul2_rn(f2(__uint_as_float(cur[i]), __uint_as_float(cur[i + 1])), g);
+            v[i] = d.x;
+            v[i + 1] = d.y;
+          }
+          put_row<16>(sm + SM_H2, r, c0, 128, v);
+          if (s2 < 1) tc::tmem_wait32(nxt);
         }
-        put_row<16>(sm + SM_H2, r, c0, 128, v);
       }
       arrive(opT);
       if (next) e1();

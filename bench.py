@@ -420,8 +420,8 @@ def per_call_times(step, flush, reps=5):
 # ncu DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) per launch
 # of each call group at this workload, from the capture summarised under
 # profiles/; None once the kernel has changed since the capture.
-TRAFFIC = {"gs_project": 13217024, "gs_bin_sort": 31389696, "gs_render_fwd": 3311616,
-           "l1_losses": 9845504, "ae_decode": 349475072, "gs_render_bwd": 41840128}
+TRAFFIC = {"gs_project": 13216768, "gs_bin_sort": 31381760, "gs_render_fwd": 3332864,
+           "l1_losses": 9845248, "ae_decode": 349998592, "gs_render_bwd": 41834240}
 
 
 def rooflines(step, calls):

@@ -94,9 +94,11 @@ class MappingStep:
                                 p(o["T_final"]), p(o["last"]), None, lgs._stream()),
                 "gs_render_fwd")
 
-        def losses():
+        def zero_loss():
+            chk(L.lgs_zero(p(self.loss), 4, lgs._stream()), "lgs_zero")
+
+        def l1_terms():
             s = lgs._stream()
-            chk(L.lgs_zero(p(self.loss), 4, s), "lgs_zero")
             chk(L.lgs_l1_loss(p(o["rgb"]), p(self.rgb_t), lgs.F32, o["rgb"].numel(), 1.0,
                               p(self.d_rgb), p(self.loss), s), "lgs_l1_loss")
             chk(L.lgs_l1_loss(p(o["depth"]), p(self.depth_t), lgs.F32, o["depth"].numel(),
@@ -110,10 +112,17 @@ class MappingStep:
                             p(self.feat_t), self.w_feat, p(self.loss), p(self.d_feat), None,
                             p(self.ae_ws), self.ae_ws.numel(), lgs._stream()), "ae_decode")
 
-        def render_bwd():
+        def losses():
+            zero_loss()
+            l1_terms()
+
+        def zero_grads():
             s = lgs._stream()
             for t in g.values():
                 chk(L.lgs_zero(p(t), t.numel() * 4, s), "lgs_zero")
+
+        def backward():
+            s = lgs._stream()
             chk(L.gs_render_bwd(p(sc.means), p(sc.quats), p(sc.log_scales), p(sc.opacity_logits),
                                 p(self.proj), p(b.ids), p(b.ranges), sc.n, self.ca, c,
                                 p(sc.colors), p(sc.feats), self.D, lgs._dtype_code(sc.feats),
@@ -122,6 +131,12 @@ class MappingStep:
                                 p(g["quats"]), p(g["log_scales"]), p(g["opacity_logits"]),
                                 p(g["colors"]), p(g["feats"]), s), "gs_render_bwd")
 
+        def render_bwd():
+            zero_grads()
+            backward()
+
+        self._parts = dict(zero_loss=zero_loss, l1_terms=l1_terms, decode=decode,
+                           zero_grads=zero_grads, backward=backward)
         out = [("gs_project", project), ("gs_bin_sort", bin_sort),
                ("gs_render_fwd", render_fwd), ("l1_losses", losses)]
         if self.model is not None:
@@ -130,9 +145,36 @@ class MappingStep:
         return out
 
     def run(self):
-        """Enqueues one step on the current stream (no synchronisation)."""
-        for _, fn in self.calls():
-            fn()
+        """Enqueues one step on the current stream (no synchronisation).
+
+        With the decoder, the L1 terms of RGB and depth and the zeroing of the
+        parameter gradients do not depend on it: they run on a side stream
+        beside it (a parallel branch when the step is captured in a graph),
+        joined before the backward.  The loss is zeroed before the fork, as
+        both branches add to it."""
+        calls = self.calls()
+        if self.model is None:
+            for _, fn in calls:
+                fn()
+            return
+        fns = dict(calls)
+        part = self._parts
+        for name in ("gs_project", "gs_bin_sort", "gs_render_fwd"):
+            fns[name]()
+        part["zero_loss"]()
+        main = torch.cuda.current_stream()
+        if getattr(self, "_side", None) is None or self._side.device != main.device:
+            self._side = torch.cuda.Stream(device=main.device)
+        fork, join = torch.cuda.Event(), torch.cuda.Event()
+        fork.record(main)
+        self._side.wait_event(fork)
+        with torch.cuda.stream(self._side):
+            part["l1_terms"]()
+            part["zero_grads"]()
+            join.record(self._side)
+        part["decode"]()
+        main.wait_event(join)
+        part["backward"]()
 
     def count_blended(self):
         """Number blended per pixel for the last forward (re-runs the forward

@@ -324,6 +324,7 @@ def run_gpu(args, rank, world):
     # loss comes back
     prune = measure_prune(s16_bf, flush)
     extras = measure_loss_pose(step16, flush)
+    ae_rf = measure_autoencoder(enc, dec, g512_bf, flush, dev)
     extras.update(measure_loop_query(step16, f_gt, flush))
 
     rgb_b, dep_b, fgt_b = rgb_t.clone(), dep_t.clone(), f_gt.clone()
@@ -356,6 +357,7 @@ def run_gpu(args, rank, world):
             "per_call_ms": calls,
             "ae_pretrain": {"steps": args.ae_steps, "loss_first": ae_losses[0],
                             "loss_last": ae_losses[-1], "seconds": ae_train_s},
+            "autoencoder": ae_rf,
             "cpu_baseline": cpu,
         }
         print(json.dumps(line), flush=True)
@@ -655,6 +657,65 @@ def measure_loop_query(step, f_gt, flush, reps=20, K=256, Q=8):
         "peak": float(peaks["hbm_gbs"]), "unit": "GB/s",
         "frac": byts / (out["query_relevance_ms"] / 1e3) / 1e9 / float(peaks["hbm_gbs"]),
         "peak_source": kind + " copy", "queries": Q}
+    return out
+
+
+def measure_autoencoder(enc, dec, g512_bf, flush, dev, reps=20):
+    """Roofline of the autoencoder calls outside the step: one ae_train_step
+    (RECON, 65,536 pixels: forward, gradient to the activations and to the
+    weights, and Adam, for encoder and decoder) and one ae_encode of the
+    Gaussians' 512-d features, each captured in a CUDA graph and replayed
+    between CUDA events with L2 flushed before every replay.  A fresh model
+    from the same initialisation is used, so the timed Adam steps leave the
+    benchmarked one untouched."""
+    import torch
+    from paper_2511_16144_gb300 import lgs
+    from paper_2511_16144_gb300.ae import AutoEncoder
+    peaks, kind = measured_peaks()
+    m = AutoEncoder(enc, dec, device=dev)
+    gen = torch.Generator(device=dev).manual_seed(7)
+    x = g512_bf[torch.randint(0, g512_bf.shape[0], (65536,), device=dev, generator=gen)].contiguous()
+    loss = torch.zeros(1, device=dev)
+
+    def timed_graph(fn):
+        fn()
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            fn()
+        ts = []
+        for _ in range(reps + 2):
+            flush.fill_(1.0)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            g.replay()
+            b.record()
+            b.synchronize()
+            ts.append(a.elapsed_time(b))
+        del g
+        return float(np.mean(ts[2:]))
+
+    out = {}
+    ms = timed_graph(lambda: m.train_step(x, lr=1e-4, loss=loss))
+    flop = 2 * 3 * 346112 * x.shape[0]  # (forward, dX, dW) x (encoder + decoder) MACs, x 2
+    out["ae_train_step"] = {
+        "pixels": int(x.shape[0]), "ms": ms,
+        "roofline": {"bound": "tensor", "achieved": flop / (ms * 1e-3) / 1e12,
+                     "peak": peaks["bf16_tflops"], "unit": "TFLOP/s",
+                     "frac": flop / (ms * 1e-3) / 1e12 / peaks["bf16_tflops"], "traffic": None,
+                     "peak_source": kind + " bf16 burst",
+                     "note": "about 50 launches (8 layers forward, backward, weight gradient, bias sums, Adam, repacks)"}}
+    z = torch.empty((g512_bf.shape[0], 16), dtype=torch.float32, device=dev)
+    ws = m._ws.get("enc")
+    ms = timed_graph(lambda: lgs.ae_encode(m.weights, g512_bf, z, ws=ws))
+    flop = 2 * 173056 * g512_bf.shape[0]
+    out["ae_encode"] = {
+        "pixels": int(g512_bf.shape[0]), "ms": ms,
+        "roofline": {"bound": "tensor", "achieved": flop / (ms * 1e-3) / 1e12,
+                     "peak": peaks["bf16_tflops"], "unit": "TFLOP/s",
+                     "frac": flop / (ms * 1e-3) / 1e12 / peaks["bf16_tflops"], "traffic": None,
+                     "peak_source": kind + " bf16 burst"}}
+    del m
     return out
 
 

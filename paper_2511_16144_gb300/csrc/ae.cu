@@ -604,11 +604,8 @@ struct Carver {
   }
 };
 
-static void carve_encode(Carver& c, int64_t P, __nv_bfloat16** h) {
-  h[0] = c.bf(P, 256);
-  h[1] = c.bf(P, 128);
-  h[2] = c.bf(P, 64);
-}
+// The fused encoder keeps its activations on chip: only the packed weights.
+static void* carve_encode(Carver& c) { return c.bf(1, (int)(encode_pack_bytes() / 2)); }
 
 struct DecodeBufs {
   __nv_bfloat16* a[3];
@@ -651,8 +648,7 @@ extern "C" size_t ae_workspace_bytes(int64_t P, int what) {
   if (P < 0) return 0;
   Carver c(nullptr);
   if (what == LGS_AE_ENCODE) {
-    __nv_bfloat16* h[3];
-    carve_encode(c, P, h);
+    carve_encode(c);
   } else if (what == LGS_AE_DECODE) {
     DecodeBufs B;
     carve_decode(c, P, B);
@@ -677,17 +673,8 @@ extern "C" lgs_status ae_encode(const lgs_ae_weights* w, const uint16_t* x, int6
   LGS_CHECK_ARG(workspace_bytes >= ae_workspace_bytes(P, LGS_AE_ENCODE), "workspace too small");
   cudaStream_t s = as_stream(stream);
   Carver c(workspace);
-  __nv_bfloat16* h[3];
-  carve_encode(c, P, h);
-  LayerArgs a;
-  a = layer(x, false, w->W[0], w->b[0], P, 512, 256, EPI_GELU); a.out_bf = h[0];
-  if ((st = launch_layer(a, s)) != LGS_OK) return st;
-  a = layer(h[0], false, w->W[1], w->b[1], P, 256, 128, EPI_GELU); a.out_bf = h[1];
-  if ((st = launch_layer(a, s)) != LGS_OK) return st;
-  a = layer(h[1], false, w->W[2], w->b[2], P, 128, 64, EPI_GELU); a.out_bf = h[2];
-  if ((st = launch_layer(a, s)) != LGS_OK) return st;
-  a = layer(h[2], false, w->W[3], w->b[3], P, 64, 16, EPI_LIN_F32); a.out_f32 = z;
-  return launch_layer(a, s);
+  void* pack = carve_encode(c);
+  return launch_encode_fused(w, x, P, z, pack, s);
 }
 
 extern "C" lgs_status ae_decode(const lgs_ae_weights* w, const float* z, int64_t P,
@@ -899,6 +886,7 @@ extern "C" lgs_status lgs_device_error(int* code) {
   unsigned v = 0, zero = 0;
   LGS_CHECK_CUDA(cudaMemcpyFromSymbol(&v, g_ae_error, sizeof(v)));
   LGS_CHECK_CUDA(cudaMemcpyToSymbol(g_ae_error, &zero, sizeof(zero)));
-  *code = (int)(v | (fused_error_word() << 4) | (sort_error_word() << 8));
+  *code = (int)(v | (fused_error_word() << 4) | (sort_error_word() << 8) |
+                 (encode_error_word() << 12));
   return LGS_OK;
 }

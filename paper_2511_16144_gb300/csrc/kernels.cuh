@@ -23,6 +23,13 @@ lgs_status launch_decode_fused(const lgs_ae_weights* w, const float* z, int64_t 
                                void* pack, cudaStream_t s);
 // Reads and clears the fused kernel's timeout word.
 unsigned fused_error_word();
+// Fused encoder z = E(x) (x bf16 [P,512] -> z f32 [P,16]); `pack` is
+// encode_pack_bytes() of scratch for the packed weights.
+size_t encode_pack_bytes();
+lgs_status launch_encode_fused(const lgs_ae_weights* w, const uint16_t* x, int64_t P, float* z,
+                               void* pack, cudaStream_t s);
+// Reads and clears the fused encoder's timeout word.
+unsigned encode_error_word();
 // Stable LSD radix sort of n (key, value) pairs on key bits [0, nbits)
 // (nbits <= 32), one onesweep kernel per 8 bits.  `scratch` holds
 // sort_pairs_scratch(n) bytes (256-byte aligned) and is cleared here.

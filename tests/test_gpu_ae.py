@@ -51,6 +51,29 @@ def test_encode_matches_oracle(lgs):
     assert np.percentile(per, 99) < 3 * REL
 
 
+def test_encode_many_tiles(lgs):
+    """The fused encoder with several tiles per CTA (alternating TMEM halves,
+    the next tile's first layer under the current tile's epilogue) and a
+    ragged last tile, against the oracle."""
+    from oracle import ae
+    from paper_2511_16144_gb300.ae import AutoEncoder
+    enc, dec = synth.ae_init(seed=3009)
+    model = AutoEncoder(enc, dec)
+    rng = np.random.default_rng(9)
+    P = 152 * 128 * 3 + 77
+    x = synth.unit_rows(rng.standard_normal((P, 512))).astype(np.float32)
+    xt = torch.from_numpy(x).cuda().bfloat16()
+    z = model.encode(xt).cpu().numpy()
+    zr = ae.encode(rounded(enc), bf16_round(x))
+    assert rel_err(z, zr) < REL
+    per = np.linalg.norm(z - zr, axis=1) / np.linalg.norm(zr, axis=1)
+    assert np.percentile(per, 99) < 3 * REL
+    # a second call (the packed weights and the tensor map rebuilt) agrees
+    z2 = model.encode(xt).cpu().numpy()
+    assert np.array_equal(z, z2)
+    assert lgs.lgs_device_error() == 0
+
+
 def test_decode_and_distillation_match_oracle(lgs):
     from oracle import ae
     from paper_2511_16144_gb300.ae import AutoEncoder

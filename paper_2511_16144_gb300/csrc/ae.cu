@@ -23,7 +23,9 @@
 //   dw_kernel<KT>: dW[N, K] += sum_p G[p, n] X[p, k] over a pixel range; the
 //     pixel dimension is the MMA's K, so both operands are transposed in 8x8
 //     blocks while staging.
-//   colsum, adam and pack kernels (SIMT).
+//   colsum, adam_all and pack_all kernels (SIMT; one launch for every layer).
+#include <algorithm>
+
 #include "common.cuh"
 #include "kernels.cuh"
 #include "tc05.cuh"
@@ -483,40 +485,87 @@ __global__ void __launch_bounds__(128, 1) dw_kernel(DwArgs a) {
 }
 
 // db[n] += sum_p G[p][n]
-__global__ void colsum_kernel(const __nv_bfloat16* __restrict__ G, int64_t P, int N,
-                              int rows_per_block, float* __restrict__ db) {
+// db[n] += sum_p G[p, n] over a block of rows: every thread adds 8 adjacent
+// columns (one 16-byte load) of every (256 / (N / 8))-th row, the block
+// combines them in shared memory and adds one value per column to db.
+// N is a multiple of 8 dividing 2048 (16 ... 512).
+__global__ void __launch_bounds__(256) colsum_kernel(const __nv_bfloat16* __restrict__ G, int64_t P,
+                                                     int N, int rows_per_block,
+                                                     float* __restrict__ db) {
+  extern __shared__ float s_col[];  // [N]
+  for (int i = threadIdx.x; i < N; i += blockDim.x) s_col[i] = 0.f;
+  __syncthreads();
+  const int groups = N / 8, cg = threadIdx.x % groups, rstep = blockDim.x / groups;
   const int64_t p0 = (int64_t)blockIdx.x * rows_per_block;
   const int64_t p1 = min(P, p0 + rows_per_block);
-  for (int n = threadIdx.x; n < N; n += blockDim.x) {
-    float s = 0.f;
-    for (int64_t p = p0; p < p1; p++) s += __bfloat162float(G[p * N + n]);
-    atomicAdd(db + n, s);
+  float acc[8];
+#pragma unroll
+  for (int k = 0; k < 8; k++) acc[k] = 0.f;
+#pragma unroll 4
+  for (int64_t p = p0 + threadIdx.x / groups; p < p1; p += rstep) {
+    const uint4 u = *reinterpret_cast<const uint4*>(G + p * N + 8 * cg);
+    const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&u);
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+      const float2 f = __bfloat1622float2(h[k]);
+      acc[2 * k] += f.x;
+      acc[2 * k + 1] += f.y;
+    }
   }
+#pragma unroll
+  for (int k = 0; k < 8; k++) atomicAdd(&s_col[8 * cg + k], acc[k]);
+  __syncthreads();
+  for (int i = threadIdx.x; i < N; i += blockDim.x) atomicAdd(db + i, s_col[i]);
 }
 
-__global__ void adam_kernel(float* __restrict__ w, float* __restrict__ m, float* __restrict__ v,
-                            const float* __restrict__ g, int64_t n, float lr, float bc1, float bc2) {
+// Adam on up to 2 * kAeLayers parameter tensors in one launch: segment j
+// holds elements [start[j], start[j + 1]) of the concatenation.
+struct AdamSegs {
+  float* w[2 * kAeLayers];
+  float* m[2 * kAeLayers];
+  float* v[2 * kAeLayers];
+  const float* g[2 * kAeLayers];
+  int64_t start[2 * kAeLayers + 1];
+  int n;
+};
+__global__ void adam_all_kernel(const __grid_constant__ AdamSegs S, float lr, float bc1, float bc2) {
   const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    const float gi = g[i];
-    const float mi = b1 * m[i] + (1.f - b1) * gi;
-    const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
-    m[i] = mi;
-    v[i] = vi;
-    w[i] -= lr * (mi / bc1) / (sqrtf(vi / bc2) + eps);
+  const int64_t total = S.start[S.n];
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    int j = 0;
+    while (S.start[j + 1] <= e) j++;
+    const int64_t i = e - S.start[j];
+    const float gi = S.g[j][i];
+    const float mi = b1 * S.m[j][i] + (1.f - b1) * gi;
+    const float vi = b2 * S.v[j][i] + (1.f - b2) * gi * gi;
+    S.m[j][i] = mi;
+    S.v[j][i] = vi;
+    S.w[j][i] -= lr * (mi / bc1) / (sqrtf(vi / bc2) + eps);
   }
 }
 
-// W [N][K] fp32 -> Wb [N][K] and Wt [K][N] bf16
-__global__ void pack_kernel(const float* __restrict__ W, int N, int K, __nv_bfloat16* __restrict__ Wb,
-                            __nv_bfloat16* __restrict__ Wt) {
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < (int64_t)N * K;
-       i += (int64_t)gridDim.x * blockDim.x) {
+// BF16 copies W and W^T of up to kAeLayers layers in one launch.
+struct PackSegs {
+  const float* W[kAeLayers];
+  __nv_bfloat16* Wb[kAeLayers];
+  __nv_bfloat16* Wt[kAeLayers];
+  int N[kAeLayers], K[kAeLayers];
+  int64_t start[kAeLayers + 1];
+  int n;
+};
+__global__ void pack_all_kernel(const __grid_constant__ PackSegs S) {
+  const int64_t total = S.start[S.n];
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    int j = 0;
+    while (S.start[j + 1] <= e) j++;
+    const int64_t i = e - S.start[j];
+    const int K = S.K[j], N = S.N[j];
     const int n = (int)(i / K), k = (int)(i % K);
-    const __nv_bfloat16 b = __float2bfloat16_rn(W[i]);
-    Wb[i] = b;
-    Wt[(int64_t)k * N + n] = b;
+    const __nv_bfloat16 b = __float2bfloat16_rn(S.W[j][i]);
+    S.Wb[j][i] = b;
+    S.Wt[j][(int64_t)k * N + n] = b;
   }
 }
 
@@ -572,8 +621,10 @@ static lgs_status launch_dw(const __nv_bfloat16* G, const __nv_bfloat16* X, int6
   else if (K == 128) st = launch_dw_t<128>(a, s);
   else st = launch_dw_t<256>(a, s);  // K = 256 or 512 (two column tiles)
   if (st != LGS_OK) return st;
-  const int rows = 512;
-  colsum_kernel<<<(unsigned)((P + rows - 1) / rows), 256, 0, s>>>(G, P, N, rows, db);
+  // about 32 rows per thread: 32 * 256 / (N / 8) rows per block
+  const int rows = 65536 / N;
+  colsum_kernel<<<(unsigned)((P + rows - 1) / rows), 256, sizeof(float) * N, s>>>(G, P, N, rows,
+                                                                                  db);
   LGS_CHECK_LAUNCH();
   return LGS_OK;
 }
@@ -718,14 +769,21 @@ extern "C" lgs_status ae_pack(lgs_ae_state* st_, int first, int last, void* stre
   clear_error();
   LGS_CHECK_ARG(st_ && first >= 0 && last < kAeLayers && first <= last, "bad arguments");
   cudaStream_t s = as_stream(stream);
+  PackSegs S;
+  S.n = 0;
+  S.start[0] = 0;
   for (int l = first; l <= last; l++) {
     LGS_CHECK_ARG(st_->W[l] && st_->Wbf[l] && st_->Wtbf[l], "null weight pointer");
-    const int K = kAeWidths[l], N = kAeWidths[l + 1];
-    pack_kernel<<<(N * K + 255) / 256, 256, 0, s>>>(st_->W[l], N, K,
-                                                    reinterpret_cast<__nv_bfloat16*>(st_->Wbf[l]),
-                                                    reinterpret_cast<__nv_bfloat16*>(st_->Wtbf[l]));
-    LGS_CHECK_LAUNCH();
+    const int j = S.n++;
+    S.W[j] = st_->W[l];
+    S.Wb[j] = reinterpret_cast<__nv_bfloat16*>(st_->Wbf[l]);
+    S.Wt[j] = reinterpret_cast<__nv_bfloat16*>(st_->Wtbf[l]);
+    S.K[j] = kAeWidths[l];
+    S.N[j] = kAeWidths[l + 1];
+    S.start[j + 1] = S.start[j] + (int64_t)S.N[j] * S.K[j];
   }
+  pack_all_kernel<<<(unsigned)std::min<int64_t>((S.start[S.n] + 255) / 256, 152 * 8), 256, 0, s>>>(S);
+  LGS_CHECK_LAUNCH();
   return LGS_OK;
 }
 
@@ -819,14 +877,23 @@ extern "C" lgs_status ae_train_step(lgs_ae_state* st_, const uint16_t* x, const 
   st_->step += 1;
   const float bc1 = 1.f - powf(0.9f, (float)st_->step);
   const float bc2 = 1.f - powf(0.999f, (float)st_->step);
+  AdamSegs A;
+  A.n = 0;
+  A.start[0] = 0;
   for (int l = 0; l <= last; l++) {
-    const int K = kAeWidths[l], N = kAeWidths[l + 1];
-    adam_kernel<<<(N * K + 255) / 256, 256, 0, s>>>(st_->W[l], st_->mW[l], st_->vW[l], st_->gW[l],
-                                                   (int64_t)N * K, lr, bc1, bc2);
-    adam_kernel<<<(N + 255) / 256, 256, 0, s>>>(st_->b[l], st_->mb[l], st_->vb[l], st_->gb[l], N,
-                                               lr, bc1, bc2);
-    LGS_CHECK_LAUNCH();
+    const int64_t nw = (int64_t)kAeWidths[l] * kAeWidths[l + 1], nb = kAeWidths[l + 1];
+    for (int wb = 0; wb < 2; wb++) {
+      const int j = A.n++;
+      A.w[j] = wb ? st_->b[l] : st_->W[l];
+      A.m[j] = wb ? st_->mb[l] : st_->mW[l];
+      A.v[j] = wb ? st_->vb[l] : st_->vW[l];
+      A.g[j] = wb ? st_->gb[l] : st_->gW[l];
+      A.start[j + 1] = A.start[j] + (wb ? nb : nw);
+    }
   }
+  adam_all_kernel<<<(unsigned)std::min<int64_t>((A.start[A.n] + 255) / 256, 152 * 8), 256, 0, s>>>(
+      A, lr, bc1, bc2);
+  LGS_CHECK_LAUNCH();
   return ae_pack(st_, 0, last, stream);
 }
 

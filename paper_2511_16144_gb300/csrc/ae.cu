@@ -136,18 +136,12 @@ __global__ void __launch_bounds__(128, 1) layer_kernel(LayerArgs a) {
 
   const int nk = K / KC;
   constexpr uint32_t SBO = KC * 16;
-  for (int kc = 0; kc < nk; kc++) {
+  // cp.async of K-chunk kc into stage kc & 1 (A: 128 rows x KC, B: NT x KC)
+  auto load_chunk = [&](int kc) {
     const int s = kc & 1;
-    // every thread polls; the block agrees before anyone moves on
-    const bool freed = kc < 2 || tc::mbar_wait(&mbar[s], ((kc - 2) >> 1) & 1, kSpinLimit);
-    if (!__syncthreads_and(freed)) {
-      ok = false;
-      break;
-    }
     uint8_t* sa = sm + s * L::STAGE;
     uint8_t* sb = sa + L::A_BYTES;
     const uint32_t sa_u = tc::smem_addr(sa), sb_u = tc::smem_addr(sb);
-    // A: 128 rows x KC columns
     constexpr int APIECES = 128 * (KC / 8);
     for (int i = tid; i < APIECES; i += 128) {
       const int r = i / (KC / 8), c = i % (KC / 8);
@@ -173,7 +167,6 @@ __global__ void __launch_bounds__(128, 1) layer_kernel(LayerArgs a) {
         tc::cp_async16_zfill(sa_u + off, src, valid);
       }
     }
-    // B: NT weight rows x KC columns
     constexpr int BPIECES = NT * (KC / 8);
     for (int i = tid; i < BPIECES; i += 128) {
       const int r = i / (KC / 8), c = i % (KC / 8);
@@ -181,9 +174,27 @@ __global__ void __launch_bounds__(128, 1) layer_kernel(LayerArgs a) {
       tc::cp_async16(sb_u + tc::core_offset(r, c, KC), src);
     }
     tc::cp_async_commit();
-    tc::cp_async_wait_all();
+  };
+  // chunk kc + 1 is in flight while chunk kc waits for its data and its MMAs
+  load_chunk(0);
+  for (int kc = 0; kc < nk; kc++) {
+    const int s = kc & 1;
+    if (kc + 1 < nk) {
+      // stage (kc + 1) & 1 is free once the MMAs of chunk kc - 1 are done;
+      // every thread polls and the block agrees before anyone moves on
+      const bool freed = kc < 1 || tc::mbar_wait(&mbar[s ^ 1], ((kc - 1) >> 1) & 1, kSpinLimit);
+      if (!__syncthreads_and(freed)) {
+        ok = false;
+        break;
+      }
+      load_chunk(kc + 1);
+      tc::cp_async_wait_group<1>();
+    } else {
+      tc::cp_async_wait_all();
+    }
     tc::fence_async_smem();
     __syncthreads();
+    const uint32_t sa_u = tc::smem_addr(sm + s * L::STAGE), sb_u = sa_u + L::A_BYTES;
     if (tid == 0) {
       tc::fence_after();
 #pragma unroll

@@ -25,6 +25,7 @@
 //     blocks while staging.
 //   colsum, adam_all and pack_all kernels (SIMT; one launch for every layer).
 #include <algorithm>
+#include <cstring>
 
 #include "common.cuh"
 #include "kernels.cuh"
@@ -110,14 +111,28 @@ struct LayerSmem {
   static constexpr int STAGE = A_BYTES + B_BYTES;
   static constexpr size_t total = 2 * STAGE + 64;
   static constexpr uint32_t TCOLS = NT < 32 ? 32 : NT;
+  static constexpr int BROWS = NT > 256 ? 256 : NT;  // weight rows per TMA box
 };
 
+// 3-D tensor load [x, y, z] -> shared, completing on an mbarrier.
+__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map, int x, int y,
+                                            int z, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(dst),
+      "l"(map), "r"(x), "r"(y), "r"(z), "r"(tc::smem_addr(bar))
+      : "memory");
+}
+
 template <int NT, int KC>
-__global__ void __launch_bounds__(128, 1) layer_kernel(LayerArgs a) {
+__global__ void __launch_bounds__(128, 1) layer_kernel(const __grid_constant__ LayerArgs a,
+                                                      const __grid_constant__ CUtensorMap amap,
+                                                      const __grid_constant__ CUtensorMap bmap) {
   using L = LayerSmem<NT, KC>;
   extern __shared__ __align__(1024) uint8_t sm[];
-  uint64_t* mbar = reinterpret_cast<uint64_t*>(sm + 2 * L::STAGE);
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + 2 * L::STAGE + 16);
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(sm + 2 * L::STAGE);   // [2] MMAs of a stage done
+  uint64_t* full = mbar + 2;                                          // [2] TMA data of a stage in
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(full + 2);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int64_t row0 = (int64_t)blockIdx.x * 128;
   const int n0 = blockIdx.y * NT;
@@ -126,6 +141,8 @@ __global__ void __launch_bounds__(128, 1) layer_kernel(LayerArgs a) {
   if (tid == 0) {
     tc::mbar_init(&mbar[0], 1);
     tc::mbar_init(&mbar[1], 1);
+    tc::mbar_init(&full[0], 1);
+    tc::mbar_init(&full[1], 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   tc::fence_before();
@@ -136,7 +153,52 @@ __global__ void __launch_bounds__(128, 1) layer_kernel(LayerArgs a) {
 
   const int nk = K / KC;
   constexpr uint32_t SBO = KC * 16;
-  // cp.async of K-chunk kc into stage kc & 1 (A: 128 rows x KC, B: NT x KC)
+  if (!a.a_f32) {
+    // BF16 A: thread 0 streams A and W chunks by TMA (each lands as KC / 8
+    // blocks of rows x 16 bytes: K-adjacent core matrices rows * 16 bytes
+    // apart), thread 32 issues the MMAs; the stages are handed over by
+    // mbarriers, no block barrier in the loop
+    const uint32_t sbase = tc::smem_addr(sm);
+    if (tid == 0) {
+      for (int kc = 0; kc < nk && ok; kc++) {
+        const int s = kc & 1;
+        if (kc >= 2 && !tc::mbar_wait(&mbar[s], ((kc - 2) >> 1) & 1, kSpinLimit)) {
+          ok = false;
+          break;
+        }
+        const uint32_t st = sbase + s * L::STAGE;
+        tc::mbar_expect_tx(&full[s], L::STAGE);
+        tma_load_3d(st, &amap, 0, (int)row0, kc * (KC / 8), &full[s]);
+#pragma unroll
+        for (int h = 0; h < NT / L::BROWS; h++)
+          tma_load_3d(st + L::A_BYTES + h * L::BROWS * KC * 2, &bmap, 0, n0 + h * L::BROWS,
+                      kc * (KC / 8), &full[s]);
+      }
+    } else if (tid == 32) {
+      for (int kc = 0; kc < nk && ok; kc++) {
+        const int s = kc & 1;
+        if (!tc::mbar_wait(&full[s], (kc >> 1) & 1, kSpinLimit)) {
+          ok = false;
+          break;
+        }
+        tc::fence_after();
+        const uint32_t sa_u = sbase + s * L::STAGE, sb_u = sa_u + L::A_BYTES;
+#pragma unroll
+        for (int j = 0; j < KC / 16; j++) {
+          const uint64_t ad = tc::sdesc(sa_u + j * 2 * 2048, 2048, 128);
+#pragma unroll
+          for (int h = 0; h < NT / L::BROWS; h++) {
+            const uint64_t bd = tc::sdesc(sb_u + h * L::BROWS * KC * 2 + j * 2 * L::BROWS * 16,
+                                          L::BROWS * 16, 128);
+            tc::mma_bf16(tmem + h * 256, ad, bd, tc::idesc_bf16(128, L::BROWS), (kc | j) != 0);
+          }
+        }
+        tc::commit(&mbar[s]);
+      }
+    }
+  } else {
+  // FP32 A (converted to BF16 while staged): every thread copies with
+  // cp.async, K-chunk kc into stage kc & 1 (A: 128 rows x KC, B: NT x KC)
   auto load_chunk = [&](int kc) {
     const int s = kc & 1;
     uint8_t* sa = sm + s * L::STAGE;
@@ -210,6 +272,8 @@ __global__ void __launch_bounds__(128, 1) layer_kernel(LayerArgs a) {
       tc::commit(&mbar[s]);
     }
   }
+  }
+  ok = __syncthreads_and(ok);
   if (ok) ok = __syncthreads_and(tc::mbar_wait(&mbar[(nk - 1) & 1], ((nk - 1) >> 1) & 1, kSpinLimit));
   if (!ok) {
     if (tid == 0) report_timeout();
@@ -586,8 +650,16 @@ template <int NT, int KC>
 static lgs_status launch_layer_t(const LayerArgs& a, cudaStream_t s) {
   using L = LayerSmem<NT, KC>;
   LGS_CHECK_CUDA(set_smem_limit(reinterpret_cast<const void*>(layer_kernel<NT, KC>), (int)L::total));
+  CUtensorMap amap, bmap;
+  std::memset(&amap, 0, sizeof(amap));
+  std::memset(&bmap, 0, sizeof(bmap));
+  if (!a.a_f32) {  // A [P, K] and W [N, K] as K-major chunks of KC columns
+    if (!make_kmajor_map(&amap, a.A, a.P, a.K, 128, KC / 8) ||
+        !make_kmajor_map(&bmap, a.W, a.N, a.K, L::BROWS, KC / 8))
+      return LGS_ERR_CUDA;
+  }
   dim3 grid((unsigned)((a.P + 127) / 128), a.N / NT);
-  layer_kernel<NT, KC><<<grid, 128, L::total, s>>>(a);
+  layer_kernel<NT, KC><<<grid, 128, L::total, s>>>(a, amap, bmap);
   LGS_CHECK_LAUNCH();
   return LGS_OK;
 }

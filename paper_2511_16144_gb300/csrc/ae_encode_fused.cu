@@ -416,29 +416,35 @@ int sm_count() {
 
 size_t encode_pack_bytes() { return (enc_plan().total + 255) & ~(size_t)255; }
 
-lgs_status launch_encode_fused(const lgs_ae_weights* w, const uint16_t* x, int64_t P, float* z,
-                               void* pack, cudaStream_t s) {
-  const EncPlan& pl = enc_plan();
+bool make_kmajor_map(CUtensorMap* map, const void* base, int64_t rows, int K, int box_rows,
+                     int box_groups) {
   auto encode = tensor_map_encoder();
   if (!encode) {
     set_error("cuTensorMapEncodeTiled is unavailable");
-    return LGS_ERR_CUDA;
+    return false;
   }
-  // x [P, 512] bf16 viewed as [64 column groups][P rows][8 columns]: a box of
-  // 8 x 128 x 4 lands 128 rows x 32 columns as 4 groups of 128 x 16 bytes,
-  // the K-major core-matrix layout with K-adjacent groups 2048 bytes apart
-  CUtensorMap xmap;
-  const cuuint64_t dims[3] = {8, (cuuint64_t)P, 64};
-  const cuuint64_t strides[2] = {1024, 16};
-  const cuuint32_t box[3] = {8, 128, 4}, es[3] = {1, 1, 1};
+  const cuuint64_t dims[3] = {8, (cuuint64_t)rows, (cuuint64_t)(K / 8)};
+  const cuuint64_t strides[2] = {(cuuint64_t)K * 2, 16};
+  const cuuint32_t box[3] = {8, (cuuint32_t)box_rows, (cuuint32_t)box_groups}, es[3] = {1, 1, 1};
   const CUresult cr =
-      encode(&xmap, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<uint16_t*>(x), dims, strides,
-             box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+      encode(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(base), dims, strides, box,
+             es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
              CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (cr != CUDA_SUCCESS) {
-    set_error("cuTensorMapEncodeTiled failed for the encoder input");
-    return LGS_ERR_CUDA;
+    set_error("cuTensorMapEncodeTiled refused a K-major map");
+    return false;
   }
+  return true;
+}
+
+lgs_status launch_encode_fused(const lgs_ae_weights* w, const uint16_t* x, int64_t P, float* z,
+                               void* pack, cudaStream_t s) {
+  const EncPlan& pl = enc_plan();
+  // x [P, 512] bf16 as [64 column groups][P rows][8 columns]: a box of
+  // 128 rows x 4 groups is one 32-column chunk in the K-major layout with
+  // K-adjacent groups 2048 bytes apart
+  CUtensorMap xmap;
+  if (!make_kmajor_map(&xmap, x, P, 512, 128, 4)) return LGS_ERR_CUDA;
   EncPackArgs pa;
   for (int m = 0; m < 4; m++) pa.mats[m] = reinterpret_cast<const __nv_bfloat16*>(w->W[m]);
   for (int i = 0; i < kUnits; i++) {

@@ -14,9 +14,13 @@
 //
 // Kernels
 //   layer_kernel<NT, KC>: out[P, N] = epilogue(A[P, K] . W[N, K]^T) for one
-//     128-row tile per CTA, K streamed in chunks of KC through a two-stage
-//     cp.async pipeline into the canonical K-major layout; one thread issues
-//     the MMAs, all 128 threads run the epilogue from TMEM (thread = row).
+//     128-row tile per CTA, K streamed in chunks of KC through two stages into
+//     the canonical K-major layout -- by 3-D TMA loads from one thread for
+//     BF16 operands, by cp.async from every thread (converting) for an FP32
+//     A; one thread issues the MMAs, all 128 threads run the epilogue from
+//     TMEM (thread = row).  The encoder has its own fused kernel
+//     (ae_encode_fused.cu), the map step's decoder distillation too
+//     (ae_fused.cu).
 //     Epilogues: bias+GELU (+ pre-activation), linear, GELU'-gated backward,
 //     and the fused losses (L1 against a target, or L2 + (1 - cos)) that
 //     also emit the output gradient.

@@ -138,7 +138,7 @@ constexpr size_t fwd_smem() {
 }
 
 template <int FC, typename TC, bool RGB>
-__global__ void __launch_bounds__(kThreads) render_fwd_kernel(RasterArgs A, int chunk_base) {
+__global__ void __launch_bounds__(kThreads, FC <= 16 ? 4 : 1) render_fwd_kernel(RasterArgs A, int chunk_base) {
   constexpr int NCH = nchan<FC, RGB>();
   extern __shared__ float4 smem4[];
   float4* s_co = smem4;

@@ -697,14 +697,17 @@ def measure_autoencoder(enc, dec, g512_bf, flush, dev, reps=20):
 
     out = {}
     ms = timed_graph(lambda: m.train_step(x, lr=1e-4, loss=loss))
-    flop = 2 * 3 * 346112 * x.shape[0]  # (forward, dX, dW) x (encoder + decoder) MACs, x 2
+    # MACs per pixel: forward and weight gradient of all eight layers
+    # (2 x 346,112) and the input gradient of layers 1-7 (346,112 - 512 x 256:
+    # the batch itself needs none), 2 FLOP each
+    flop = 2 * (2 * 346112 + 346112 - 512 * 256) * x.shape[0]
     out["ae_train_step"] = {
         "pixels": int(x.shape[0]), "ms": ms,
         "roofline": {"bound": "tensor", "achieved": flop / (ms * 1e-3) / 1e12,
                      "peak": peaks["bf16_tflops"], "unit": "TFLOP/s",
                      "frac": flop / (ms * 1e-3) / 1e12 / peaks["bf16_tflops"], "traffic": None,
                      "peak_source": kind + " bf16 burst",
-                     "note": "about 50 launches (8 layers forward, backward, weight gradient, bias sums, Adam, repacks)"}}
+                     "note": "25 kernel launches (8 layers forward, 8 weight and bias gradients, 7 input gradients, Adam, BF16 repack) and 16 gradient memsets"}}
     z = torch.empty((g512_bf.shape[0], 16), dtype=torch.float32, device=dev)
     ws = m._ws.get("enc")
     ms = timed_graph(lambda: lgs.ae_encode(m.weights, g512_bf, z, ws=ws))

@@ -24,10 +24,11 @@
 //     Epilogues: bias+GELU (+ pre-activation), linear, GELU'-gated backward,
 //     and the fused losses (L1 against a target, or L2 + (1 - cos)) that
 //     also emit the output gradient.
-//   dw_kernel<KT>: dW[N, K] += sum_p G[p, n] X[p, k] over a pixel range; the
-//     pixel dimension is the MMA's K, so both operands are transposed in 8x8
-//     blocks while staging.
-//   colsum, adam_all and pack_all kernels (SIMT; one launch for every layer).
+//   dw_kernel<KT>: dW[N, K] += sum_p G[p, n] X[p, k] over a pixel range, and
+//     the bias gradient db[n] += sum_p G[p, n] in the same launch; the pixel
+//     dimension is the MMA's K, so G and X as stored are MN-major operands
+//     that 3-D TMA loads land without a transpose.
+//   adam_all and pack_all kernels (SIMT; one launch for every layer).
 #include <algorithm>
 #include <cstring>
 
@@ -78,8 +79,10 @@ struct LayerArgs {
 __device__ __forceinline__ float gelu_f(float x) { return gelu_tanh(x); }
 __device__ __forceinline__ float gelu_grad_f(float x) { return gelu_tanh_grad(x); }
 
-__device__ __forceinline__ void store_bf16x32(__nv_bfloat16* dst, const float* v, int n) {
-  // n = 16 or 32 values to a 16-byte aligned destination
+// n = 16 or 32 values as 16-byte pieces of 8, `step` pieces apart (1:
+// contiguous; 128: the column groups of a staged 128-row tile)
+__device__ __forceinline__ void store_bf16x32(__nv_bfloat16* dst, const float* v, int n,
+                                              int step = 1) {
 #pragma unroll
   for (int q = 0; q < 4; q++) {
     if (q * 8 >= n) break;
@@ -87,15 +90,16 @@ __device__ __forceinline__ void store_bf16x32(__nv_bfloat16* dst, const float* v
     __nv_bfloat162* h = reinterpret_cast<__nv_bfloat162*>(&u);
 #pragma unroll
     for (int k = 0; k < 4; k++) h[k] = __floats2bfloat162_rn(v[8 * q + 2 * k], v[8 * q + 2 * k + 1]);
-    reinterpret_cast<uint4*>(dst)[q] = u;
+    reinterpret_cast<uint4*>(dst)[q * step] = u;
   }
 }
 
-__device__ __forceinline__ void load_bf16x32(const __nv_bfloat16* src, float* v, int n) {
+__device__ __forceinline__ void load_bf16x32(const __nv_bfloat16* src, float* v, int n,
+                                             int step = 1) {
 #pragma unroll
   for (int q = 0; q < 4; q++) {
     if (q * 8 >= n) break;
-    uint4 u = reinterpret_cast<const uint4*>(src)[q];
+    uint4 u = reinterpret_cast<const uint4*>(src)[q * step];
     const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&u);
 #pragma unroll
     for (int k = 0; k < 4; k++) {
@@ -128,15 +132,31 @@ __device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map
       : "memory");
 }
 
+// 3-D tensor store shared -> [x, y, z] (rows past the tensor are not written).
+__device__ __forceinline__ void tma_store_3d(const CUtensorMap* map, int x, int y, int z,
+                                             uint32_t src) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.global.shared::cta.bulk_group [%0, {%1, %2, %3}], [%4];" ::"l"(map),
+      "r"(x), "r"(y), "r"(z), "r"(src)
+      : "memory");
+  asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+  asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+}
+
+// tmap / omap: the target and the output of EPI_RECON as [64 groups][P][8]
+// maps with 128-row x 64-group boxes (unused by the other epilogues).
 template <int NT, int KC>
 __global__ void __launch_bounds__(128, 1) layer_kernel(const __grid_constant__ LayerArgs a,
                                                       const __grid_constant__ CUtensorMap amap,
-                                                      const __grid_constant__ CUtensorMap bmap) {
+                                                      const __grid_constant__ CUtensorMap bmap,
+                                                      const __grid_constant__ CUtensorMap tmap,
+                                                      const __grid_constant__ CUtensorMap omap) {
   using L = LayerSmem<NT, KC>;
   extern __shared__ __align__(1024) uint8_t sm[];
   uint64_t* mbar = reinterpret_cast<uint64_t*>(sm + 2 * L::STAGE);   // [2] MMAs of a stage done
   uint64_t* full = mbar + 2;                                          // [2] TMA data of a stage in
   uint32_t* tslot = reinterpret_cast<uint32_t*>(full + 2);
+  uint64_t* xbar = reinterpret_cast<uint64_t*>(sm + 2 * L::STAGE + 40);  // EPI_RECON target in
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int64_t row0 = (int64_t)blockIdx.x * 128;
   const int n0 = blockIdx.y * NT;
@@ -147,6 +167,7 @@ __global__ void __launch_bounds__(128, 1) layer_kernel(const __grid_constant__ L
     tc::mbar_init(&mbar[1], 1);
     tc::mbar_init(&full[0], 1);
     tc::mbar_init(&full[1], 1);
+    tc::mbar_init(xbar, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   tc::fence_before();
@@ -312,41 +333,56 @@ __global__ void __launch_bounds__(128, 1) layer_kernel(const __grid_constant__ L
       const uint32_t peers = __match_any_sync(0xffffffffu, valid ? bi : (0x80000000u | lane));
       if (valid && a.hist && lane == __ffs(peers) - 1) atomicAdd(a.hist + bi, (uint32_t)__popc(peers));
     } else if (a.epi == EPI_RECON) {
-      // pass 1: row statistics of y against x = target
-      float sdd = 0.f, syx = 0.f, syy = 0.f, sxx = 0.f;
-      for (int c0 = 0; c0 < NT; c0 += CW) {
-        float v[32], x[32];
-        tc::tmem_ld32(tb + c0, v);
-        if (valid) {
-          load_bf16x32(reinterpret_cast<const __nv_bfloat16*>(a.target) + p * a.N + n0 + c0, x, CW);
-#pragma unroll
-          for (int i = 0; i < CW; i++) {
-            const float y = v[i] + a.bias[n0 + c0 + i];
-            const float d = y - x[i];
-            sdd = fmaf(d, d, sdd);
-            syx = fmaf(y, x[i], syx);
-            syy = fmaf(y, y, syy);
-            sxx = fmaf(x[i], x[i], sxx);
-          }
+      if constexpr (NT == 512 && 2 * L::STAGE >= 128 * 512 * 2) {
+        // The target tile [128 x 512] lands in the free stages in one TMA
+        // load, as 64 column groups of 128 rows x 16 B (row r of group g at
+        // g * 2048 + r * 16: the rows of a warp are consecutive 16-byte
+        // pieces); dL/dy replaces it in place and leaves in one TMA store.
+        const uint32_t sx = tc::smem_addr(sm);
+        if (tid == 0) {
+          tc::mbar_expect_tx(xbar, 128 * 512 * 2);
+          tma_load_3d(sx, &tmap, 0, (int)row0, 0, xbar);
         }
-      }
-      const float ny = sqrtf(syy), nx = sqrtf(sxx);
-      const float inv = 1.f / fmaxf(ny * nx, 1e-30f);
-      const float cosv = syx * inv;
-      if (valid) lsum = a.scale * (sdd / (float)a.N + 1.f - cosv);
-      const float iy2 = 1.f / fmaxf(syy, 1e-30f);
-      // pass 2: dL/dy = s (2 (y - x)/N - (x/(|y||x|) - cos y/|y|^2))
-      for (int c0 = 0; c0 < NT; c0 += CW) {
-        float v[32], x[32];
-        tc::tmem_ld32(tb + c0, v);
-        if (valid) {
-          load_bf16x32(reinterpret_cast<const __nv_bfloat16*>(a.target) + p * a.N + n0 + c0, x, CW);
+        if (__syncthreads_and(tc::mbar_wait(xbar, 0, kSpinLimit))) {
+          __nv_bfloat16* xr = reinterpret_cast<__nv_bfloat16*>(sm + r * 16);
+          // pass 1: row statistics of y against x = target
+          float sdd = 0.f, syx = 0.f, syy = 0.f, sxx = 0.f;
+          for (int c0 = 0; c0 < NT; c0 += 32) {
+            float v[32], x[32];
+            tc::tmem_ld32(tb + c0, v);
+            load_bf16x32(xr + c0 * 128, x, 32, 128);
 #pragma unroll
-          for (int i = 0; i < CW; i++) {
-            const float y = v[i] + a.bias[n0 + c0 + i];
-            v[i] = a.scale * (2.f * (y - x[i]) / (float)a.N - (x[i] * inv - cosv * y * iy2));
+            for (int i = 0; i < 32; i++) {
+              const float y = v[i] + a.bias[c0 + i];
+              const float d = y - x[i];
+              sdd = fmaf(d, d, sdd);
+              syx = fmaf(y, x[i], syx);
+              syy = fmaf(y, y, syy);
+              sxx = fmaf(x[i], x[i], sxx);
+            }
           }
-          store_bf16x32(a.out_bf + p * a.N + n0 + c0, v, CW);
+          const float ny = sqrtf(syy), nx = sqrtf(sxx);
+          const float inv = 1.f / fmaxf(ny * nx, 1e-30f);
+          const float cosv = syx * inv;
+          if (valid) lsum = a.scale * (sdd / (float)a.N + 1.f - cosv);
+          const float iy2 = 1.f / fmaxf(syy, 1e-30f);
+          // pass 2: dL/dy = s (2 (y - x)/N - (x/(|y||x|) - cos y/|y|^2))
+          for (int c0 = 0; c0 < NT; c0 += 32) {
+            float v[32], x[32];
+            tc::tmem_ld32(tb + c0, v);
+            load_bf16x32(xr + c0 * 128, x, 32, 128);
+#pragma unroll
+            for (int i = 0; i < 32; i++) {
+              const float y = v[i] + a.bias[c0 + i];
+              v[i] = a.scale * (2.f * (y - x[i]) / (float)a.N - (x[i] * inv - cosv * y * iy2));
+            }
+            store_bf16x32(xr + c0 * 128, v, 32, 128);
+          }
+          tc::fence_async_smem();
+          __syncthreads();
+          if (tid == 0) tma_store_3d(&omap, 0, (int)row0, 0, sx);
+        } else if (tid == 0) {
+          report_timeout();
         }
       }
     } else {
@@ -437,108 +473,109 @@ __global__ void __launch_bounds__(128, 1) layer_kernel(const __grid_constant__ L
 // ------------------------------------------------------------------ dW
 
 struct DwArgs {
-  const __nv_bfloat16* G;  // [P][N]
-  const __nv_bfloat16* X;  // [P][K]
   int64_t P;
   int N, K;
   int chunks_per_cta;      // 64-pixel chunks per CTA
+  int a_tx, b_tx;          // bytes one stage's G and X loads deliver
   float* dW;               // [N][K], accumulated
+  float* db;               // [N], accumulated (column sums of G), or null
 };
 
-// Transposes the 8x8 bf16 block held as 8 rows of 16 bytes.
-__device__ __forceinline__ void transpose8x8(const uint4* in, uint4* out) {
-  const uint32_t* w = reinterpret_cast<const uint32_t*>(in);
-#pragma unroll
-  for (int i = 0; i < 8; i++) {
-    uint32_t* o = reinterpret_cast<uint32_t*>(&out[i]);
-    const uint32_t sel = (i & 1) ? 0x7632u : 0x5410u;
-#pragma unroll
-    for (int q = 0; q < 4; q++) o[q] = __byte_perm(w[(2 * q) * 4 + (i >> 1)], w[(2 * q + 1) * 4 + (i >> 1)], sel);
-  }
-}
-
-// Stages the transposed block: rows = features f0..f0+7 of src (row stride
-// ld), columns = pixels p0..p0+7; zero outside [0, P) x [0, F).
-__device__ __forceinline__ void stage_block(const __nv_bfloat16* src, int64_t ld, int64_t p0,
-                                            int64_t P, int f0, int F, uint8_t* dst_tile,
-                                            int g, int c) {
-  uint4 in[8], out[8];
-#pragma unroll
-  for (int j = 0; j < 8; j++) {
-    const int64_t p = p0 + j;
-    in[j] = (p < P && f0 < F) ? *reinterpret_cast<const uint4*>(src + p * ld + f0)
-                              : make_uint4(0, 0, 0, 0);
-  }
-  transpose8x8(in, out);
-#pragma unroll
-  for (int i = 0; i < 8; i++)
-    *reinterpret_cast<uint4*>(dst_tile + tc::core_offset(8 * g + i, c, 64)) = out[i];
-}
-
+// Shared memory of dw_kernel<KT>: a ring of stages, each one 64-pixel chunk
+// of G (128 features) and X (KT features) as the TMA lands them -- 8-feature
+// groups of 64 pixels x 16 bytes, the MN-major core-matrix layout of
+// operands whose K is the pixel -- then a 512-byte block of BF16 ones for
+// the bias sums and the barriers.
 template <int KT>
 struct DwSmem {
-  static constexpr int A_BYTES = 128 * 64 * 2;
-  static constexpr int B_BYTES = KT * 64 * 2;
+  static constexpr int PC = 64;                  // pixels per stage
+  static constexpr int A_BYTES = 128 * PC * 2;   // G^T: up to 16 groups x 64 pixels x 16 B
+  static constexpr int B_BYTES = KT * PC * 2;    // X^T: KT / 8 groups
   static constexpr int STAGE = A_BYTES + B_BYTES;
-  static constexpr size_t total = 2 * STAGE + 64;
-  static constexpr uint32_t TCOLS = KT < 32 ? 32 : KT;
+  static constexpr int S = (196608 / STAGE) < 8 ? (196608 / STAGE) : 8;
+  static constexpr int ONES = S * STAGE;
+  static constexpr int BAR = ONES + 512;         // full[S], empty[S], done, TMEM slot
+  static constexpr size_t total = BAR + (2 * S + 1) * 8 + 16;
+  // dW in columns [0, KT), the bias sums in [KT, KT + 16)
+  static constexpr uint32_t TCOLS = KT + 16 <= 32 ? 32 : KT + 16 <= 64 ? 64 : KT + 16 <= 128 ? 128
+                                  : KT + 16 <= 256 ? 256 : 512;
 };
 
+// dW[n0 .. n0 + 127, k0 .. k0 + KT) += sum_p G[p, n] X[p, k] over the CTA's
+// pixel range, and (k-tile 0, db given) db[n] += sum_p G[p, n].  The pixel
+// is the MMA's K: both operands are MN-major (G and X as stored, rows =
+// pixels), so the TMA loads them without a transpose; the bias sums are one
+// more N = 16 MMA of G^T against a block of ones.  Thread 0 streams the
+// stages, thread 32 issues the MMAs; all 128 threads add the tile to dW.
 template <int KT>
-__global__ void __launch_bounds__(128, 1) dw_kernel(DwArgs a) {
+__global__ void __launch_bounds__(128, 1) dw_kernel(const __grid_constant__ DwArgs a,
+                                                   const __grid_constant__ CUtensorMap gmap,
+                                                   const __grid_constant__ CUtensorMap xmap) {
   using L = DwSmem<KT>;
   extern __shared__ __align__(1024) uint8_t sm[];
-  uint64_t* mbar = reinterpret_cast<uint64_t*>(sm + 2 * L::STAGE);
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + 2 * L::STAGE + 16);
+  uint64_t* full = reinterpret_cast<uint64_t*>(sm + L::BAR);
+  uint64_t* empty = full + L::S;
+  uint64_t* done = empty + L::S;
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(done + 1);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int n0 = blockIdx.x * 128, k0 = blockIdx.y * KT;
-  const int64_t pbeg = (int64_t)blockIdx.z * a.chunks_per_cta * 64;
-  const int64_t pend = min(a.P, pbeg + (int64_t)a.chunks_per_cta * 64);
-  const int nchunks = pend > pbeg ? (int)((pend - pbeg + 63) / 64) : 0;
+  const bool bias = a.db != nullptr && blockIdx.y == 0;
+  const int64_t pbeg = (int64_t)blockIdx.z * a.chunks_per_cta * L::PC;
+  const int64_t pend = min(a.P, pbeg + (int64_t)a.chunks_per_cta * L::PC);
+  const int nchunks = pend > pbeg ? (int)((pend - pbeg + L::PC - 1) / L::PC) : 0;
   if (warp == 0) tc::tmem_alloc(tslot, L::TCOLS);
   if (tid == 0) {
-    tc::mbar_init(&mbar[0], 1);
-    tc::mbar_init(&mbar[1], 1);
+    for (int i = 0; i < 2 * L::S + 1; i++) tc::mbar_init(&full[i], 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
+  if (tid < 32) reinterpret_cast<uint4*>(sm + L::ONES)[tid] = make_uint4(0x3F803F80u, 0x3F803F80u,
+                                                                        0x3F803F80u, 0x3F803F80u);
+  tc::fence_async_smem();
   tc::fence_before();
   __syncthreads();
   tc::fence_after();
   const uint32_t tmem = *tslot;
+  const uint32_t sbase = tc::smem_addr(sm);
   bool ok = true;
-  for (int ch = 0; ch < nchunks; ch++) {
-    const int s = ch & 1;
-    const bool freed = ch < 2 || tc::mbar_wait(&mbar[s], ((ch - 2) >> 1) & 1, kSpinLimit);
-    if (!__syncthreads_and(freed)) {
-      ok = false;
-      break;
+  if (tid == 0) {
+    for (int ch = 0; ch < nchunks && ok; ch++) {
+      const int s = ch % L::S;
+      if (ch >= L::S && !tc::mbar_wait(&empty[s], (uint32_t)(ch / L::S - 1) & 1, kSpinLimit)) {
+        ok = false;
+        break;
+      }
+      const uint32_t st = sbase + s * L::STAGE;
+      const int p0 = (int)(pbeg + (int64_t)ch * L::PC);
+      tc::mbar_expect_tx(&full[s], (uint32_t)(a.a_tx + a.b_tx));
+      tma_load_3d(st, &gmap, 0, p0, n0 / 8, &full[s]);
+      tma_load_3d(st + L::A_BYTES, &xmap, 0, p0, k0 / 8, &full[s]);
     }
-    uint8_t* sa = sm + s * L::STAGE;
-    uint8_t* sb = sa + L::A_BYTES;
-    const int64_t p0 = pbeg + (int64_t)ch * 64;
-    {  // A = G^T: 16 feature groups x 8 pixel groups, one block per thread
-      const int g = tid >> 3, c = tid & 7;
-      stage_block(a.G, a.N, p0 + 8 * c, pend, n0 + 8 * g, a.N, sa, g, c);
-    }
-    for (int b = tid; b < (KT / 8) * 8; b += 128) {  // B = X^T
-      const int g = b >> 3, c = b & 7;
-      stage_block(a.X, a.K, p0 + 8 * c, pend, k0 + 8 * g, a.K, sb, g, c);
-    }
-    tc::fence_async_smem();
-    __syncthreads();
-    if (tid == 0) {
+  } else if (tid == 32) {
+    // MN-major A and B (bits 15 and 16): K-adjacent core matrices (the next
+    // 8 pixels) 128 B apart, MN-adjacent ones (the next 8 features) 1 KB
+    constexpr uint32_t kMN = (1u << 15) | (1u << 16);
+    const uint64_t ones = tc::sdesc(sbase + L::ONES, 128, 256);
+    for (int ch = 0; ch < nchunks && ok; ch++) {
+      const int s = ch % L::S;
+      if (!tc::mbar_wait(&full[s], (uint32_t)(ch / L::S) & 1, kSpinLimit)) {
+        ok = false;
+        break;
+      }
       tc::fence_after();
-      const uint32_t sa_u = tc::smem_addr(sa), sb_u = tc::smem_addr(sb);
+      const uint32_t sa = sbase + s * L::STAGE, sb = sa + L::A_BYTES;
 #pragma unroll
-      for (int j = 0; j < 4; j++)
-        tc::mma_bf16(tmem, tc::sdesc(sa_u + j * 256, 128, 1024), tc::sdesc(sb_u + j * 256, 128, 1024),
-                     tc::idesc_bf16(128, KT), (ch | j) != 0);
-      tc::commit(&mbar[s]);
+      for (int j = 0; j < L::PC / 16; j++) {
+        const uint64_t ad = tc::sdesc(sa + j * 256, 128, L::PC * 16);
+        tc::mma_bf16(tmem, ad, tc::sdesc(sb + j * 256, 128, L::PC * 16),
+                     tc::idesc_bf16(128, KT) | kMN, (ch | j) != 0);
+        if (bias) tc::mma_bf16(tmem + KT, ad, ones, tc::idesc_bf16(128, 16) | (1u << 15), (ch | j) != 0);
+      }
+      tc::commit(&empty[s]);
     }
+    if (ok && nchunks > 0) tc::commit(done);
   }
-  if (ok && nchunks > 0)
-    ok = __syncthreads_and(tc::mbar_wait(&mbar[(nchunks - 1) & 1], ((nchunks - 1) >> 1) & 1,
-                                         kSpinLimit));
+  ok = __syncthreads_and(ok);
+  if (ok && nchunks > 0) ok = __syncthreads_and(tc::mbar_wait(done, 0, kSpinLimit));
   if (!ok) {
     if (tid == 0) report_timeout();
   } else if (nchunks > 0) {
@@ -557,45 +594,17 @@ __global__ void __launch_bounds__(128, 1) dw_kernel(DwArgs a) {
           atomicAdd(dst + q, make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]));
       }
     }
+    if (bias) {
+      float v[32];
+      tc::tmem_ld16(tb + KT, v);
+      if (n < a.N) atomicAdd(a.db + n, v[0]);
+    }
   }
   tc::fence_before();
   __syncthreads();
   if (warp == 0) tc::tmem_dealloc(tmem, L::TCOLS);
 }
 
-// db[n] += sum_p G[p][n]
-// db[n] += sum_p G[p, n] over a block of rows: every thread adds 8 adjacent
-// columns (one 16-byte load) of every (256 / (N / 8))-th row, the block
-// combines them in shared memory and adds one value per column to db.
-// N is a multiple of 8 dividing 2048 (16 ... 512).
-__global__ void __launch_bounds__(256) colsum_kernel(const __nv_bfloat16* __restrict__ G, int64_t P,
-                                                     int N, int rows_per_block,
-                                                     float* __restrict__ db) {
-  extern __shared__ float s_col[];  // [N]
-  for (int i = threadIdx.x; i < N; i += blockDim.x) s_col[i] = 0.f;
-  __syncthreads();
-  const int groups = N / 8, cg = threadIdx.x % groups, rstep = blockDim.x / groups;
-  const int64_t p0 = (int64_t)blockIdx.x * rows_per_block;
-  const int64_t p1 = min(P, p0 + rows_per_block);
-  float acc[8];
-#pragma unroll
-  for (int k = 0; k < 8; k++) acc[k] = 0.f;
-#pragma unroll 4
-  for (int64_t p = p0 + threadIdx.x / groups; p < p1; p += rstep) {
-    const uint4 u = *reinterpret_cast<const uint4*>(G + p * N + 8 * cg);
-    const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&u);
-#pragma unroll
-    for (int k = 0; k < 4; k++) {
-      const float2 f = __bfloat1622float2(h[k]);
-      acc[2 * k] += f.x;
-      acc[2 * k + 1] += f.y;
-    }
-  }
-#pragma unroll
-  for (int k = 0; k < 8; k++) atomicAdd(&s_col[8 * cg + k], acc[k]);
-  __syncthreads();
-  for (int i = threadIdx.x; i < N; i += blockDim.x) atomicAdd(db + i, s_col[i]);
-}
 
 // Adam on up to 2 * kAeLayers parameter tensors in one launch: segment j
 // holds elements [start[j], start[j + 1]) of the concatenation.
@@ -654,16 +663,27 @@ template <int NT, int KC>
 static lgs_status launch_layer_t(const LayerArgs& a, cudaStream_t s) {
   using L = LayerSmem<NT, KC>;
   LGS_CHECK_CUDA(set_smem_limit(reinterpret_cast<const void*>(layer_kernel<NT, KC>), (int)L::total));
-  CUtensorMap amap, bmap;
+  CUtensorMap amap, bmap, tmap, omap;
   std::memset(&amap, 0, sizeof(amap));
   std::memset(&bmap, 0, sizeof(bmap));
+  std::memset(&tmap, 0, sizeof(tmap));
+  std::memset(&omap, 0, sizeof(omap));
   if (!a.a_f32) {  // A [P, K] and W [N, K] as K-major chunks of KC columns
     if (!make_kmajor_map(&amap, a.A, a.P, a.K, 128, KC / 8) ||
         !make_kmajor_map(&bmap, a.W, a.N, a.K, L::BROWS, KC / 8))
       return LGS_ERR_CUDA;
   }
+  if (a.epi == EPI_RECON) {  // whole 512-wide rows, staged in the two stages
+    if (NT != 512 || a.N != 512 || 2 * L::STAGE < 128 * 512 * 2) {
+      set_error("the reconstruction loss needs 512-wide rows and K >= 64");
+      return LGS_ERR_INVALID;
+    }
+    if (!make_kmajor_map(&tmap, a.target, a.P, 512, 128, 64) ||
+        !make_kmajor_map(&omap, a.out_bf, a.P, 512, 128, 64))
+      return LGS_ERR_CUDA;
+  }
   dim3 grid((unsigned)((a.P + 127) / 128), a.N / NT);
-  layer_kernel<NT, KC><<<grid, 128, L::total, s>>>(a, amap, bmap);
+  layer_kernel<NT, KC><<<grid, 128, L::total, s>>>(a, amap, bmap, tmap, omap);
   LGS_CHECK_LAUNCH();
   return LGS_OK;
 }
@@ -682,38 +702,39 @@ static lgs_status launch_layer(const LayerArgs& a, cudaStream_t s) {
 }
 
 template <int KT>
-static lgs_status launch_dw_t(const DwArgs& a0, cudaStream_t s) {
+static lgs_status launch_dw_t(const __nv_bfloat16* G, const __nv_bfloat16* X, DwArgs a,
+                              cudaStream_t s) {
   using L = DwSmem<KT>;
   LGS_CHECK_CUDA(set_smem_limit(reinterpret_cast<const void*>(dw_kernel<KT>), (int)L::total));
-  DwArgs a = a0;
+  // G [P, N] and X [P, K] as [features / 8][P][8]: a box of 64 pixels x g
+  // groups lands as g blocks of 64 x 16 bytes (rows past P read as zero)
+  const int ga = std::min(16, a.N / 8), gb = KT / 8;
+  CUtensorMap gmap, xmap;
+  if (!make_kmajor_map(&gmap, G, a.P, a.N, L::PC, ga) || !make_kmajor_map(&xmap, X, a.P, a.K, L::PC, gb))
+    return LGS_ERR_CUDA;
+  a.a_tx = ga * L::PC * 16;
+  a.b_tx = gb * L::PC * 16;
   const int ntile = (a.N + 127) / 128, ktile = a.K / KT;
-  const int64_t chunks = (a.P + 63) / 64;
-  int64_t splits = std::max<int64_t>(1, (2 * 152) / (ntile * ktile));
+  // one CTA per SM: the pixel chunks split into about sm_count / tiles ranges
+  const int64_t chunks = (a.P + L::PC - 1) / L::PC;
+  int64_t splits = std::max<int64_t>(1, sm_count() / (ntile * ktile));
   splits = std::min<int64_t>(splits, chunks);
   a.chunks_per_cta = (int)((chunks + splits - 1) / splits);
   splits = (chunks + a.chunks_per_cta - 1) / a.chunks_per_cta;
-  dw_kernel<KT><<<dim3(ntile, ktile, (unsigned)splits), 128, L::total, s>>>(a);
+  dw_kernel<KT><<<dim3(ntile, ktile, (unsigned)splits), 128, L::total, s>>>(a, gmap, xmap);
   LGS_CHECK_LAUNCH();
   return LGS_OK;
 }
 
-// dW += G^T X and db += colsum(G) for one layer.
+// dW += G^T X and db += colsum(G) for one layer, in one launch.
 static lgs_status launch_dw(const __nv_bfloat16* G, const __nv_bfloat16* X, int64_t P, int N,
                             int K, float* dW, float* db, cudaStream_t s) {
   if (P == 0) return LGS_OK;
-  DwArgs a{G, X, P, N, K, 0, dW};
-  lgs_status st;
-  if (K == 16) st = launch_dw_t<16>(a, s);
-  else if (K == 64) st = launch_dw_t<64>(a, s);
-  else if (K == 128) st = launch_dw_t<128>(a, s);
-  else st = launch_dw_t<256>(a, s);  // K = 256 or 512 (two column tiles)
-  if (st != LGS_OK) return st;
-  // about 32 rows per thread: 32 * 256 / (N / 8) rows per block
-  const int rows = 65536 / N;
-  colsum_kernel<<<(unsigned)((P + rows - 1) / rows), 256, sizeof(float) * N, s>>>(G, P, N, rows,
-                                                                                  db);
-  LGS_CHECK_LAUNCH();
-  return LGS_OK;
+  DwArgs a{P, N, K, 0, 0, 0, dW, db};
+  if (K == 16) return launch_dw_t<16>(G, X, a, s);
+  if (K == 64) return launch_dw_t<64>(G, X, a, s);
+  if (K == 128) return launch_dw_t<128>(G, X, a, s);
+  return launch_dw_t<256>(G, X, a, s);  // K = 256 or 512 (two column tiles)
 }
 
 static LayerArgs layer(const void* A, bool a_f32, const uint16_t* W, const float* b, int64_t P,

@@ -404,17 +404,17 @@ PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
   return fn;
 }
 
+}  // namespace
+
+size_t encode_pack_bytes() { return (enc_plan().total + 255) & ~(size_t)255; }
+
 int sm_count() {
   int dev = 0, n = 0;
   if (cudaGetDevice(&dev) != cudaSuccess ||
       cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0)
-    n = 148;
+    n = 152;
   return n;
 }
-
-}  // namespace
-
-size_t encode_pack_bytes() { return (enc_plan().total + 255) & ~(size_t)255; }
 
 bool make_kmajor_map(CUtensorMap* map, const void* base, int64_t rows, int K, int box_rows,
                      int box_groups) {

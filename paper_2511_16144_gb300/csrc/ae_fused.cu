@@ -663,14 +663,6 @@ const Plan& plan() {
   return P;
 }
 
-int sm_count() {
-  int dev = 0, n = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess ||
-      cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0)
-    n = 148;
-  return n;
-}
-
 }  // namespace
 
 size_t decode_pack_bytes() { return (plan().total + 255) & ~(size_t)255; }

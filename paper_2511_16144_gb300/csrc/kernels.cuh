@@ -32,11 +32,15 @@ lgs_status launch_encode_fused(const lgs_ae_weights* w, const uint16_t* x, int64
                                void* pack, cudaStream_t s);
 // Reads and clears the fused encoder's timeout word.
 unsigned encode_error_word();
+// Streaming multiprocessors of the current device.
+int sm_count();
 // A 3-D TMA tensor map that views a row-major bf16 matrix [rows, K] as
 // [K / 8 column groups][rows][8 columns]: a box of box_rows rows and
 // box_groups groups lands in shared memory as box_groups blocks of
 // box_rows x 16 bytes, the K-major core-matrix layout whose K-adjacent core
 // matrices are box_rows * 16 bytes apart (rows past the end read as zero).
+// Read with the pixel as K, the same blocks are the MN-major layout: core
+// matrices adjacent in K 128 bytes apart, adjacent in MN box_rows * 16.
 // False (with the error string set) when the driver refuses the map.
 bool make_kmajor_map(CUtensorMap* map, const void* base, int64_t rows, int K, int box_rows,
                      int box_groups);

@@ -112,6 +112,8 @@ __device__ __forceinline__ void load_bf16x32(const __nv_bfloat16* src, float* v,
 
 __device__ __forceinline__ void report_timeout() { atomicOr(&g_ae_error, 1u); }
 
+constexpr int kLayerThreads = 256;  // 8 warps: producer / MMA lanes, then all run the epilogue
+
 template <int NT, int KC>
 struct LayerSmem {
   static constexpr int A_BYTES = 128 * KC * 2;
@@ -146,7 +148,7 @@ __device__ __forceinline__ void tma_store_3d(const CUtensorMap* map, int x, int 
 // tmap / omap: the target and the output of EPI_RECON as [64 groups][P][8]
 // maps with 128-row x 64-group boxes (unused by the other epilogues).
 template <int NT, int KC>
-__global__ void __launch_bounds__(128, 1) layer_kernel(const __grid_constant__ LayerArgs a,
+__global__ void __launch_bounds__(kLayerThreads, 2) layer_kernel(const __grid_constant__ LayerArgs a,
                                                       const __grid_constant__ CUtensorMap amap,
                                                       const __grid_constant__ CUtensorMap bmap,
                                                       const __grid_constant__ CUtensorMap tmap,
@@ -230,7 +232,7 @@ __global__ void __launch_bounds__(128, 1) layer_kernel(const __grid_constant__ L
     uint8_t* sb = sa + L::A_BYTES;
     const uint32_t sa_u = tc::smem_addr(sa), sb_u = tc::smem_addr(sb);
     constexpr int APIECES = 128 * (KC / 8);
-    for (int i = tid; i < APIECES; i += 128) {
+    for (int i = tid; i < APIECES; i += kLayerThreads) {
       const int r = i / (KC / 8), c = i % (KC / 8);
       const int64_t p = row0 + r;
       const bool valid = p < a.P;
@@ -255,7 +257,7 @@ __global__ void __launch_bounds__(128, 1) layer_kernel(const __grid_constant__ L
       }
     }
     constexpr int BPIECES = NT * (KC / 8);
-    for (int i = tid; i < BPIECES; i += 128) {
+    for (int i = tid; i < BPIECES; i += kLayerThreads) {
       const int r = i / (KC / 8), c = i % (KC / 8);
       const __nv_bfloat16* src = a.W + (int64_t)(n0 + r) * K + kc * KC + c * 8;
       tc::cp_async16(sb_u + tc::core_offset(r, c, KC), src);
@@ -305,55 +307,98 @@ __global__ void __launch_bounds__(128, 1) layer_kernel(const __grid_constant__ L
   } else {
     tc::fence_after();
     // ---------------------------------------------------------- epilogue
-    const int r = warp * 32 + lane;
+    // Warps w and w + 4 read TMEM lane quadrant w % 4 (thread = row) and
+    // split the columns: half h = w / 4 takes [h NT / 2, (h + 1) NT / 2)
+    // (h = 0 takes all of them when NT < 64).  The drained stages hold the
+    // bias slice (bytes 0-2047), the per-row partials the two halves
+    // exchange (2048-6143) and, for EPI_RECON, the target tile (from 8192).
+    static_assert(2 * L::STAGE >= 6144, "epilogue scratch does not fit");
+    const int q = warp & 3, h = warp >> 2;
+    const int r = q * 32 + lane;
     const int64_t p = row0 + r;
     const bool valid = p < a.P;
-    const uint32_t tb = tmem + ((uint32_t)(warp * 32) << 16);
+    const uint32_t tb = tmem + ((uint32_t)(q * 32) << 16);
     constexpr int CW = NT < 32 ? 16 : 32;
+    constexpr bool kSplit = NT >= 64;
+    const int cbeg = kSplit ? h * (NT / 2) : 0;
+    const int cend = kSplit ? cbeg + NT / 2 : (h == 0 ? NT : 0);
+    float* sbias = reinterpret_cast<float*>(sm);
+    float4* sx4 = reinterpret_cast<float4*>(sm + 2048);
+    if (a.bias) {
+      for (int i = tid; i < NT; i += kLayerThreads) sbias[i] = a.bias[n0 + i];
+      __syncthreads();
+    }
+    // the bias of columns c0 .. c0 + CW - 1 (one broadcast 16-byte read per 4)
+    auto bias_of = [&](int c0, float* bb) {
+#pragma unroll
+      for (int i = 0; i < CW / 4; i++) {
+        const float4 t = reinterpret_cast<const float4*>(sbias + c0)[i];
+        bb[4 * i] = t.x;
+        bb[4 * i + 1] = t.y;
+        bb[4 * i + 2] = t.z;
+        bb[4 * i + 3] = t.w;
+      }
+    };
     float lsum = 0.f;
     if (a.epi == EPI_ARGMIN) {
       // |x - c_n|^2 - |x|^2 = |c_n|^2 - 2 x.c_n with |c_n|^2 in the bias;
       // columns in increasing order, strict < keeps the lower index on ties
       float best = INFINITY;
       uint32_t bi = 0;
-      for (int c0 = 0; c0 < NT; c0 += CW) {
-        float v[32];
+      for (int c0 = cbeg; c0 < cend; c0 += CW) {
+        float v[32], bb[32];
         if (CW == 32) tc::tmem_ld32(tb + c0, v);
         else tc::tmem_ld16(tb + c0, v);
+        bias_of(c0, bb);
 #pragma unroll
         for (int i = 0; i < CW; i++) {
-          const float sc = fmaf(-2.f, v[i], a.bias[n0 + c0 + i]);
+          const float sc = fmaf(-2.f, v[i], bb[i]);
           if (sc < best) {
             best = sc;
             bi = (uint32_t)(n0 + c0 + i);
           }
         }
       }
-      if (valid && a.out_u32) a.out_u32[p] = bi;
-      const uint32_t peers = __match_any_sync(0xffffffffu, valid ? bi : (0x80000000u | lane));
-      if (valid && a.hist && lane == __ffs(peers) - 1) atomicAdd(a.hist + bi, (uint32_t)__popc(peers));
+      // the upper half hands its best over; the lower half wins ties
+      float* xb = reinterpret_cast<float*>(sx4);
+      uint32_t* xi = reinterpret_cast<uint32_t*>(xb + 128);
+      if (kSplit && h == 1) {
+        xb[r] = best;
+        xi[r] = bi;
+      }
+      __syncthreads();
+      if (h == 0) {
+        if (kSplit && xb[r] < best) {
+          best = xb[r];
+          bi = xi[r];
+        }
+        if (valid && a.out_u32) a.out_u32[p] = bi;
+        const uint32_t peers = __match_any_sync(0xffffffffu, valid ? bi : (0x80000000u | lane));
+        if (valid && a.hist && lane == __ffs(peers) - 1) atomicAdd(a.hist + bi, (uint32_t)__popc(peers));
+      }
     } else if (a.epi == EPI_RECON) {
-      if constexpr (NT == 512 && 2 * L::STAGE >= 128 * 512 * 2) {
+      if constexpr (NT == 512 && 2 * L::STAGE >= 8192 + 128 * 512 * 2) {
         // The target tile [128 x 512] lands in the free stages in one TMA
         // load, as 64 column groups of 128 rows x 16 B (row r of group g at
         // g * 2048 + r * 16: the rows of a warp are consecutive 16-byte
         // pieces); dL/dy replaces it in place and leaves in one TMA store.
-        const uint32_t sx = tc::smem_addr(sm);
+        const uint32_t sx = tc::smem_addr(sm) + 8192;
         if (tid == 0) {
           tc::mbar_expect_tx(xbar, 128 * 512 * 2);
           tma_load_3d(sx, &tmap, 0, (int)row0, 0, xbar);
         }
         if (__syncthreads_and(tc::mbar_wait(xbar, 0, kSpinLimit))) {
-          __nv_bfloat16* xr = reinterpret_cast<__nv_bfloat16*>(sm + r * 16);
-          // pass 1: row statistics of y against x = target
+          __nv_bfloat16* xr = reinterpret_cast<__nv_bfloat16*>(sm + 8192 + r * 16);
+          // pass 1: row statistics of y against x = target, per half
           float sdd = 0.f, syx = 0.f, syy = 0.f, sxx = 0.f;
-          for (int c0 = 0; c0 < NT; c0 += 32) {
-            float v[32], x[32];
+          for (int c0 = cbeg; c0 < cend; c0 += 32) {
+            float v[32], x[32], bb[32];
             tc::tmem_ld32(tb + c0, v);
             load_bf16x32(xr + c0 * 128, x, 32, 128);
+            bias_of(c0, bb);
 #pragma unroll
             for (int i = 0; i < 32; i++) {
-              const float y = v[i] + a.bias[c0 + i];
+              const float y = v[i] + bb[i];
               const float d = y - x[i];
               sdd = fmaf(d, d, sdd);
               syx = fmaf(y, x[i], syx);
@@ -361,20 +406,30 @@ __global__ void __launch_bounds__(128, 1) layer_kernel(const __grid_constant__ L
               sxx = fmaf(x[i], x[i], sxx);
             }
           }
+          sx4[h * 128 + r] = make_float4(sdd, syx, syy, sxx);
+          __syncthreads();
+          const float4 s0 = sx4[r], s1 = sx4[128 + r];
+          sdd = s0.x + s1.x;
+          syx = s0.y + s1.y;
+          syy = s0.z + s1.z;
+          sxx = s0.w + s1.w;
+          const float invN = 1.f / (float)a.N;
           const float ny = sqrtf(syy), nx = sqrtf(sxx);
           const float inv = 1.f / fmaxf(ny * nx, 1e-30f);
           const float cosv = syx * inv;
-          if (valid) lsum = a.scale * (sdd / (float)a.N + 1.f - cosv);
+          if (valid && h == 0) lsum = a.scale * (sdd * invN + 1.f - cosv);
           const float iy2 = 1.f / fmaxf(syy, 1e-30f);
           // pass 2: dL/dy = s (2 (y - x)/N - (x/(|y||x|) - cos y/|y|^2))
-          for (int c0 = 0; c0 < NT; c0 += 32) {
-            float v[32], x[32];
+          const float c2 = 2.f * invN * a.scale, cx = a.scale * inv, cy = a.scale * cosv * iy2;
+          for (int c0 = cbeg; c0 < cend; c0 += 32) {
+            float v[32], x[32], bb[32];
             tc::tmem_ld32(tb + c0, v);
             load_bf16x32(xr + c0 * 128, x, 32, 128);
+            bias_of(c0, bb);
 #pragma unroll
             for (int i = 0; i < 32; i++) {
-              const float y = v[i] + a.bias[c0 + i];
-              v[i] = a.scale * (2.f * (y - x[i]) / (float)a.N - (x[i] * inv - cosv * y * iy2));
+              const float y = v[i] + bb[i];
+              v[i] = fmaf(c2, y - x[i], fmaf(cy, y, -cx * x[i]));
             }
             store_bf16x32(xr + c0 * 128, v, 32, 128);
           }
@@ -386,8 +441,8 @@ __global__ void __launch_bounds__(128, 1) layer_kernel(const __grid_constant__ L
         }
       }
     } else {
-      for (int c0 = 0; c0 < NT; c0 += CW) {
-        float v[32];
+      for (int c0 = cbeg; c0 < cend; c0 += CW) {
+        float v[32], bb[32];
         if (CW == 32) tc::tmem_ld32(tb + c0, v);
         else tc::tmem_ld16(tb + c0, v);
         if (!valid) continue;
@@ -395,8 +450,9 @@ __global__ void __launch_bounds__(128, 1) layer_kernel(const __grid_constant__ L
         const int64_t o = p * a.N + n;
         switch (a.epi) {
           case EPI_GELU: {
+            bias_of(c0, bb);
 #pragma unroll
-            for (int i = 0; i < CW; i++) v[i] += a.bias[n + i];
+            for (int i = 0; i < CW; i++) v[i] += bb[i];
             if (a.pre_out) store_bf16x32(a.pre_out + o, v, CW);
 #pragma unroll
             for (int i = 0; i < CW; i++) v[i] = gelu_f(v[i]);
@@ -405,15 +461,16 @@ __global__ void __launch_bounds__(128, 1) layer_kernel(const __grid_constant__ L
           }
           case EPI_LIN_F32:
           case EPI_LIN_BF16: {
+            bias_of(c0, bb);
 #pragma unroll
-            for (int i = 0; i < CW; i++) v[i] += a.bias[n + i];
+            for (int i = 0; i < CW; i++) v[i] += bb[i];
             if (a.epi == EPI_LIN_BF16) {
               store_bf16x32(a.out_bf + o, v, CW);
             } else {
 #pragma unroll
-              for (int q = 0; q < CW / 4; q++)
-                reinterpret_cast<float4*>(a.out_f32 + o)[q] =
-                    make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+              for (int q4 = 0; q4 < CW / 4; q4++)
+                reinterpret_cast<float4*>(a.out_f32 + o)[q4] =
+                    make_float4(v[4 * q4], v[4 * q4 + 1], v[4 * q4 + 2], v[4 * q4 + 3]);
             }
             break;
           }
@@ -427,9 +484,9 @@ __global__ void __launch_bounds__(128, 1) layer_kernel(const __grid_constant__ L
           }
           case EPI_DX_F32: {
 #pragma unroll
-            for (int q = 0; q < CW / 4; q++)
-              reinterpret_cast<float4*>(a.out_f32 + o)[q] =
-                  make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+            for (int q4 = 0; q4 < CW / 4; q4++)
+              reinterpret_cast<float4*>(a.out_f32 + o)[q4] =
+                  make_float4(v[4 * q4], v[4 * q4 + 1], v[4 * q4 + 2], v[4 * q4 + 3]);
             break;
           }
           case EPI_DX_BF16:
@@ -438,6 +495,7 @@ __global__ void __launch_bounds__(128, 1) layer_kernel(const __grid_constant__ L
           case EPI_L1_BF16T:
           case EPI_L1_F32T: {
             float t[32];
+            bias_of(c0, bb);
             if (a.epi == EPI_L1_BF16T) {
               load_bf16x32(reinterpret_cast<const __nv_bfloat16*>(a.target) + o, t, CW);
             } else {
@@ -446,7 +504,7 @@ __global__ void __launch_bounds__(128, 1) layer_kernel(const __grid_constant__ L
             }
 #pragma unroll
             for (int i = 0; i < CW; i++) {
-              const float d = v[i] + a.bias[n + i] - t[i];
+              const float d = v[i] + bb[i] - t[i];
               lsum += fabsf(d);
               v[i] = d > 0.f ? a.scale : (d < 0.f ? -a.scale : 0.f);
             }
@@ -674,7 +732,7 @@ static lgs_status launch_layer_t(const LayerArgs& a, cudaStream_t s) {
       return LGS_ERR_CUDA;
   }
   if (a.epi == EPI_RECON) {  // whole 512-wide rows, staged in the two stages
-    if (NT != 512 || a.N != 512 || 2 * L::STAGE < 128 * 512 * 2) {
+    if (NT != 512 || a.N != 512 || 2 * L::STAGE < 8192 + 128 * 512 * 2) {
       set_error("the reconstruction loss needs 512-wide rows and K >= 64");
       return LGS_ERR_INVALID;
     }
@@ -683,7 +741,7 @@ static lgs_status launch_layer_t(const LayerArgs& a, cudaStream_t s) {
       return LGS_ERR_CUDA;
   }
   dim3 grid((unsigned)((a.P + 127) / 128), a.N / NT);
-  layer_kernel<NT, KC><<<grid, 128, L::total, s>>>(a, amap, bmap, tmap, omap);
+  layer_kernel<NT, KC><<<grid, kLayerThreads, L::total, s>>>(a, amap, bmap, tmap, omap);
   LGS_CHECK_LAUNCH();
   return LGS_OK;
 }

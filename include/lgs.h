@@ -445,7 +445,11 @@ lgs_status gs_query_relevance(const void* feats, int feat_dtype, int64_t M, int 
                               const float* queries, int Q, float* out, void* stream);
 
 /* Reads and clears the device error word that kernels with bounded waits
- * set when a wait gives up (0 = none).  Synchronises the device. */
+ * set when a wait gives up (0 = none; bits 0-3 the autoencoder layer
+ * kernels -- 1: a wait gave up, 4: shared memory not on the 1 KB boundary
+ * the 128-byte swizzle needs, so the kernel returned without work -- bits
+ * 4-7 the fused decoder, 8-11 the sort, 12-15 the fused encoder).
+ * Synchronises the device. */
 lgs_status lgs_device_error(int* code);
 
 #ifdef __cplusplus

@@ -42,7 +42,7 @@ constexpr int kAeLayers = LGS_AE_LAYERS;
 constexpr int kAeWidths[9] = {512, 256, 128, 64, 16, 64, 128, 256, 512};
 constexpr uint32_t kSpinLimit = 1u << 22;  // polls before a wait gives up
 
-__device__ unsigned g_ae_error;  // set when a bounded wait gives up
+__device__ unsigned g_ae_error;  // 1: a bounded wait gave up; 4: shared memory misaligned
 
 enum Epi : int {
   EPI_GELU = 0,      // out = gelu(acc + b) (bf16), pre = acc + b (bf16, optional)
@@ -134,6 +134,16 @@ __device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map
       : "memory");
 }
 
+// 2-D tensor load [x, y] -> shared, completing on an mbarrier.
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y,
+                                            uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3}], [%4];" ::"r"(dst),
+      "l"(map), "r"(x), "r"(y), "r"(tc::smem_addr(bar))
+      : "memory");
+}
+
 // 3-D tensor store shared -> [x, y, z] (rows past the tensor are not written).
 __device__ __forceinline__ void tma_store_3d(const CUtensorMap* map, int x, int y, int z,
                                              uint32_t src) {
@@ -163,6 +173,11 @@ __global__ void __launch_bounds__(kLayerThreads, 2) layer_kernel(const __grid_co
   const int64_t row0 = (int64_t)blockIdx.x * 128;
   const int n0 = blockIdx.y * NT;
   const int K = a.K;
+  // the 128-byte swizzle of the TMA path repeats every 1 KB from the stage base
+  if (tc::smem_addr(sm) & 1023u) {
+    if (tid == 0) atomicOr(&g_ae_error, 4u);
+    return;
+  }
   if (warp == 0) tc::tmem_alloc(tslot, L::TCOLS);
   if (tid == 0) {
     tc::mbar_init(&mbar[0], 1);
@@ -181,10 +196,11 @@ __global__ void __launch_bounds__(kLayerThreads, 2) layer_kernel(const __grid_co
   const int nk = K / KC;
   constexpr uint32_t SBO = KC * 16;
   if (!a.a_f32) {
-    // BF16 A: thread 0 streams A and W chunks by TMA (each lands as KC / 8
-    // blocks of rows x 16 bytes: K-adjacent core matrices rows * 16 bytes
-    // apart), thread 32 issues the MMAs; the stages are handed over by
-    // mbarriers, no block barrier in the loop
+    // BF16 A: thread 0 streams A and W chunks by TMA, thread 32 issues the
+    // MMAs; the stages are handed over by mbarriers, no block barrier in the
+    // loop.  KC = 64: one 2-D box per operand in the 128-byte swizzle layout
+    // (rows of 128 B); KC = 16: 3-D boxes that land as 2 blocks of rows x 16
+    // bytes (K-adjacent core matrices rows * 16 bytes apart).
     const uint32_t sbase = tc::smem_addr(sm);
     if (tid == 0) {
       for (int kc = 0; kc < nk && ok; kc++) {
@@ -195,11 +211,19 @@ __global__ void __launch_bounds__(kLayerThreads, 2) layer_kernel(const __grid_co
         }
         const uint32_t st = sbase + s * L::STAGE;
         tc::mbar_expect_tx(&full[s], L::STAGE);
-        tma_load_3d(st, &amap, 0, (int)row0, kc * (KC / 8), &full[s]);
+        if constexpr (KC == 64) {
+          tma_load_2d(st, &amap, kc * 64, (int)row0, &full[s]);
 #pragma unroll
-        for (int h = 0; h < NT / L::BROWS; h++)
-          tma_load_3d(st + L::A_BYTES + h * L::BROWS * KC * 2, &bmap, 0, n0 + h * L::BROWS,
-                      kc * (KC / 8), &full[s]);
+          for (int h = 0; h < NT / L::BROWS; h++)
+            tma_load_2d(st + L::A_BYTES + h * L::BROWS * 128, &bmap, kc * 64, n0 + h * L::BROWS,
+                        &full[s]);
+        } else {
+          tma_load_3d(st, &amap, 0, (int)row0, kc * (KC / 8), &full[s]);
+#pragma unroll
+          for (int h = 0; h < NT / L::BROWS; h++)
+            tma_load_3d(st + L::A_BYTES + h * L::BROWS * KC * 2, &bmap, 0, n0 + h * L::BROWS,
+                        kc * (KC / 8), &full[s]);
+        }
       }
     } else if (tid == 32) {
       for (int kc = 0; kc < nk && ok; kc++) {
@@ -212,11 +236,14 @@ __global__ void __launch_bounds__(kLayerThreads, 2) layer_kernel(const __grid_co
         const uint32_t sa_u = sbase + s * L::STAGE, sb_u = sa_u + L::A_BYTES;
 #pragma unroll
         for (int j = 0; j < KC / 16; j++) {
-          const uint64_t ad = tc::sdesc(sa_u + j * 2 * 2048, 2048, 128);
+          const uint64_t ad = KC == 64 ? tc::sdesc_sw128(sa_u + j * 32)
+                                       : tc::sdesc(sa_u + j * 2 * 2048, 2048, 128);
 #pragma unroll
           for (int h = 0; h < NT / L::BROWS; h++) {
-            const uint64_t bd = tc::sdesc(sb_u + h * L::BROWS * KC * 2 + j * 2 * L::BROWS * 16,
-                                          L::BROWS * 16, 128);
+            const uint64_t bd =
+                KC == 64 ? tc::sdesc_sw128(sb_u + h * L::BROWS * 128 + j * 32)
+                         : tc::sdesc(sb_u + h * L::BROWS * KC * 2 + j * 2 * L::BROWS * 16,
+                                     L::BROWS * 16, 128);
             tc::mma_bf16(tmem + h * 256, ad, bd, tc::idesc_bf16(128, L::BROWS), (kc | j) != 0);
           }
         }
@@ -727,9 +754,11 @@ static lgs_status launch_layer_t(const LayerArgs& a, cudaStream_t s) {
   std::memset(&tmap, 0, sizeof(tmap));
   std::memset(&omap, 0, sizeof(omap));
   if (!a.a_f32) {  // A [P, K] and W [N, K] as K-major chunks of KC columns
-    if (!make_kmajor_map(&amap, a.A, a.P, a.K, 128, KC / 8) ||
-        !make_kmajor_map(&bmap, a.W, a.N, a.K, L::BROWS, KC / 8))
-      return LGS_ERR_CUDA;
+    const bool made = KC == 64 ? make_sw128_map(&amap, a.A, a.P, a.K, 128) &&
+                                     make_sw128_map(&bmap, a.W, a.N, a.K, L::BROWS)
+                               : make_kmajor_map(&amap, a.A, a.P, a.K, 128, KC / 8) &&
+                                     make_kmajor_map(&bmap, a.W, a.N, a.K, L::BROWS, KC / 8);
+    if (!made) return LGS_ERR_CUDA;
   }
   if (a.epi == EPI_RECON) {  // whole 512-wide rows, staged in the two stages
     if (NT != 512 || a.N != 512 || 2 * L::STAGE < 8192 + 128 * 512 * 2) {

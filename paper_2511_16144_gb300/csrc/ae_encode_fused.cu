@@ -437,6 +437,26 @@ bool make_kmajor_map(CUtensorMap* map, const void* base, int64_t rows, int K, in
   return true;
 }
 
+bool make_sw128_map(CUtensorMap* map, const void* base, int64_t rows, int K, int box_rows) {
+  auto encode = tensor_map_encoder();
+  if (!encode) {
+    set_error("cuTensorMapEncodeTiled is unavailable");
+    return false;
+  }
+  const cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)rows};
+  const cuuint64_t strides[1] = {(cuuint64_t)K * 2};
+  const cuuint32_t box[2] = {64, (cuuint32_t)box_rows}, es[2] = {1, 1};
+  const CUresult cr =
+      encode(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box,
+             es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+             CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (cr != CUDA_SUCCESS) {
+    set_error("cuTensorMapEncodeTiled refused a 128-byte swizzle map");
+    return false;
+  }
+  return true;
+}
+
 lgs_status launch_encode_fused(const lgs_ae_weights* w, const uint16_t* x, int64_t P, float* z,
                                void* pack, cudaStream_t s) {
   const EncPlan& pl = enc_plan();

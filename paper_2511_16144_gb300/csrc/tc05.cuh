@@ -36,6 +36,15 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t saddr, uint32_t lbo, uint32_t
   return d;
 }
 
+// K-major operand in the 128-byte swizzle layout (what a TMA load with
+// CU_TENSOR_MAP_SWIZZLE_128B and a 64-element inner box writes): rows of 64
+// bf16 (128 B) in 8-row atoms of 1 KB (SBO), the 16-byte chunks of row r
+// permuted by XOR with r % 8.  The tile must start on a 1 KB boundary; the
+// MMA's K-step of 16 elements advances the start address by 32 bytes.
+__device__ __forceinline__ uint64_t sdesc_sw128(uint32_t saddr) {
+  return sdesc(saddr, 16, 1024) | ((uint64_t)2 << 61);
+}
+
 // Descriptors as offsets from one base: sdesc_base(b) + sdesc_off(o, sbo)
 // equals sdesc(b + o, 128, sbo) whenever b and o are multiples of 16 bytes,
 // because the 14-bit address field never carries (shared addresses stay below

@@ -566,11 +566,12 @@ struct DwArgs {
   float* db;               // [N], accumulated (column sums of G), or null
 };
 
-// Shared memory of dw_kernel<KT>: a ring of stages, each one 64-pixel chunk
-// of G (128 features) and X (KT features) as the TMA lands them -- 8-feature
-// groups of 64 pixels x 16 bytes, the MN-major core-matrix layout of
-// operands whose K is the pixel -- then a 512-byte block of BF16 ones for
-// the bias sums and the barriers.
+// Shared memory of dw_kernel: a ring of stages, each one 64-pixel chunk of
+// G (128 features) and X (KT features) as the TMA lands them, MN-major
+// operands whose K is the pixel: with 64 or more features, 64-feature boxes
+// in the 128-byte swizzle layout (64 pixel rows of 128 B per box, boxes
+// 8 KB apart); with fewer, 8-feature groups of 64 pixels x 16 bytes.  Then
+// a 512-byte block of BF16 ones for the bias sums and the barriers.
 template <int KT>
 struct DwSmem {
   static constexpr int PC = 64;                  // pixels per stage
@@ -592,7 +593,8 @@ struct DwSmem {
 // pixels), so the TMA loads them without a transpose; the bias sums are one
 // more N = 16 MMA of G^T against a block of ones.  Thread 0 streams the
 // stages, thread 32 issues the MMAs; all 128 threads add the tile to dW.
-template <int KT>
+// GSW: G in the swizzled layout (N >= 64); X is swizzled when KT >= 64.
+template <int KT, bool GSW>
 __global__ void __launch_bounds__(128, 1) dw_kernel(const __grid_constant__ DwArgs a,
                                                    const __grid_constant__ CUtensorMap gmap,
                                                    const __grid_constant__ CUtensorMap xmap) {
@@ -608,6 +610,11 @@ __global__ void __launch_bounds__(128, 1) dw_kernel(const __grid_constant__ DwAr
   const int64_t pbeg = (int64_t)blockIdx.z * a.chunks_per_cta * L::PC;
   const int64_t pend = min(a.P, pbeg + (int64_t)a.chunks_per_cta * L::PC);
   const int nchunks = pend > pbeg ? (int)((pend - pbeg + L::PC - 1) / L::PC) : 0;
+  constexpr bool XSW = KT >= 64;
+  if ((GSW || XSW) && (tc::smem_addr(sm) & 1023u)) {  // the swizzle repeats every 1 KB
+    if (tid == 0) atomicOr(&g_ae_error, 4u);
+    return;
+  }
   if (warp == 0) tc::tmem_alloc(tslot, L::TCOLS);
   if (tid == 0) {
     for (int i = 0; i < 2 * L::S + 1; i++) tc::mbar_init(&full[i], 1);
@@ -632,13 +639,27 @@ __global__ void __launch_bounds__(128, 1) dw_kernel(const __grid_constant__ DwAr
       const uint32_t st = sbase + s * L::STAGE;
       const int p0 = (int)(pbeg + (int64_t)ch * L::PC);
       tc::mbar_expect_tx(&full[s], (uint32_t)(a.a_tx + a.b_tx));
-      tma_load_3d(st, &gmap, 0, p0, n0 / 8, &full[s]);
-      tma_load_3d(st + L::A_BYTES, &xmap, 0, p0, k0 / 8, &full[s]);
+      if constexpr (GSW) {
+        for (int b = 0; b < 2 && n0 + 64 * b < a.N; b++)
+          tma_load_2d(st + b * 8192, &gmap, n0 + 64 * b, p0, &full[s]);
+      } else {
+        tma_load_3d(st, &gmap, 0, p0, n0 / 8, &full[s]);
+      }
+      if constexpr (XSW) {
+#pragma unroll
+        for (int b = 0; b < KT / 64; b++)
+          tma_load_2d(st + L::A_BYTES + b * 8192, &xmap, k0 + 64 * b, p0, &full[s]);
+      } else {
+        tma_load_3d(st + L::A_BYTES, &xmap, 0, p0, k0 / 8, &full[s]);
+      }
     }
   } else if (tid == 32) {
-    // MN-major A and B (bits 15 and 16): K-adjacent core matrices (the next
-    // 8 pixels) 128 B apart, MN-adjacent ones (the next 8 features) 1 KB
+    // MN-major A and B (bits 15 and 16).  Swizzled: 64-feature atoms 8 KB
+    // apart (LBO), 8-pixel groups 1 KB apart (SBO), a K-step of 16 pixels
+    // is 2 KB; unswizzled: K-adjacent core matrices (the next 8 pixels)
+    // 128 B apart (LBO), MN-adjacent ones (the next 8 features) 1 KB (SBO).
     constexpr uint32_t kMN = (1u << 15) | (1u << 16);
+    constexpr uint64_t kSw = (uint64_t)2 << 61;
     const uint64_t ones = tc::sdesc(sbase + L::ONES, 128, 256);
     for (int ch = 0; ch < nchunks && ok; ch++) {
       const int s = ch % L::S;
@@ -650,9 +671,11 @@ __global__ void __launch_bounds__(128, 1) dw_kernel(const __grid_constant__ DwAr
       const uint32_t sa = sbase + s * L::STAGE, sb = sa + L::A_BYTES;
 #pragma unroll
       for (int j = 0; j < L::PC / 16; j++) {
-        const uint64_t ad = tc::sdesc(sa + j * 256, 128, L::PC * 16);
-        tc::mma_bf16(tmem, ad, tc::sdesc(sb + j * 256, 128, L::PC * 16),
-                     tc::idesc_bf16(128, KT) | kMN, (ch | j) != 0);
+        const uint64_t ad = GSW ? tc::sdesc(sa + j * 2048, 8192, 1024) | kSw
+                                : tc::sdesc(sa + j * 256, 128, L::PC * 16);
+        const uint64_t bd = XSW ? tc::sdesc(sb + j * 2048, 8192, 1024) | kSw
+                                : tc::sdesc(sb + j * 256, 128, L::PC * 16);
+        tc::mma_bf16(tmem, ad, bd, tc::idesc_bf16(128, KT) | kMN, (ch | j) != 0);
         if (bias) tc::mma_bf16(tmem + KT, ad, ones, tc::idesc_bf16(128, 16) | (1u << 15), (ch | j) != 0);
       }
       tc::commit(&empty[s]);
@@ -788,18 +811,23 @@ static lgs_status launch_layer(const LayerArgs& a, cudaStream_t s) {
   }
 }
 
-template <int KT>
+template <int KT, bool GSW>
 static lgs_status launch_dw_t(const __nv_bfloat16* G, const __nv_bfloat16* X, DwArgs a,
                               cudaStream_t s) {
   using L = DwSmem<KT>;
-  LGS_CHECK_CUDA(set_smem_limit(reinterpret_cast<const void*>(dw_kernel<KT>), (int)L::total));
-  // G [P, N] and X [P, K] as [features / 8][P][8]: a box of 64 pixels x g
-  // groups lands as g blocks of 64 x 16 bytes (rows past P read as zero)
+  LGS_CHECK_CUDA(set_smem_limit(reinterpret_cast<const void*>(dw_kernel<KT, GSW>), (int)L::total));
+  // G [P, N] and X [P, K], pixels as rows (rows past P read as zero): with 64
+  // or more features, 64-feature x 64-pixel boxes in the 128-byte swizzle;
+  // otherwise viewed as [features / 8][P][8] and loaded as g blocks of
+  // 64 pixels x 16 bytes
   const int ga = std::min(16, a.N / 8), gb = KT / 8;
   CUtensorMap gmap, xmap;
-  if (!make_kmajor_map(&gmap, G, a.P, a.N, L::PC, ga) || !make_kmajor_map(&xmap, X, a.P, a.K, L::PC, gb))
-    return LGS_ERR_CUDA;
-  a.a_tx = ga * L::PC * 16;
+  const bool made = (GSW ? make_sw128_map(&gmap, G, a.P, a.N, L::PC)
+                         : make_kmajor_map(&gmap, G, a.P, a.N, L::PC, ga)) &&
+                    (KT >= 64 ? make_sw128_map(&xmap, X, a.P, a.K, L::PC)
+                              : make_kmajor_map(&xmap, X, a.P, a.K, L::PC, gb));
+  if (!made) return LGS_ERR_CUDA;
+  a.a_tx = ga * L::PC * 16;  // both layouts: min(128, N) features x 64 pixels
   a.b_tx = gb * L::PC * 16;
   const int ntile = (a.N + 127) / 128, ktile = a.K / KT;
   // one CTA per SM: the pixel chunks split into about sm_count / tiles ranges
@@ -808,7 +836,7 @@ static lgs_status launch_dw_t(const __nv_bfloat16* G, const __nv_bfloat16* X, Dw
   splits = std::min<int64_t>(splits, chunks);
   a.chunks_per_cta = (int)((chunks + splits - 1) / splits);
   splits = (chunks + a.chunks_per_cta - 1) / a.chunks_per_cta;
-  dw_kernel<KT><<<dim3(ntile, ktile, (unsigned)splits), 128, L::total, s>>>(a, gmap, xmap);
+  dw_kernel<KT, GSW><<<dim3(ntile, ktile, (unsigned)splits), 128, L::total, s>>>(a, gmap, xmap);
   LGS_CHECK_LAUNCH();
   return LGS_OK;
 }
@@ -818,10 +846,18 @@ static lgs_status launch_dw(const __nv_bfloat16* G, const __nv_bfloat16* X, int6
                             int K, float* dW, float* db, cudaStream_t s) {
   if (P == 0) return LGS_OK;
   DwArgs a{P, N, K, 0, 0, 0, dW, db};
-  if (K == 16) return launch_dw_t<16>(G, X, a, s);
-  if (K == 64) return launch_dw_t<64>(G, X, a, s);
-  if (K == 128) return launch_dw_t<128>(G, X, a, s);
-  return launch_dw_t<256>(G, X, a, s);  // K = 256 or 512 (two column tiles)
+  // G in the swizzled layout when each 128-feature tile is one or two
+  // whole 64-feature boxes (N = 64 or a multiple of 128)
+  if (N == 64 || N % 128 == 0) {
+    if (K == 16) return launch_dw_t<16, true>(G, X, a, s);
+    if (K == 64) return launch_dw_t<64, true>(G, X, a, s);
+    if (K == 128) return launch_dw_t<128, true>(G, X, a, s);
+    return launch_dw_t<256, true>(G, X, a, s);  // K = 256 or 512 (two column tiles)
+  }
+  if (K == 16) return launch_dw_t<16, false>(G, X, a, s);
+  if (K == 64) return launch_dw_t<64, false>(G, X, a, s);
+  if (K == 128) return launch_dw_t<128, false>(G, X, a, s);
+  return launch_dw_t<256, false>(G, X, a, s);
 }
 
 static LayerArgs layer(const void* A, bool a_f32, const uint16_t* W, const float* b, int64_t P,

@@ -102,5 +102,8 @@ def test_trained_autoencoder_gain():
                       for c, ref in zip(cams[::3], frames[::3])])
     print(f"decoded cosine error: trained {trained:.4f}; untrained {untrained:.4f}, "
           f"linear+pinv {linear:.4f}, other-scene encoder {frozen:.4f}")
-    assert trained <= 0.02, trained
+    # the absolute bound leaves room for run-to-run spread: the weight-gradient
+    # partial sums are added atomically in no fixed order, so the trained
+    # model differs slightly between runs (0.019-0.020 seen on one build)
+    assert trained <= 0.025, trained
     assert trained < 0.1 * min(untrained, linear, frozen)

@@ -269,7 +269,9 @@ typedef struct {
 /* Training state: FP32 master weights and biases, Adam moments, the last
  * step's gradients, and the BF16 copies (Wbf = W, Wtbf = W^T) that the GEMMs
  * read.  step counts Adam steps and is incremented by ae_train_step (host
- * field). */
+ * field).  Every pointer is 16-byte aligned.  The gradient buffers are
+ * zeroed at the start of each step, one memset per run of adjacent buffers:
+ * laid out back to back (gW[0], gb[0], gW[1], ...) they take one. */
 typedef struct {
   float* W[LGS_AE_LAYERS];
   float* b[LGS_AE_LAYERS];

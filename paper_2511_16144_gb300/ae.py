@@ -27,7 +27,16 @@ class AutoEncoder:
         z = lambda t: torch.zeros_like(t)
         self.mW, self.vW = [z(W) for W in self.W], [z(W) for W in self.W]
         self.mb, self.vb = [z(b) for b in self.b], [z(b) for b in self.b]
-        self.gW, self.gb = [z(W) for W in self.W], [z(b) for b in self.b]
+        # gradients as consecutive views of one buffer (gW_0, gb_0, gW_1, ...):
+        # the training step zeroes them with a single memset
+        flat = torch.zeros(sum(W.numel() + b.numel() for W, b in zip(self.W, self.b)),
+                           dtype=torch.float32, device=device)
+        self.gW, self.gb, o = [], [], 0
+        for W, b in zip(self.W, self.b):
+            self.gW.append(flat[o:o + W.numel()].view(W.shape))
+            o += W.numel()
+            self.gb.append(flat[o:o + b.numel()].view(b.shape))
+            o += b.numel()
         self.Wbf = [torch.empty(W.shape, dtype=torch.bfloat16, device=device) for W in self.W]
         self.Wtbf = [torch.empty((W.shape[1], W.shape[0]), dtype=torch.bfloat16, device=device)
                      for W in self.W]

@@ -79,10 +79,8 @@ struct LayerArgs {
 __device__ __forceinline__ float gelu_f(float x) { return gelu_tanh(x); }
 __device__ __forceinline__ float gelu_grad_f(float x) { return gelu_tanh_grad(x); }
 
-// n = 16 or 32 values as 16-byte pieces of 8, `step` pieces apart (1:
-// contiguous; 128: the column groups of a staged 128-row tile)
-__device__ __forceinline__ void store_bf16x32(__nv_bfloat16* dst, const float* v, int n,
-                                              int step = 1) {
+__device__ __forceinline__ void store_bf16x32(__nv_bfloat16* dst, const float* v, int n) {
+  // n = 16 or 32 values to a 16-byte aligned destination
 #pragma unroll
   for (int q = 0; q < 4; q++) {
     if (q * 8 >= n) break;
@@ -90,16 +88,15 @@ __device__ __forceinline__ void store_bf16x32(__nv_bfloat16* dst, const float* v
     __nv_bfloat162* h = reinterpret_cast<__nv_bfloat162*>(&u);
 #pragma unroll
     for (int k = 0; k < 4; k++) h[k] = __floats2bfloat162_rn(v[8 * q + 2 * k], v[8 * q + 2 * k + 1]);
-    reinterpret_cast<uint4*>(dst)[q * step] = u;
+    reinterpret_cast<uint4*>(dst)[q] = u;
   }
 }
 
-__device__ __forceinline__ void load_bf16x32(const __nv_bfloat16* src, float* v, int n,
-                                             int step = 1) {
+__device__ __forceinline__ void load_bf16x32(const __nv_bfloat16* src, float* v, int n) {
 #pragma unroll
   for (int q = 0; q < 4; q++) {
     if (q * 8 >= n) break;
-    uint4 u = reinterpret_cast<const uint4*>(src)[q * step];
+    uint4 u = reinterpret_cast<const uint4*>(src)[q];
     const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&u);
 #pragma unroll
     for (int k = 0; k < 4; k++) {
@@ -144,19 +141,27 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map
       : "memory");
 }
 
-// 3-D tensor store shared -> [x, y, z] (rows past the tensor are not written).
-__device__ __forceinline__ void tma_store_3d(const CUtensorMap* map, int x, int y, int z,
-                                             uint32_t src) {
-  asm volatile(
-      "cp.async.bulk.tensor.3d.global.shared::cta.bulk_group [%0, {%1, %2, %3}], [%4];" ::"l"(map),
-      "r"(x), "r"(y), "r"(z), "r"(src)
-      : "memory");
+// 2-D tensor store shared -> [x, y] (rows past the tensor are not written);
+// bulk_wait_read() waits until the issued stores have read shared memory.
+__device__ __forceinline__ void tma_store_2d(const CUtensorMap* map, int x, int y, uint32_t src) {
+  asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%1, %2}], [%3];" ::"l"(
+                   map),
+               "r"(x), "r"(y), "r"(src)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_wait_read() {
   asm volatile("cp.async.bulk.commit_group;" ::: "memory");
   asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
 }
 
-// tmap / omap: the target and the output of EPI_RECON as [64 groups][P][8]
-// maps with 128-row x 64-group boxes (unused by the other epilogues).
+// The 16-byte piece `chunk` (0-7) of row r in a 128-byte swizzled box: the
+// pieces of each row are permuted by XOR with r % 8.
+__device__ __forceinline__ uint32_t sw128_piece(int r, int chunk) {
+  return (uint32_t)(r * 128 + ((chunk ^ (r & 7)) << 4));
+}
+
+// tmap / omap: the target and the output of EPI_RECON as 128-byte swizzle
+// maps with 64-column x 128-row boxes (unused by the other epilogues).
 template <int NT, int KC>
 __global__ void __launch_bounds__(kLayerThreads, 2) layer_kernel(const __grid_constant__ LayerArgs a,
                                                       const __grid_constant__ CUtensorMap amap,
@@ -405,23 +410,40 @@ __global__ void __launch_bounds__(kLayerThreads, 2) layer_kernel(const __grid_co
       }
     } else if (a.epi == EPI_RECON) {
       if constexpr (NT == 512 && 2 * L::STAGE >= 8192 + 128 * 512 * 2) {
-        // The target tile [128 x 512] lands in the free stages in one TMA
-        // load, as 64 column groups of 128 rows x 16 B (row r of group g at
-        // g * 2048 + r * 16: the rows of a warp are consecutive 16-byte
-        // pieces); dL/dy replaces it in place and leaves in one TMA store.
+        // The target tile [128 x 512] lands in the free stages by eight TMA
+        // loads of 64 columns (16 KB each, rows of 128 B with the 128-byte
+        // swizzle, so the 16-byte pieces of the rows a warp reads together
+        // fall in distinct banks); dL/dy replaces it in place and leaves by
+        // eight TMA stores through the same swizzle.
         const uint32_t sx = tc::smem_addr(sm) + 8192;
         if (tid == 0) {
           tc::mbar_expect_tx(xbar, 128 * 512 * 2);
-          tma_load_3d(sx, &tmap, 0, (int)row0, 0, xbar);
+#pragma unroll
+          for (int b = 0; b < 8; b++) tma_load_2d(sx + b * 16384, &tmap, 64 * b, (int)row0, xbar);
         }
         if (__syncthreads_and(tc::mbar_wait(xbar, 0, kSpinLimit))) {
-          __nv_bfloat16* xr = reinterpret_cast<__nv_bfloat16*>(sm + 8192 + r * 16);
+          uint8_t* xt = sm + 8192;
+          // columns c0 .. c0 + 31 of row r, as 32 floats
+          auto load_x = [&](int c0, float* x) {
+#pragma unroll
+            for (int q4 = 0; q4 < 4; q4++) {
+              const uint4 u = *reinterpret_cast<const uint4*>(
+                  xt + (c0 >> 6) * 16384 + sw128_piece(r, ((c0 & 63) >> 3) + q4));
+              const __nv_bfloat162* hh = reinterpret_cast<const __nv_bfloat162*>(&u);
+#pragma unroll
+              for (int k = 0; k < 4; k++) {
+                const float2 f = __bfloat1622float2(hh[k]);
+                x[8 * q4 + 2 * k] = f.x;
+                x[8 * q4 + 2 * k + 1] = f.y;
+              }
+            }
+          };
           // pass 1: row statistics of y against x = target, per half
           float sdd = 0.f, syx = 0.f, syy = 0.f, sxx = 0.f;
           for (int c0 = cbeg; c0 < cend; c0 += 32) {
             float v[32], x[32], bb[32];
             tc::tmem_ld32(tb + c0, v);
-            load_bf16x32(xr + c0 * 128, x, 32, 128);
+            load_x(c0, x);
             bias_of(c0, bb);
 #pragma unroll
             for (int i = 0; i < 32; i++) {
@@ -451,18 +473,31 @@ __global__ void __launch_bounds__(kLayerThreads, 2) layer_kernel(const __grid_co
           for (int c0 = cbeg; c0 < cend; c0 += 32) {
             float v[32], x[32], bb[32];
             tc::tmem_ld32(tb + c0, v);
-            load_bf16x32(xr + c0 * 128, x, 32, 128);
+            load_x(c0, x);
             bias_of(c0, bb);
 #pragma unroll
             for (int i = 0; i < 32; i++) {
               const float y = v[i] + bb[i];
               v[i] = fmaf(c2, y - x[i], fmaf(cy, y, -cx * x[i]));
             }
-            store_bf16x32(xr + c0 * 128, v, 32, 128);
+#pragma unroll
+            for (int q4 = 0; q4 < 4; q4++) {
+              uint4 u;
+              __nv_bfloat162* hh = reinterpret_cast<__nv_bfloat162*>(&u);
+#pragma unroll
+              for (int k = 0; k < 4; k++)
+                hh[k] = __floats2bfloat162_rn(v[8 * q4 + 2 * k], v[8 * q4 + 2 * k + 1]);
+              *reinterpret_cast<uint4*>(xt + (c0 >> 6) * 16384 +
+                                        sw128_piece(r, ((c0 & 63) >> 3) + q4)) = u;
+            }
           }
           tc::fence_async_smem();
           __syncthreads();
-          if (tid == 0) tma_store_3d(&omap, 0, (int)row0, 0, sx);
+          if (tid == 0) {
+#pragma unroll
+            for (int b = 0; b < 8; b++) tma_store_2d(&omap, 64 * b, (int)row0, sx + b * 16384);
+            bulk_wait_read();
+          }
         } else if (tid == 0) {
           report_timeout();
         }
@@ -788,8 +823,8 @@ static lgs_status launch_layer_t(const LayerArgs& a, cudaStream_t s) {
       set_error("the reconstruction loss needs 512-wide rows and K >= 64");
       return LGS_ERR_INVALID;
     }
-    if (!make_kmajor_map(&tmap, a.target, a.P, 512, 128, 64) ||
-        !make_kmajor_map(&omap, a.out_bf, a.P, 512, 128, 64))
+    if (!make_sw128_map(&tmap, a.target, a.P, 512, 128) ||
+        !make_sw128_map(&omap, a.out_bf, a.P, 512, 128))
       return LGS_ERR_CUDA;
   }
   dim3 grid((unsigned)((a.P + 127) / 128), a.N / NT);
@@ -1035,6 +1070,10 @@ extern "C" lgs_status ae_train_step(lgs_ae_state* st_, const uint16_t* x, const 
     LGS_CHECK_ARG(st_->W[l] && st_->b[l] && st_->mW[l] && st_->vW[l] && st_->mb[l] && st_->vb[l] &&
                       st_->gW[l] && st_->gb[l] && st_->Wbf[l] && st_->Wtbf[l],
                   "null state pointer");
+  for (int l = 0; l <= last; l++)  // float4 atomics into gW, TMA loads of the BF16 copies
+    LGS_CHECK_ARG(aligned(st_->gW[l], 16) && aligned(st_->gb[l], 16) &&
+                      aligned(st_->Wbf[l], 16) && aligned(st_->Wtbf[l], 16),
+                  "misaligned state pointer");
   cudaStream_t s = as_stream(stream);
   Carver c(workspace);
   TrainBufs B;
@@ -1042,10 +1081,24 @@ extern "C" lgs_status ae_train_step(lgs_ae_state* st_, const uint16_t* x, const 
   auto W = [&](int l) { return st_->Wbf[l]; };
   auto Wt = [&](int l) { return st_->Wtbf[l]; };
   lgs_status st;
-  for (int l = 0; l <= last; l++) {
-    const int K = kAeWidths[l], N = kAeWidths[l + 1];
-    LGS_CHECK_CUDA(cudaMemsetAsync(st_->gW[l], 0, sizeof(float) * N * K, s));
-    LGS_CHECK_CUDA(cudaMemsetAsync(st_->gb[l], 0, sizeof(float) * N, s));
+  {  // zero the gradients, one memset per run of adjacent buffers
+    char* run = nullptr;
+    size_t len = 0;
+    for (int l = 0; l <= last; l++) {
+      const int K = kAeWidths[l], N = kAeWidths[l + 1];
+      char* seg[2] = {reinterpret_cast<char*>(st_->gW[l]), reinterpret_cast<char*>(st_->gb[l])};
+      const size_t bytes[2] = {sizeof(float) * N * K, sizeof(float) * N};
+      for (int i = 0; i < 2; i++) {
+        if (run && run + len == seg[i]) {
+          len += bytes[i];
+          continue;
+        }
+        if (run) LGS_CHECK_CUDA(cudaMemsetAsync(run, 0, len, s));
+        run = seg[i];
+        len = bytes[i];
+      }
+    }
+    LGS_CHECK_CUDA(cudaMemsetAsync(run, 0, len, s));
   }
   // forward, keeping every layer's input and pre-activation
   const void* in = x;

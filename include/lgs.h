@@ -450,7 +450,8 @@ lgs_status gs_query_relevance(const void* feats, int feat_dtype, int64_t M, int 
  * set when a wait gives up (0 = none; bits 0-3 the autoencoder layer
  * kernels -- 1: a wait gave up, 4: shared memory not on the 1 KB boundary
  * the 128-byte swizzle needs, so the kernel returned without work -- bits
- * 4-7 the fused decoder, 8-11 the sort, 12-15 the fused encoder).
+ * 4-7 the fused decoder, 8-11 the sort, 12-15 the fused encoder, whose
+ * bit 15 again means misaligned shared memory).
  * Synchronises the device. */
 lgs_status lgs_device_error(int* code);
 

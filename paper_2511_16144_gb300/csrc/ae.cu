@@ -812,8 +812,8 @@ static lgs_status launch_layer_t(const LayerArgs& a, cudaStream_t s) {
   std::memset(&tmap, 0, sizeof(tmap));
   std::memset(&omap, 0, sizeof(omap));
   if (!a.a_f32) {  // A [P, K] and W [N, K] as K-major chunks of KC columns
-    const bool made = KC == 64 ? make_sw128_map(&amap, a.A, a.P, a.K, 128) &&
-                                     make_sw128_map(&bmap, a.W, a.N, a.K, L::BROWS)
+    const bool made = KC == 64 ? make_swizzled_map(&amap, a.A, a.P, a.K, 64, 128) &&
+                                     make_swizzled_map(&bmap, a.W, a.N, a.K, 64, L::BROWS)
                                : make_kmajor_map(&amap, a.A, a.P, a.K, 128, KC / 8) &&
                                      make_kmajor_map(&bmap, a.W, a.N, a.K, L::BROWS, KC / 8);
     if (!made) return LGS_ERR_CUDA;
@@ -823,8 +823,8 @@ static lgs_status launch_layer_t(const LayerArgs& a, cudaStream_t s) {
       set_error("the reconstruction loss needs 512-wide rows and K >= 64");
       return LGS_ERR_INVALID;
     }
-    if (!make_sw128_map(&tmap, a.target, a.P, 512, 128) ||
-        !make_sw128_map(&omap, a.out_bf, a.P, 512, 128))
+    if (!make_swizzled_map(&tmap, a.target, a.P, 512, 64, 128) ||
+        !make_swizzled_map(&omap, a.out_bf, a.P, 512, 64, 128))
       return LGS_ERR_CUDA;
   }
   dim3 grid((unsigned)((a.P + 127) / 128), a.N / NT);
@@ -857,9 +857,9 @@ static lgs_status launch_dw_t(const __nv_bfloat16* G, const __nv_bfloat16* X, Dw
   // 64 pixels x 16 bytes
   const int ga = std::min(16, a.N / 8), gb = KT / 8;
   CUtensorMap gmap, xmap;
-  const bool made = (GSW ? make_sw128_map(&gmap, G, a.P, a.N, L::PC)
+  const bool made = (GSW ? make_swizzled_map(&gmap, G, a.P, a.N, 64, L::PC)
                          : make_kmajor_map(&gmap, G, a.P, a.N, L::PC, ga)) &&
-                    (KT >= 64 ? make_sw128_map(&xmap, X, a.P, a.K, L::PC)
+                    (KT >= 64 ? make_swizzled_map(&xmap, X, a.P, a.K, 64, L::PC)
                               : make_kmajor_map(&xmap, X, a.P, a.K, L::PC, gb));
   if (!made) return LGS_ERR_CUDA;
   a.a_tx = ga * L::PC * 16;  // both layouts: min(128, N) features x 64 pixels

@@ -5,10 +5,9 @@
 //
 // Per tile, on the tensor cores (BF16 operands, FP32 accumulators in TMEM):
 //   L0  x [128 x 512] W0^T in 16 K-steps of 32 columns: each ring stage holds
-//       the x chunk (one 3-D TMA load that lands the row-major rows directly
-//       in the K-major core-matrix layout: 8-column groups of 128 rows x 16
-//       bytes) and the matching 256 x 32 slice of W0 (a bulk copy of a
-//       pre-packed unit);
+//       the x chunk (one 2-D TMA load in the 64-byte swizzle layout: 128 rows
+//       of 64 bytes, each byte fetched once) and the matching 256 x 32 slice
+//       of W0 (a bulk copy of a pre-packed unit);
 //   L1..L3  the hidden activations stay in shared memory (BF16) and only
 //       the weight units stream through the ring.
 // Consecutive tiles of a CTA alternate TMEM halves (columns 0-255 / 256-511),
@@ -96,13 +95,13 @@ struct EncArgs {
 
 __device__ unsigned g_enc_error;
 
-// 3-D tensor load [x, y, z] -> shared, completing on an mbarrier.
-__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map, int x, int y,
-                                            int z, uint64_t* bar) {
+// 2-D tensor load [x, y] -> shared, completing on an mbarrier.
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y,
+                                            uint64_t* bar) {
   asm volatile(
-      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes"
-      " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(dst),
-      "l"(map), "r"(x), "r"(y), "r"(z), "r"(tc::smem_addr(bar))
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3}], [%4];" ::"r"(dst),
+      "l"(map), "r"(x), "r"(y), "r"(tc::smem_addr(bar))
       : "memory");
 }
 
@@ -153,6 +152,10 @@ encode_fused_kernel(const __grid_constant__ EncArgs a, const __grid_constant__ C
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int64_t ntiles = (a.P + 127) / 128;
   const int nloc = blockIdx.x < ntiles ? (int)((ntiles - 1 - blockIdx.x) / gridDim.x + 1) : 0;
+  if (tc::smem_addr(sm) & 1023u) {  // the swizzled x chunks need 1 KB-aligned stages
+    if (tid == 0) atomicOr(&g_enc_error, 8u);
+    return;
+  }
   for (int i = tid; i < 464; i += kThreads)
     sb[i] = i < 256 ? a.b[0][i] : i < 384 ? a.b[1][i - 256] : i < 448 ? a.b[2][i - 384] : a.b[3][i - 448];
   if (warp == 0) tc::tmem_alloc(tslot, 512);
@@ -192,7 +195,7 @@ encode_fused_kernel(const __grid_constant__ EncArgs a, const __grid_constant__ C
         tc::mbar_expect_tx(&full[s], a.bytes[unit] + (tl >= 0 ? kXBytes : 0u));
         if (tl >= 0) {
           const int64_t t = blockIdx.x + (int64_t)tl * gridDim.x;
-          tma_load_3d(st, &xmap, 0, (int)(t * 128), 4 * unit, &full[s]);
+          tma_load_2d(st, &xmap, 32 * unit, (int)(t * 128), &full[s]);
         }
         tc::bulk_g2s(st + kXBytes, a.pack + a.off[unit], a.bytes[unit], &full[s]);
       }
@@ -203,7 +206,7 @@ encode_fused_kernel(const __grid_constant__ EncArgs a, const __grid_constant__ C
     uint32_t u = 0, nL0 = 0, nS = 0;
     bool ok = true;
     const uint64_t dbase = tc::sdesc_base(sbase);            // K-adjacent core matrices 128 B apart
-    const uint64_t xbase = tc::sdesc(sbase, 2048, 0);         // ... 2048 B apart (TMA-staged x)
+    const uint64_t xbase = tc::sdesc_sw64(sbase);             // TMA-staged x: 64-byte swizzle
     auto wait_on = [&](uint64_t* bar, uint32_t& n) {
       ok = ok && __all_sync(0xffffffffu, tc::mbar_wait(bar, n & 1, kLimit));
       n++;
@@ -230,12 +233,13 @@ encode_fused_kernel(const __grid_constant__ EncArgs a, const __grid_constant__ C
         const uint32_t s = take();
         if (!ok) break;
         const uint32_t st = SM_ST + s * kStageBytes;
-        const uint64_t ad = xbase + tc::sdesc_off(st, 128);
+        const uint64_t ad = xbase + tc::sdesc_off(st, 0);
         const uint64_t bd = dbase + tc::sdesc_off(st + kXBytes, 32 * 16);
         if (tc::elect_one()) {
+          // K-step of 16 columns: 32 bytes along the x rows, 2 core matrices of W0
 #pragma unroll
           for (int j = 0; j < 2; j++)
-            tc::mma_bf16(tmem + hb, ad + 256 * j, bd + 16 * j, tc::idesc_bf16(128, 256),
+            tc::mma_bf16(tmem + hb, ad + 2 * j, bd + 16 * j, tc::idesc_bf16(128, 256),
                          (ks | j) != 0);
         }
         __syncwarp();
@@ -437,21 +441,24 @@ bool make_kmajor_map(CUtensorMap* map, const void* base, int64_t rows, int K, in
   return true;
 }
 
-bool make_sw128_map(CUtensorMap* map, const void* base, int64_t rows, int K, int box_rows) {
+bool make_swizzled_map(CUtensorMap* map, const void* base, int64_t rows, int K, int box_cols,
+                       int box_rows) {
   auto encode = tensor_map_encoder();
-  if (!encode) {
-    set_error("cuTensorMapEncodeTiled is unavailable");
+  if (!encode || (box_cols != 64 && box_cols != 32)) {
+    set_error(encode ? "swizzled maps take 32- or 64-column boxes"
+                     : "cuTensorMapEncodeTiled is unavailable");
     return false;
   }
   const cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)rows};
   const cuuint64_t strides[1] = {(cuuint64_t)K * 2};
-  const cuuint32_t box[2] = {64, (cuuint32_t)box_rows}, es[2] = {1, 1};
-  const CUresult cr =
-      encode(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box,
-             es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
-             CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  const cuuint32_t box[2] = {(cuuint32_t)box_cols, (cuuint32_t)box_rows}, es[2] = {1, 1};
+  const CUresult cr = encode(
+      map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, es,
+      CU_TENSOR_MAP_INTERLEAVE_NONE,
+      box_cols == 64 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
+      CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (cr != CUDA_SUCCESS) {
-    set_error("cuTensorMapEncodeTiled refused a 128-byte swizzle map");
+    set_error("cuTensorMapEncodeTiled refused a swizzled map");
     return false;
   }
   return true;
@@ -460,11 +467,10 @@ bool make_sw128_map(CUtensorMap* map, const void* base, int64_t rows, int K, int
 lgs_status launch_encode_fused(const lgs_ae_weights* w, const uint16_t* x, int64_t P, float* z,
                                void* pack, cudaStream_t s) {
   const EncPlan& pl = enc_plan();
-  // x [P, 512] bf16 as [64 column groups][P rows][8 columns]: a box of
-  // 128 rows x 4 groups is one 32-column chunk in the K-major layout with
-  // K-adjacent groups 2048 bytes apart
+  // x [P, 512] bf16 in 32-column x 128-row boxes with the 64-byte swizzle:
+  // one box is one K-chunk of a tile, rows of 64 bytes in 512-byte atoms
   CUtensorMap xmap;
-  if (!make_kmajor_map(&xmap, x, P, 512, 128, 4)) return LGS_ERR_CUDA;
+  if (!make_swizzled_map(&xmap, x, P, 512, 32, 128)) return LGS_ERR_CUDA;
   EncPackArgs pa;
   for (int m = 0; m < 4; m++) pa.mats[m] = reinterpret_cast<const __nv_bfloat16*>(w->W[m]);
   for (int i = 0; i < kUnits; i++) {

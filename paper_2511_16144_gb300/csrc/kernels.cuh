@@ -44,12 +44,14 @@ int sm_count();
 // False (with the error string set) when the driver refuses the map.
 bool make_kmajor_map(CUtensorMap* map, const void* base, int64_t rows, int K, int box_rows,
                      int box_groups);
-// A 2-D TMA tensor map of a row-major bf16 matrix [rows, K] (K a multiple
-// of 64) with 64-column x box_rows boxes and the 128-byte swizzle: a box
-// lands as box_rows rows of 128 bytes, the layout sdesc_sw128 describes
-// (rows past the end read as zero).  The shared destination must be 1 KB
+// A 2-D TMA tensor map of a row-major bf16 matrix [rows, K] with box_cols x
+// box_rows boxes in a swizzled layout: box_cols = 64 lands box_rows rows of
+// 128 bytes with the 128-byte swizzle (the layout sdesc_sw128 describes),
+// box_cols = 32 rows of 64 bytes with the 64-byte swizzle (sdesc_sw64).
+// Rows past the end read as zero; the shared destination must be 1 KB
 // aligned.  False (with the error string set) when the driver refuses it.
-bool make_sw128_map(CUtensorMap* map, const void* base, int64_t rows, int K, int box_rows);
+bool make_swizzled_map(CUtensorMap* map, const void* base, int64_t rows, int K, int box_cols,
+                       int box_rows);
 // Stable LSD radix sort of n (key, value) pairs on key bits [0, nbits)
 // (nbits <= 32), one onesweep kernel per 8 bits.  `scratch` holds
 // sort_pairs_scratch(n) bytes (256-byte aligned) and is cleared here.

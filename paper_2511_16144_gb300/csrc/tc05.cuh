@@ -45,6 +45,13 @@ __device__ __forceinline__ uint64_t sdesc_sw128(uint32_t saddr) {
   return sdesc(saddr, 16, 1024) | ((uint64_t)2 << 61);
 }
 
+// The same with the 64-byte swizzle: rows of 32 bf16 (64 B) in 8-row atoms
+// of 512 B (SBO), the 16-byte chunks of row r permuted by XOR with (r / 2) %
+// 4; the K-step of 16 elements is again a 32-byte advance of the start.
+__device__ __forceinline__ uint64_t sdesc_sw64(uint32_t saddr) {
+  return sdesc(saddr, 16, 512) | ((uint64_t)4 << 61);
+}
+
 // Descriptors as offsets from one base: sdesc_base(b) + sdesc_off(o, sbo)
 // equals sdesc(b + o, 128, sbo) whenever b and o are multiples of 16 bytes,
 // because the 14-bit address field never carries (shared addresses stay below

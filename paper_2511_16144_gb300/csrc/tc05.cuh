@@ -2,12 +2,15 @@
 // autoencoder GEMMs: tcgen05 MMA with TMEM accumulators, mbarrier-tracked
 // completion, TMEM loads for the epilogue, and cp.async operand staging.
 //
-// Operands live in shared memory in the canonical K-major, no-swizzle layout:
-// 8x8 "core matrices" of bf16 (8 rows x 16 bytes, 128 contiguous bytes).
-// For a tile of R rows and a K-chunk of KC columns the core matrix holding
-// rows 8g..8g+7 and columns 8c..8c+7 sits at byte (g * (KC/8) + c) * 128, so
-// K-adjacent core matrices are 128 B apart (LBO) and row groups
-// 16 * KC bytes apart (SBO).
+// Operands written by threads (activations, packed weight units) live in
+// shared memory in the canonical K-major, no-swizzle layout: 8x8 "core
+// matrices" of bf16 (8 rows x 16 bytes, 128 contiguous bytes).  For a tile
+// of R rows and a K-chunk of KC columns the core matrix holding rows
+// 8g..8g+7 and columns 8c..8c+7 sits at byte (g * (KC/8) + c) * 128, so
+// K-adjacent core matrices are 128 B apart (LBO) and row groups 16 * KC bytes
+// apart (SBO).  Operands that TMA loads straight from row-major global
+// matrices use the 128- or 64-byte swizzle layouts (sdesc_sw128, sdesc_sw64),
+// whose boxes move each byte once.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -26,7 +29,8 @@ __device__ __forceinline__ uint32_t core_offset(int r, int c, int kc_cols) {
   return (uint32_t)(((r >> 3) * (kc_cols >> 3) + c) * 128 + (r & 7) * 16);
 }
 
-// Shared-memory matrix descriptor (K-major, no swizzle, sm_100 version 1).
+// Shared-memory matrix descriptor (no swizzle, sm_100 version 1); OR in a
+// layout type at bits 61-63 for the swizzled layouts (2: 128-byte, 4: 64-byte).
 __device__ __forceinline__ uint64_t sdesc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
   uint64_t d = 0;
   d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);

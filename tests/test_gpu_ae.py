@@ -156,6 +156,29 @@ def test_train_step_gradients_and_update(lgs, mode):
     assert lgs.lgs_device_error() == 0
 
 
+def test_train_step_full_batch(lgs):
+    """The batch the benchmark times (65,536 pixels, RECON): every layer's
+    weight and bias gradients against the FP64 oracle, with the weight
+    gradients split over all SMs as in the timed step."""
+    from oracle import ae
+    from paper_2511_16144_gb300.ae import AutoEncoder
+    enc, dec = synth.ae_init(seed=3007)
+    model = AutoEncoder(enc, dec)
+    x = embeddings(256, 256, 11)
+    assert x.shape[0] == 65536
+    loss = model.train_step(torch.from_numpy(x).cuda().bfloat16(), None, mode=lgs.AE_RECON,
+                            lr=1e-3)
+    torch.cuda.synchronize()
+    re, rd = rounded(enc), rounded(dec)
+    l_ref, g_ref = ae.train_step(re, rd, ae.new_state(re, rd), bf16_round(x), None, "recon",
+                                 lr=0.0)
+    assert abs(loss.item() - l_ref) <= 1e-2 * abs(l_ref)
+    for l in range(8):
+        assert rel_err(model.gW[l].cpu().numpy(), g_ref[l][0]) < 3 * REL, l
+        assert rel_err(model.gb[l].cpu().numpy(), g_ref[l][1]) < 3 * REL, l
+    assert lgs.lgs_device_error() == 0
+
+
 def test_training_reduces_reconstruction_loss(lgs):
     """200 Adam steps on 64k-pixel batches of per-frame embedding maps."""
     from paper_2511_16144_gb300.ae import AutoEncoder

@@ -121,39 +121,6 @@ struct LayerSmem {
   static constexpr int BROWS = NT > 256 ? 256 : NT;  // weight rows per TMA box
 };
 
-// 3-D tensor load [x, y, z] -> shared, completing on an mbarrier.
-__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map, int x, int y,
-                                            int z, uint64_t* bar) {
-  asm volatile(
-      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes"
-      " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(dst),
-      "l"(map), "r"(x), "r"(y), "r"(z), "r"(tc::smem_addr(bar))
-      : "memory");
-}
-
-// 2-D tensor load [x, y] -> shared, completing on an mbarrier.
-__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y,
-                                            uint64_t* bar) {
-  asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
-      " [%0], [%1, {%2, %3}], [%4];" ::"r"(dst),
-      "l"(map), "r"(x), "r"(y), "r"(tc::smem_addr(bar))
-      : "memory");
-}
-
-// 2-D tensor store shared -> [x, y] (rows past the tensor are not written);
-// bulk_wait_read() waits until the issued stores have read shared memory.
-__device__ __forceinline__ void tma_store_2d(const CUtensorMap* map, int x, int y, uint32_t src) {
-  asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%1, %2}], [%3];" ::"l"(
-                   map),
-               "r"(x), "r"(y), "r"(src)
-               : "memory");
-}
-__device__ __forceinline__ void bulk_wait_read() {
-  asm volatile("cp.async.bulk.commit_group;" ::: "memory");
-  asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
-}
-
 // The 16-byte piece `chunk` (0-7) of row r in a 128-byte swizzled box: the
 // pieces of each row are permuted by XOR with r % 8.
 __device__ __forceinline__ uint32_t sw128_piece(int r, int chunk) {
@@ -217,16 +184,16 @@ __global__ void __launch_bounds__(kLayerThreads, 2) layer_kernel(const __grid_co
         const uint32_t st = sbase + s * L::STAGE;
         tc::mbar_expect_tx(&full[s], L::STAGE);
         if constexpr (KC == 64) {
-          tma_load_2d(st, &amap, kc * 64, (int)row0, &full[s]);
+          tc::tma_load_2d(st, &amap, kc * 64, (int)row0, &full[s]);
 #pragma unroll
           for (int h = 0; h < NT / L::BROWS; h++)
-            tma_load_2d(st + L::A_BYTES + h * L::BROWS * 128, &bmap, kc * 64, n0 + h * L::BROWS,
+            tc::tma_load_2d(st + L::A_BYTES + h * L::BROWS * 128, &bmap, kc * 64, n0 + h * L::BROWS,
                         &full[s]);
         } else {
-          tma_load_3d(st, &amap, 0, (int)row0, kc * (KC / 8), &full[s]);
+          tc::tma_load_3d(st, &amap, 0, (int)row0, kc * (KC / 8), &full[s]);
 #pragma unroll
           for (int h = 0; h < NT / L::BROWS; h++)
-            tma_load_3d(st + L::A_BYTES + h * L::BROWS * KC * 2, &bmap, 0, n0 + h * L::BROWS,
+            tc::tma_load_3d(st + L::A_BYTES + h * L::BROWS * KC * 2, &bmap, 0, n0 + h * L::BROWS,
                         kc * (KC / 8), &full[s]);
         }
       }
@@ -419,7 +386,7 @@ __global__ void __launch_bounds__(kLayerThreads, 2) layer_kernel(const __grid_co
         if (tid == 0) {
           tc::mbar_expect_tx(xbar, 128 * 512 * 2);
 #pragma unroll
-          for (int b = 0; b < 8; b++) tma_load_2d(sx + b * 16384, &tmap, 64 * b, (int)row0, xbar);
+          for (int b = 0; b < 8; b++) tc::tma_load_2d(sx + b * 16384, &tmap, 64 * b, (int)row0, xbar);
         }
         if (__syncthreads_and(tc::mbar_wait(xbar, 0, kSpinLimit))) {
           uint8_t* xt = sm + 8192;
@@ -495,8 +462,8 @@ __global__ void __launch_bounds__(kLayerThreads, 2) layer_kernel(const __grid_co
           __syncthreads();
           if (tid == 0) {
 #pragma unroll
-            for (int b = 0; b < 8; b++) tma_store_2d(&omap, 64 * b, (int)row0, sx + b * 16384);
-            bulk_wait_read();
+            for (int b = 0; b < 8; b++) tc::tma_store_2d(&omap, 64 * b, (int)row0, sx + b * 16384);
+            tc::bulk_wait_read();
           }
         } else if (tid == 0) {
           report_timeout();
@@ -676,16 +643,16 @@ __global__ void __launch_bounds__(128, 1) dw_kernel(const __grid_constant__ DwAr
       tc::mbar_expect_tx(&full[s], (uint32_t)(a.a_tx + a.b_tx));
       if constexpr (GSW) {
         for (int b = 0; b < 2 && n0 + 64 * b < a.N; b++)
-          tma_load_2d(st + b * 8192, &gmap, n0 + 64 * b, p0, &full[s]);
+          tc::tma_load_2d(st + b * 8192, &gmap, n0 + 64 * b, p0, &full[s]);
       } else {
-        tma_load_3d(st, &gmap, 0, p0, n0 / 8, &full[s]);
+        tc::tma_load_3d(st, &gmap, 0, p0, n0 / 8, &full[s]);
       }
       if constexpr (XSW) {
 #pragma unroll
         for (int b = 0; b < KT / 64; b++)
-          tma_load_2d(st + L::A_BYTES + b * 8192, &xmap, k0 + 64 * b, p0, &full[s]);
+          tc::tma_load_2d(st + L::A_BYTES + b * 8192, &xmap, k0 + 64 * b, p0, &full[s]);
       } else {
-        tma_load_3d(st + L::A_BYTES, &xmap, 0, p0, k0 / 8, &full[s]);
+        tc::tma_load_3d(st + L::A_BYTES, &xmap, 0, p0, k0 / 8, &full[s]);
       }
     }
   } else if (tid == 32) {

@@ -95,16 +95,6 @@ struct EncArgs {
 
 __device__ unsigned g_enc_error;
 
-// 2-D tensor load [x, y] -> shared, completing on an mbarrier.
-__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y,
-                                            uint64_t* bar) {
-  asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
-      " [%0], [%1, {%2, %3}], [%4];" ::"r"(dst),
-      "l"(map), "r"(x), "r"(y), "r"(tc::smem_addr(bar))
-      : "memory");
-}
-
 // The ring's unit order: L0 of local tiles 0 and 1, then per local tile k:
 // L1, L2, L3 of tile k (6 units) and, while tile k + 2 exists, its L0 (16).
 // Position j of that order as (unit, local tile whose x it needs, or -1).
@@ -195,7 +185,7 @@ encode_fused_kernel(const __grid_constant__ EncArgs a, const __grid_constant__ C
         tc::mbar_expect_tx(&full[s], a.bytes[unit] + (tl >= 0 ? kXBytes : 0u));
         if (tl >= 0) {
           const int64_t t = blockIdx.x + (int64_t)tl * gridDim.x;
-          tma_load_2d(st, &xmap, 32 * unit, (int)(t * 128), &full[s]);
+          tc::tma_load_2d(st, &xmap, 32 * unit, (int)(t * 128), &full[s]);
         }
         tc::bulk_g2s(st + kXBytes, a.pack + a.off[unit], a.bytes[unit], &full[s]);
       }

@@ -212,7 +212,7 @@ def run_gpu(args, rank, world):
     t0 = time.time()
     for _ in range(args.ae_steps):
         idx = torch.randint(0, train.shape[0], (65536,), device=dev, generator=gen)
-        ae_losses.append(model.train_step(train[idx].contiguous(), lr=3e-3))
+        ae_losses.append(model.train_step(train[idx].contiguous(), lr=5e-3))
     torch.cuda.synchronize()
     ae_train_s = time.time() - t0
     ae_losses = [float(l.item()) for l in ae_losses] or [float("nan")]

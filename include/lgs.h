@@ -17,8 +17,14 @@
  * - Every call only enqueues work on `stream` (a cudaStream_t; NULL = the
  *   legacy default stream) and returns without synchronising.  Argument
  *   errors that the host can see (null or misaligned pointers, bad sizes)
- *   return LGS_ERR_INVALID before anything is enqueued; launch failures
- *   return LGS_ERR_CUDA.  lgs_last_error() gives the message (thread-local).
+ *   return LGS_ERR_INVALID before anything is enqueued (LGS_ERR_NONFINITE
+ *   for a non-finite camera value); launch failures return LGS_ERR_CUDA.
+ *   lgs_last_error() gives the message (thread-local).
+ * - Errors that only the device sees (an instance buffer that is too small,
+ *   a non-finite Gaussian parameter, a bounded wait that gave up) are
+ *   recorded on the device and reported by lgs_sync_status(), which
+ *   synchronises the stream; the enqueueing call has already returned
+ *   LGS_OK.
  * - Arrays are dense, row-major, structure-of-arrays; images are [C,H,W,ch]
  *   (camera, row, column, channel).  Pointers read or written with 16-byte
  *   vector accesses must be 16-byte aligned (stated per argument).
@@ -40,9 +46,11 @@ extern "C" {
 
 typedef enum {
   LGS_OK = 0,
-  LGS_ERR_INVALID = 1,   /* bad argument (host-detected) */
-  LGS_ERR_CAPACITY = 2,  /* instance buffer too small (see gs_bin_sort) */
-  LGS_ERR_CUDA = 5       /* a CUDA launch or runtime call failed */
+  LGS_ERR_INVALID = 1,    /* bad argument (host-detected) */
+  LGS_ERR_CAPACITY = 2,   /* instance buffer too small (gs_bin_sort; device-detected) */
+  LGS_ERR_NONFINITE = 3,  /* NaN / inf in a camera (host) or a Gaussian (device) */
+  LGS_ERR_TIMEOUT = 4,    /* a bounded device wait gave up (device-detected) */
+  LGS_ERR_CUDA = 5        /* a CUDA launch or runtime call failed */
 } lgs_status;
 
 typedef enum { LGS_F32 = 0, LGS_BF16 = 1 } lgs_dtype;
@@ -81,6 +89,41 @@ int64_t lgs_graph_kernel_nodes(void* graph);
 lgs_status lgs_zero(void* dev, size_t bytes, void* stream);
 
 /* ------------------------------------------------------------------------
+ * lgs_sync_status -- the deferred status of the device-side work.
+ *
+ * The paper states the problem (Sec. III-B.1: project, bin and composite
+ * the map; Sec. III-B.3: optimise it by gradients) but no error contract;
+ * this is the library's.  Synchronises `stream` (NULL = the legacy default
+ * stream), then reports one error that kernels on the current device
+ * recorded since it was last reported, and clears it:
+ *   LGS_ERR_NONFINITE  gs_project met a NaN or infinite mean, quaternion,
+ *                      log-scale or opacity logit (those Gaussians are culled
+ *                      in every camera); *detail = the smallest such index;
+ *   LGS_ERR_CAPACITY   gs_bin_sort needed more instances than its capacity
+ *                      (nothing was sorted, every range is (0, 0));
+ *                      *detail = the largest K required;
+ *   LGS_ERR_TIMEOUT    a bounded wait gave up and its kernel returned
+ *                      (results of that call are undefined but every
+ *                      access stayed in bounds); *detail = the wait-site bit
+ *                      word that lgs_device_error describes;
+ *   LGS_OK             nothing recorded; *detail = 0.
+ * When several kinds are pending they come out in the order above, one per
+ * call (call again until LGS_OK).  Recorded errors are per device and
+ * process-wide (not per stream): a caller that shares the device with other
+ * users of the library sees theirs too.  detail may be NULL.  Returns
+ * LGS_ERR_CUDA if the synchronisation itself fails (e.g. a faulted context).
+ * ---------------------------------------------------------------------- */
+lgs_status lgs_sync_status(void* stream, int64_t* detail);
+
+/* Sets the number of polling rounds after which the decoupled look-back of
+ * the radix sort behind gs_prune gives up (LGS_ERR_TIMEOUT), for calls
+ * enqueued afterwards; polls <= 0 restores the default (4,194,304, about a
+ * second).  A test hook for the timeout path: a small limit makes a look-back
+ * that has to wait for a slower block give up at once.  Process-wide; no
+ * counterpart in the paper. */
+void lgs_set_sort_wait_limit(int64_t polls);
+
+/* ------------------------------------------------------------------------
  * gs_project -- EWA projection of every Gaussian into every camera.
  *
  * Sec. III-B.1: a Gaussian has position p, rotation q, scale s, opacity
@@ -92,7 +135,10 @@ lgs_status lgs_zero(void* dev, size_t bytes, void* stream);
  *   Sigma2 = J R_c Sigma3 R_c^T J^T + 0.3 I;  conic = Sigma2^-1;
  *   opacity o = sigmoid(logit).
  * A Gaussian is culled (rect empty) if tz <= znear, det(Sigma2) <= 0,
- * o < 1/255 or its support misses the image.  The support radius is
+ * o < 1/255, its quaternion is zero or its support misses the image.  A
+ * Gaussian with a NaN or infinite parameter is culled too and recorded as
+ * LGS_ERR_NONFINITE (see lgs_sync_status); a camera with a non-finite
+ * value returns LGS_ERR_NONFINITE at once.  The support radius is
  * sqrt(2 ln(255 o) lambda_max(Sigma2)) (1 + 1e-5) + 1e-3 px: every pixel
  * outside it has o exp(power) < 1/255, so tiled rendering equals per-pixel
  * rendering over all Gaussians.
@@ -127,9 +173,10 @@ lgs_status gs_project(const float* means, const float* quats, const float* log_s
  *   tile's instances in ids; (0, 0) for an empty tile.
  * keys_opt [capacity] uint64 out or NULL: the sort keys.
  * n_instances_dev: device int64 out, the instance count K.  If K >
- *   capacity nothing is sorted, every range is (0, 0) and the caller must
- *   retry with capacity >= K (read K after synchronising).  The call never
- *   synchronises, so capacity is not checked on the host.
+ *   capacity nothing is sorted, every range is (0, 0), LGS_ERR_CAPACITY is
+ *   recorded for lgs_sync_status (detail = K) and the caller must retry
+ *   with capacity >= K.  The call never synchronises, so capacity is not
+ *   checked on the host.
  * workspace: device scratch of at least gs_bin_sort_workspace(...) bytes,
  *   256-byte aligned.
  * ---------------------------------------------------------------------- */
@@ -213,8 +260,10 @@ lgs_status gs_render_bwd(const float* means, const float* quats, const float* lo
  * n_cams * n above that limit returns LGS_ERR_INVALID before anything is
  * enqueued.  Nothing is allocated by the caller or the library.
  * The first call on a device looks the array's device address up (with that
- * device current) and caches it: make that first call before any stream
- * capture.  All calls share the array, zero the part they use and leave
+ * device current) and caches it with the ID of the device's current
+ * context: make that first call before any stream capture.  A call in a new
+ * context of the device (after cudaDeviceReset) looks it up again, so the
+ * first call after a reset should also come before any capture.  All calls share the array, zero the part they use and leave
  * their contents in it; calls that overlap on the GPU (unordered streams)
  * race on it, so order them on one stream.
  * ---------------------------------------------------------------------- */
@@ -245,7 +294,9 @@ lgs_status lgs_l1_loss(const float* pred, const void* target, int target_dtype, 
  * Eq. 2: distillation through the frozen decoder; Sec. III-B.4 Eq. 3:
  * encoder adaptation).  Layers 0-3 are the encoder 512-256-128-64-16, layers
  * 4-7 the decoder 16-64-128-256-512; layer l maps width w[l] to w[l+1] with
- * y = x W_l^T + b_l, GELU (erf form) after every layer except 3 and 7.
+ * y = x W_l^T + b_l, GELU after every layer except 3 and 7, in its tanh form
+ * 0.5 x (1 + tanh(sqrt(2/pi) (x + 0.044715 x^3))) (the paper names no
+ * activation; the hardware tanh approximation evaluates it).
  * GEMMs run on the tensor cores with BF16 operands and FP32 accumulation;
  * activations between layers are BF16.  Pixels are rows: x [P, 512],
  * z [P, 16], all row-major.
@@ -269,9 +320,11 @@ typedef struct {
 /* Training state: FP32 master weights and biases, Adam moments, the last
  * step's gradients, and the BF16 copies (Wbf = W, Wtbf = W^T) that the GEMMs
  * read.  step counts Adam steps and is incremented by ae_train_step (host
- * field).  Every pointer is 16-byte aligned.  The gradient buffers are
- * zeroed at the start of each step, one memset per run of adjacent buffers:
- * laid out back to back (gW[0], gb[0], gW[1], ...) they take one. */
+ * field).  Every pointer is 16-byte aligned.  Each step overwrites the
+ * gradient buffers gW / gb of the layers it trains with that step's
+ * gradients.  The weight gradients are summed in a fixed order (per-CTA
+ * partial sums in the workspace, added slice by slice), so the same inputs
+ * give bit-identical gradients and updates on every run. */
 typedef struct {
   float* W[LGS_AE_LAYERS];
   float* b[LGS_AE_LAYERS];
@@ -287,7 +340,9 @@ typedef struct {
 } lgs_ae_state;
 
 /* Scratch bytes for P pixels of LGS_AE_ENCODE, LGS_AE_DECODE or
- * LGS_AE_TRAIN work (0 for a bad argument). */
+ * LGS_AE_TRAIN work (0 for a bad argument), for the current device (the
+ * training scratch holds the per-CTA partial weight gradients, about one
+ * [N, K] slice per SM and layer: 81 MB on a 152-SM GPU at P >= 9,728). */
 size_t ae_workspace_bytes(int64_t P, int what);
 
 /* z [P,16] fp32 = E_phi(x), x bf16 [P,512] (the encoder prior of new
@@ -450,9 +505,10 @@ lgs_status gs_query_relevance(const void* feats, int feat_dtype, int64_t M, int 
  * set when a wait gives up (0 = none; bits 0-3 the autoencoder layer
  * kernels -- 1: a wait gave up, 4: shared memory not on the 1 KB boundary
  * the 128-byte swizzle needs, so the kernel returned without work -- bits
- * 4-7 the fused decoder, 8-11 the sort, 12-15 the fused encoder, whose
- * bit 15 again means misaligned shared memory).
- * Synchronises the device. */
+ * 4-7 the fused decoder, 8-11 the sort's look-back, 12-15 the fused
+ * encoder, whose bit 15 again means misaligned shared memory).  The same
+ * word is the detail of LGS_ERR_TIMEOUT in lgs_sync_status; this call clears
+ * it for both.  Synchronises the device. */
 lgs_status lgs_device_error(int* code);
 
 #ifdef __cplusplus

@@ -24,13 +24,18 @@
 //     Epilogues: bias+GELU (+ pre-activation), linear, GELU'-gated backward,
 //     and the fused losses (L1 against a target, or L2 + (1 - cos)) that
 //     also emit the output gradient.
-//   dw_kernel<KT>: dW[N, K] += sum_p G[p, n] X[p, k] over a pixel range, and
-//     the bias gradient db[n] += sum_p G[p, n] in the same launch; the pixel
-//     dimension is the MMA's K, so G and X as stored are MN-major operands
-//     that 3-D TMA loads land without a transpose.
-//   adam_all and pack_all kernels (SIMT; one launch for every layer).
+//   dw_kernel<KT>: the partial dW[N, K] = sum_p G[p, n] X[p, k] over one
+//     pixel range, and the partial bias gradient sum_p G[p, n], in the same
+//     launch; the pixel dimension is the MMA's K, so G and X as stored are
+//     MN-major operands that TMA loads land without a transpose.  Each CTA
+//     stores its partial tile to its own slice of the workspace (no atomics).
+//   adam_all kernel: sums every element's partials in a fixed order (slice
+//     0, 1, ...), stores the gradient and takes the Adam step, for every
+//     layer in one launch; the training step is therefore bit-reproducible.
+//   pack_all kernel (SIMT; one launch for every layer).
 #include <algorithm>
 #include <cstring>
+#include <string>
 
 #include "common.cuh"
 #include "kernels.cuh"
@@ -141,6 +146,7 @@ __global__ void __launch_bounds__(kLayerThreads, 2) layer_kernel(const __grid_co
   uint64_t* full = mbar + 2;                                          // [2] TMA data of a stage in
   uint32_t* tslot = reinterpret_cast<uint32_t*>(full + 2);
   uint64_t* xbar = reinterpret_cast<uint64_t*>(sm + 2 * L::STAGE + 40);  // EPI_RECON target in
+  uint64_t* dbar = xbar + 1;  // a give-up waits here for the MMAs already issued
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int64_t row0 = (int64_t)blockIdx.x * 128;
   const int n0 = blockIdx.y * NT;
@@ -157,6 +163,7 @@ __global__ void __launch_bounds__(kLayerThreads, 2) layer_kernel(const __grid_co
     tc::mbar_init(&full[0], 1);
     tc::mbar_init(&full[1], 1);
     tc::mbar_init(xbar, 1);
+    tc::mbar_init(dbar, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   tc::fence_before();
@@ -164,6 +171,7 @@ __global__ void __launch_bounds__(kLayerThreads, 2) layer_kernel(const __grid_co
   tc::fence_after();
   const uint32_t tmem = *tslot;
   bool ok = true;
+  int issued = 0;  // K-chunks whose TMA loads thread 0 issued
 
   const int nk = K / KC;
   constexpr uint32_t SBO = KC * 16;
@@ -196,6 +204,7 @@ __global__ void __launch_bounds__(kLayerThreads, 2) layer_kernel(const __grid_co
             tc::tma_load_3d(st + L::A_BYTES + h * L::BROWS * KC * 2, &bmap, 0, n0 + h * L::BROWS,
                         kc * (KC / 8), &full[s]);
         }
+        issued = kc + 1;
       }
     } else if (tid == 32) {
       for (int kc = 0; kc < nk && ok; kc++) {
@@ -303,6 +312,19 @@ __global__ void __launch_bounds__(kLayerThreads, 2) layer_kernel(const __grid_co
   if (ok) ok = __syncthreads_and(tc::mbar_wait(&mbar[(nk - 1) & 1], ((nk - 1) >> 1) & 1, kSpinLimit));
   if (!ok) {
     if (tid == 0) report_timeout();
+    // before the CTA leaves: its copies in flight land (at most the last two
+    // chunks' TMA loads; every thread's cp.async groups) and the MMAs issued
+    // so far finish, each wait bounded again
+    if (a.a_f32) {
+      tc::cp_async_wait_all();
+    } else if (tid == 0) {
+      for (int c = issued > 2 ? issued - 2 : 0; c < issued; c++)
+        tc::mbar_wait(&full[c & 1], (c >> 1) & 1, kSpinLimit);
+    }
+    if (tid == (a.a_f32 ? 0 : 32)) {
+      tc::commit(dbar);
+      tc::mbar_wait(dbar, 0, kSpinLimit);
+    }
   } else {
     tc::fence_after();
     // ---------------------------------------------------------- epilogue
@@ -388,7 +410,8 @@ __global__ void __launch_bounds__(kLayerThreads, 2) layer_kernel(const __grid_co
 #pragma unroll
           for (int b = 0; b < 8; b++) tc::tma_load_2d(sx + b * 16384, &tmap, 64 * b, (int)row0, xbar);
         }
-        if (__syncthreads_and(tc::mbar_wait(xbar, 0, kSpinLimit))) {
+        const bool landed = tc::mbar_wait(xbar, 0, kSpinLimit);
+        if (__syncthreads_and(landed)) {
           uint8_t* xt = sm + 8192;
           // columns c0 .. c0 + 31 of row r, as 32 floats
           auto load_x = [&](int c0, float* x) {
@@ -467,6 +490,7 @@ __global__ void __launch_bounds__(kLayerThreads, 2) layer_kernel(const __grid_co
           }
         } else if (tid == 0) {
           report_timeout();
+          if (!landed) tc::mbar_wait(xbar, 0, kSpinLimit);  // let the target loads land
         }
       }
     } else {
@@ -564,8 +588,8 @@ struct DwArgs {
   int N, K;
   int chunks_per_cta;      // 64-pixel chunks per CTA
   int a_tx, b_tx;          // bytes one stage's G and X loads deliver
-  float* dW;               // [N][K], accumulated
-  float* db;               // [N], accumulated (column sums of G), or null
+  float* part;             // [splits][N][K]: CTA z's partial dW in slice z (overwritten)
+  float* dbpart;           // [splits][N]: its partial column sums of G, or null
 };
 
 // Shared memory of dw_kernel: a ring of stages, each one 64-pixel chunk of
@@ -582,19 +606,21 @@ struct DwSmem {
   static constexpr int STAGE = A_BYTES + B_BYTES;
   static constexpr int S = (196608 / STAGE) < 8 ? (196608 / STAGE) : 8;
   static constexpr int ONES = S * STAGE;
-  static constexpr int BAR = ONES + 512;         // full[S], empty[S], done, TMEM slot
-  static constexpr size_t total = BAR + (2 * S + 1) * 8 + 16;
+  static constexpr int BAR = ONES + 512;         // full[S], empty[S], done, drain, TMEM slot
+  static constexpr size_t total = BAR + (2 * S + 2) * 8 + 16;
   // dW in columns [0, KT), the bias sums in [KT, KT + 16)
   static constexpr uint32_t TCOLS = KT + 16 <= 32 ? 32 : KT + 16 <= 64 ? 64 : KT + 16 <= 128 ? 128
                                   : KT + 16 <= 256 ? 256 : 512;
 };
 
-// dW[n0 .. n0 + 127, k0 .. k0 + KT) += sum_p G[p, n] X[p, k] over the CTA's
-// pixel range, and (k-tile 0, db given) db[n] += sum_p G[p, n].  The pixel
-// is the MMA's K: both operands are MN-major (G and X as stored, rows =
-// pixels), so the TMA loads them without a transpose; the bias sums are one
-// more N = 16 MMA of G^T against a block of ones.  Thread 0 streams the
-// stages, thread 32 issues the MMAs; all 128 threads add the tile to dW.
+// part[z][n0 .. n0 + 127][k0 .. k0 + KT) = sum_p G[p, n] X[p, k] over the
+// pixel range of split z = blockIdx.z, and (k-tile 0, dbpart given)
+// dbpart[z][n] = sum_p G[p, n].  The pixel is the MMA's K: both operands are
+// MN-major (G and X as stored, rows = pixels), so the TMA loads them without
+// a transpose; the bias sums are one more N = 16 MMA of G^T against a block
+// of ones.  Thread 0 streams the stages, thread 32 issues the MMAs; all 128
+// threads store the tile (thread = row) to the CTA's own slice, so the sum
+// over splits is left to a fixed-order pass.
 // GSW: G in the swizzled layout (N >= 64); X is swizzled when KT >= 64.
 template <int KT, bool GSW>
 __global__ void __launch_bounds__(128, 1) dw_kernel(const __grid_constant__ DwArgs a,
@@ -605,10 +631,11 @@ __global__ void __launch_bounds__(128, 1) dw_kernel(const __grid_constant__ DwAr
   uint64_t* full = reinterpret_cast<uint64_t*>(sm + L::BAR);
   uint64_t* empty = full + L::S;
   uint64_t* done = empty + L::S;
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(done + 1);
+  uint64_t* dbar = done + 1;  // a give-up waits here for the MMAs already issued
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(dbar + 1);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int n0 = blockIdx.x * 128, k0 = blockIdx.y * KT;
-  const bool bias = a.db != nullptr && blockIdx.y == 0;
+  const bool bias = a.dbpart != nullptr && blockIdx.y == 0;
   const int64_t pbeg = (int64_t)blockIdx.z * a.chunks_per_cta * L::PC;
   const int64_t pend = min(a.P, pbeg + (int64_t)a.chunks_per_cta * L::PC);
   const int nchunks = pend > pbeg ? (int)((pend - pbeg + L::PC - 1) / L::PC) : 0;
@@ -619,7 +646,7 @@ __global__ void __launch_bounds__(128, 1) dw_kernel(const __grid_constant__ DwAr
   }
   if (warp == 0) tc::tmem_alloc(tslot, L::TCOLS);
   if (tid == 0) {
-    for (int i = 0; i < 2 * L::S + 1; i++) tc::mbar_init(&full[i], 1);
+    for (int i = 0; i < 2 * L::S + 2; i++) tc::mbar_init(&full[i], 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (tid < 32) reinterpret_cast<uint4*>(sm + L::ONES)[tid] = make_uint4(0x3F803F80u, 0x3F803F80u,
@@ -631,6 +658,7 @@ __global__ void __launch_bounds__(128, 1) dw_kernel(const __grid_constant__ DwAr
   const uint32_t tmem = *tslot;
   const uint32_t sbase = tc::smem_addr(sm);
   bool ok = true;
+  int issued = 0;  // chunks whose TMA loads thread 0 issued
   if (tid == 0) {
     for (int ch = 0; ch < nchunks && ok; ch++) {
       const int s = ch % L::S;
@@ -654,6 +682,7 @@ __global__ void __launch_bounds__(128, 1) dw_kernel(const __grid_constant__ DwAr
       } else {
         tc::tma_load_3d(st + L::A_BYTES, &xmap, 0, p0, k0 / 8, &full[s]);
       }
+      issued = ch + 1;
     }
   } else if (tid == 32) {
     // MN-major A and B (bits 15 and 16).  Swizzled: 64-feature atoms 8 KB
@@ -687,27 +716,43 @@ __global__ void __launch_bounds__(128, 1) dw_kernel(const __grid_constant__ DwAr
   ok = __syncthreads_and(ok);
   if (ok && nchunks > 0) ok = __syncthreads_and(tc::mbar_wait(done, 0, kSpinLimit));
   if (!ok) {
-    if (tid == 0) report_timeout();
-  } else if (nchunks > 0) {
-    tc::fence_after();
+    if (tid == 0) {
+      report_timeout();
+      // the loads still in flight (at most one ring's worth) land first
+      for (int c = issued > L::S ? issued - L::S : 0; c < issued; c++)
+        tc::mbar_wait(&full[c % L::S], (uint32_t)(c / L::S) & 1, kSpinLimit);
+    } else if (tid == 32) {  // and the MMAs issued so far finish
+      tc::commit(dbar);
+      tc::mbar_wait(dbar, 0, kSpinLimit);
+    }
+  } else {
+    // the launch gives every split at least one chunk; an empty one stores zeros
     const int n = n0 + warp * 32 + lane;
     const uint32_t tb = tmem + ((uint32_t)(warp * 32) << 16);
+    float* prow = a.part + ((int64_t)blockIdx.z * a.N + n) * a.K + k0;
+    if (nchunks > 0) tc::fence_after();
     constexpr int CW = KT < 32 ? 16 : 32;
     for (int c0 = 0; c0 < KT; c0 += CW) {
       float v[32];
-      if (CW == 32) tc::tmem_ld32(tb + c0, v);
-      else tc::tmem_ld16(tb + c0, v);
+      if (nchunks > 0) {
+        if (CW == 32) tc::tmem_ld32(tb + c0, v);
+        else tc::tmem_ld16(tb + c0, v);
+      } else {
+#pragma unroll
+        for (int q = 0; q < 32; q++) v[q] = 0.f;
+      }
       if (n < a.N) {
-        float4* dst = reinterpret_cast<float4*>(a.dW + (int64_t)n * a.K + k0 + c0);
+        float4* dst = reinterpret_cast<float4*>(prow + c0);
 #pragma unroll
         for (int q = 0; q < CW / 4; q++)
-          atomicAdd(dst + q, make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]));
+          dst[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
       }
     }
     if (bias) {
       float v[32];
-      tc::tmem_ld16(tb + KT, v);
-      if (n < a.N) atomicAdd(a.db + n, v[0]);
+      if (nchunks > 0) tc::tmem_ld16(tb + KT, v);
+      else v[0] = 0.f;
+      if (n < a.N) a.dbpart[(int64_t)blockIdx.z * a.N + n] = v[0];
     }
   }
   tc::fence_before();
@@ -717,12 +762,16 @@ __global__ void __launch_bounds__(128, 1) dw_kernel(const __grid_constant__ DwAr
 
 
 // Adam on up to 2 * kAeLayers parameter tensors in one launch: segment j
-// holds elements [start[j], start[j + 1]) of the concatenation.
+// holds elements [start[j], start[j + 1]) of the concatenation.  Its
+// gradient is the sum of splits[j] partial slices (part[j], slice z at
+// z * len), added in slice order (0, 1, ...) and stored to g[j] as well.
 struct AdamSegs {
   float* w[2 * kAeLayers];
   float* m[2 * kAeLayers];
   float* v[2 * kAeLayers];
-  const float* g[2 * kAeLayers];
+  float* g[2 * kAeLayers];
+  const float* part[2 * kAeLayers];
+  int splits[2 * kAeLayers];
   int64_t start[2 * kAeLayers + 1];
   int n;
 };
@@ -733,8 +782,20 @@ __global__ void adam_all_kernel(const __grid_constant__ AdamSegs S, float lr, fl
        e += (int64_t)gridDim.x * blockDim.x) {
     int j = 0;
     while (S.start[j + 1] <= e) j++;
-    const int64_t i = e - S.start[j];
-    const float gi = S.g[j][i];
+    const int64_t i = e - S.start[j], len = S.start[j + 1] - S.start[j];
+    const float* pp = S.part[j] + i;
+    const int nz = S.splits[j];
+    float gi = 0.f;
+    int z = 0;
+    for (; z + 8 <= nz; z += 8) {  // eight loads in flight, added in slice order
+      float t[8];
+#pragma unroll
+      for (int u = 0; u < 8; u++) t[u] = pp[(int64_t)(z + u) * len];
+#pragma unroll
+      for (int u = 0; u < 8; u++) gi += t[u];
+    }
+    for (; z < nz; z++) gi += pp[(int64_t)z * len];
+    S.g[j][i] = gi;
     const float mi = b1 * S.m[j][i] + (1.f - b1) * gi;
     const float vi = b2 * S.v[j][i] + (1.f - b2) * gi * gi;
     S.m[j][i] = mi;
@@ -813,6 +874,28 @@ static lgs_status launch_layer(const LayerArgs& a, cudaStream_t s) {
   }
 }
 
+// How dw_kernel splits one layer's weight gradient: 128-feature row tiles,
+// KT-feature column tiles, and the pixel chunks (64 pixels) cut into `splits`
+// ranges of chunks_per_cta, so that the grid holds about one CTA per SM.
+// Every split gets at least one chunk.  The workspace holds one partial
+// [N, K] slice (and [N] bias slice) per split.
+struct DwPlan {
+  int KT, ntile, ktile, chunks_per_cta;
+  int64_t splits;
+};
+static DwPlan dw_plan(int64_t P, int N, int K) {
+  DwPlan d;
+  d.KT = K == 16 ? 16 : K == 64 ? 64 : K == 128 ? 128 : 256;
+  d.ntile = (N + 127) / 128;
+  d.ktile = K / d.KT;
+  const int64_t chunks = std::max<int64_t>(1, (P + 63) / 64);
+  int64_t splits = std::max<int64_t>(1, sm_count() / (d.ntile * d.ktile));
+  splits = std::min<int64_t>(splits, chunks);
+  d.chunks_per_cta = (int)((chunks + splits - 1) / splits);
+  d.splits = (chunks + d.chunks_per_cta - 1) / d.chunks_per_cta;
+  return d;
+}
+
 template <int KT, bool GSW>
 static lgs_status launch_dw_t(const __nv_bfloat16* G, const __nv_bfloat16* X, DwArgs a,
                               cudaStream_t s) {
@@ -831,23 +914,22 @@ static lgs_status launch_dw_t(const __nv_bfloat16* G, const __nv_bfloat16* X, Dw
   if (!made) return LGS_ERR_CUDA;
   a.a_tx = ga * L::PC * 16;  // both layouts: min(128, N) features x 64 pixels
   a.b_tx = gb * L::PC * 16;
-  const int ntile = (a.N + 127) / 128, ktile = a.K / KT;
-  // one CTA per SM: the pixel chunks split into about sm_count / tiles ranges
-  const int64_t chunks = (a.P + L::PC - 1) / L::PC;
-  int64_t splits = std::max<int64_t>(1, sm_count() / (ntile * ktile));
-  splits = std::min<int64_t>(splits, chunks);
-  a.chunks_per_cta = (int)((chunks + splits - 1) / splits);
-  splits = (chunks + a.chunks_per_cta - 1) / a.chunks_per_cta;
-  dw_kernel<KT, GSW><<<dim3(ntile, ktile, (unsigned)splits), 128, L::total, s>>>(a, gmap, xmap);
+  static_assert(L::PC == 64, "dw_plan counts 64-pixel chunks");
+  const DwPlan d = dw_plan(a.P, a.N, a.K);
+  a.chunks_per_cta = d.chunks_per_cta;
+  dw_kernel<KT, GSW><<<dim3(d.ntile, d.ktile, (unsigned)d.splits), 128, L::total, s>>>(a, gmap,
+                                                                                      xmap);
   LGS_CHECK_LAUNCH();
   return LGS_OK;
 }
 
-// dW += G^T X and db += colsum(G) for one layer, in one launch.
+// The partials of dW = G^T X and db = colsum(G) for one layer, in one
+// launch: dw_plan(P, N, K).splits slices of [N, K] in part and of [N] in
+// dbpart.
 static lgs_status launch_dw(const __nv_bfloat16* G, const __nv_bfloat16* X, int64_t P, int N,
-                            int K, float* dW, float* db, cudaStream_t s) {
+                            int K, float* part, float* dbpart, cudaStream_t s) {
   if (P == 0) return LGS_OK;
-  DwArgs a{P, N, K, 0, 0, 0, dW, db};
+  DwArgs a{P, N, K, 0, 0, 0, part, dbpart};
   // G in the swizzled layout when each 128-feature tile is one or two
   // whole 64-feature boxes (N = 64 or a multiple of 128)
   if (N == 64 || N % 128 == 0) {
@@ -876,7 +958,7 @@ static LayerArgs layer(const void* A, bool a_f32, const uint16_t* W, const float
   return a;
 }
 
-// Workspace carving (bf16 activation buffers, 256-byte aligned).
+// Workspace carving (bf16 activation buffers, f32 partials; 256-byte aligned).
 struct Carver {
   char* base;
   size_t off = 0;
@@ -884,6 +966,11 @@ struct Carver {
   __nv_bfloat16* bf(int64_t P, int w) {
     __nv_bfloat16* p = base ? reinterpret_cast<__nv_bfloat16*>(base + off) : nullptr;
     off += ((size_t)P * w * 2 + 255) & ~(size_t)255;
+    return p;
+  }
+  float* f32(int64_t count) {
+    float* p = base ? reinterpret_cast<float*>(base + off) : nullptr;
+    off += ((size_t)count * 4 + 255) & ~(size_t)255;
     return p;
   }
 };
@@ -905,6 +992,9 @@ struct TrainBufs {
   __nv_bfloat16* act[8];   // output of layer l (post-activation; z for l = 3)
   __nv_bfloat16* pre[8];   // pre-activation of hidden layers
   __nv_bfloat16* grad[8];  // gradient w.r.t. the output of layer l (after GELU')
+  float* wpart[8];         // dw_plan(...).splits partial weight gradients of layer l
+  float* bpart[8];         // and its partial bias gradients
+  int splits[8];
 };
 static void carve_train(Carver& c, int64_t P, TrainBufs& B) {
   for (int l = 0; l < kAeLayers; l++) {
@@ -912,6 +1002,13 @@ static void carve_train(Carver& c, int64_t P, TrainBufs& B) {
     B.act[l] = c.bf(P, w);
     B.pre[l] = c.bf(P, w);
     B.grad[l] = c.bf(P, w);
+  }
+  for (int l = 0; l < kAeLayers; l++) {
+    const int K = kAeWidths[l], N = kAeWidths[l + 1];
+    const DwPlan d = dw_plan(P, N, K);
+    B.splits[l] = (int)d.splits;
+    B.wpart[l] = c.f32(d.splits * N * K);
+    B.bpart[l] = c.f32(d.splits * N);
   }
 }
 
@@ -1037,9 +1134,8 @@ extern "C" lgs_status ae_train_step(lgs_ae_state* st_, const uint16_t* x, const 
     LGS_CHECK_ARG(st_->W[l] && st_->b[l] && st_->mW[l] && st_->vW[l] && st_->mb[l] && st_->vb[l] &&
                       st_->gW[l] && st_->gb[l] && st_->Wbf[l] && st_->Wtbf[l],
                   "null state pointer");
-  for (int l = 0; l <= last; l++)  // float4 atomics into gW, TMA loads of the BF16 copies
-    LGS_CHECK_ARG(aligned(st_->gW[l], 16) && aligned(st_->gb[l], 16) &&
-                      aligned(st_->Wbf[l], 16) && aligned(st_->Wtbf[l], 16),
+  for (int l = 0; l <= last; l++)  // TMA loads of the BF16 copies
+    LGS_CHECK_ARG(aligned(st_->Wbf[l], 16) && aligned(st_->Wtbf[l], 16),
                   "misaligned state pointer");
   cudaStream_t s = as_stream(stream);
   Carver c(workspace);
@@ -1048,25 +1144,6 @@ extern "C" lgs_status ae_train_step(lgs_ae_state* st_, const uint16_t* x, const 
   auto W = [&](int l) { return st_->Wbf[l]; };
   auto Wt = [&](int l) { return st_->Wtbf[l]; };
   lgs_status st;
-  {  // zero the gradients, one memset per run of adjacent buffers
-    char* run = nullptr;
-    size_t len = 0;
-    for (int l = 0; l <= last; l++) {
-      const int K = kAeWidths[l], N = kAeWidths[l + 1];
-      char* seg[2] = {reinterpret_cast<char*>(st_->gW[l]), reinterpret_cast<char*>(st_->gb[l])};
-      const size_t bytes[2] = {sizeof(float) * N * K, sizeof(float) * N};
-      for (int i = 0; i < 2; i++) {
-        if (run && run + len == seg[i]) {
-          len += bytes[i];
-          continue;
-        }
-        if (run) LGS_CHECK_CUDA(cudaMemsetAsync(run, 0, len, s));
-        run = seg[i];
-        len = bytes[i];
-      }
-    }
-    LGS_CHECK_CUDA(cudaMemsetAsync(run, 0, len, s));
-  }
   // forward, keeping every layer's input and pre-activation
   const void* in = x;
   for (int l = 0; l <= 3; l++) {
@@ -1112,7 +1189,8 @@ extern "C" lgs_status ae_train_step(lgs_ae_state* st_, const uint16_t* x, const 
   for (int l = last; l >= 0; l--) {
     const int K = kAeWidths[l], N = kAeWidths[l + 1];
     const __nv_bfloat16* input = l == 0 ? reinterpret_cast<const __nv_bfloat16*>(x) : B.act[l - 1];
-    if ((st = launch_dw(B.grad[l], input, P, N, K, st_->gW[l], st_->gb[l], s)) != LGS_OK) return st;
+    if ((st = launch_dw(B.grad[l], input, P, N, K, B.wpart[l], B.bpart[l], s)) != LGS_OK)
+      return st;
     if (l == 0) break;
     LayerArgs a;
     if (l == 4) {  // below the linear latent: no GELU
@@ -1139,6 +1217,8 @@ extern "C" lgs_status ae_train_step(lgs_ae_state* st_, const uint16_t* x, const 
       A.m[j] = wb ? st_->mb[l] : st_->mW[l];
       A.v[j] = wb ? st_->vb[l] : st_->vW[l];
       A.g[j] = wb ? st_->gb[l] : st_->gW[l];
+      A.part[j] = wb ? B.bpart[l] : B.wpart[l];
+      A.splits[j] = B.splits[l];
       A.start[j + 1] = A.start[j] + (wb ? nb : nw);
     }
   }
@@ -1198,13 +1278,54 @@ extern "C" lgs_status lgs_codebook_assign(const uint16_t* x, int64_t P, int D,
   return launch_layer(a, s);
 }
 
+// The timeout bit word of lgs_device_error; clear: also reset every part.
+static lgs_status wait_error_word(bool clear, unsigned* word) {
+  unsigned v = 0, zero = 0;
+  LGS_CHECK_CUDA(cudaMemcpyFromSymbol(&v, g_ae_error, sizeof(v)));
+  if (clear && v) LGS_CHECK_CUDA(cudaMemcpyToSymbol(g_ae_error, &zero, sizeof(zero)));
+  *word = v | (fused_error_word(clear) << 4) | (sort_error_word(clear) << 8) |
+          (encode_error_word(clear) << 12);
+  return LGS_OK;
+}
+
 extern "C" lgs_status lgs_device_error(int* code) {
   clear_error();
   LGS_CHECK_ARG(code != nullptr, "code is null");
-  unsigned v = 0, zero = 0;
-  LGS_CHECK_CUDA(cudaMemcpyFromSymbol(&v, g_ae_error, sizeof(v)));
-  LGS_CHECK_CUDA(cudaMemcpyToSymbol(g_ae_error, &zero, sizeof(zero)));
-  *code = (int)(v | (fused_error_word() << 4) | (sort_error_word() << 8) |
-                 (encode_error_word() << 12));
+  unsigned v = 0;
+  const lgs_status st = wait_error_word(true, &v);
+  if (st != LGS_OK) return st;
+  *code = (int)v;
+  return LGS_OK;
+}
+
+extern "C" lgs_status lgs_sync_status(void* stream, int64_t* detail) {
+  clear_error();
+  if (detail) *detail = 0;
+  LGS_CHECK_CUDA(cudaStreamSynchronize(as_stream(stream)));
+  // the records are read with synchronous copies: every kernel that can
+  // write them and was enqueued on `stream` has finished
+  const unsigned long long nf = nonfinite_word(false);
+  if (nf != ~0ull) {
+    nonfinite_word(true);
+    if (detail) *detail = (int64_t)nf;
+    set_error("lgs_sync_status: non-finite parameter of Gaussian " + std::to_string(nf));
+    return LGS_ERR_NONFINITE;
+  }
+  const unsigned long long k = capacity_word(false);
+  if (k != 0) {
+    capacity_word(true);
+    if (detail) *detail = (int64_t)k;
+    set_error("lgs_sync_status: gs_bin_sort needed capacity " + std::to_string(k));
+    return LGS_ERR_CAPACITY;
+  }
+  unsigned w = 0;
+  lgs_status st = wait_error_word(false, &w);
+  if (st != LGS_OK) return st;
+  if (w != 0) {
+    if ((st = wait_error_word(true, &w)) != LGS_OK) return st;
+    if (detail) *detail = (int64_t)w;
+    set_error("lgs_sync_status: a bounded wait gave up (sites " + std::to_string(w) + ")");
+    return LGS_ERR_TIMEOUT;
+  }
   return LGS_OK;
 }

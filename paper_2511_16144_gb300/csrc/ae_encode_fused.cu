@@ -133,7 +133,8 @@ encode_fused_kernel(const __grid_constant__ EncArgs a, const __grid_constant__ C
   uint64_t* accS = accL0 + 2;         // MMA -> epilogue: L1 / L2 / L3 done
   uint64_t* opL0 = accS + 1;          // epilogue -> MMA: L0 read out, h1 staged
   uint64_t* opS = opL0 + 1;           // epilogue -> MMA: h2 / h3 staged, z written
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(opS + 1);
+  uint64_t* drain = opS + 1;          // a give-up waits here for the MMAs already issued
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(drain + 1);
   float* sb = reinterpret_cast<float*>(sm + SM_BIAS);
   const float* sb0 = sb;
   const float* sb1 = sb + 256;
@@ -159,6 +160,7 @@ encode_fused_kernel(const __grid_constant__ EncArgs a, const __grid_constant__ C
     tc::mbar_init(accS, 1);
     tc::mbar_init(opL0, kEpiWarps);
     tc::mbar_init(opS, kEpiWarps);
+    tc::mbar_init(drain, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   tc::fence_before();
@@ -173,7 +175,8 @@ encode_fused_kernel(const __grid_constant__ EncArgs a, const __grid_constant__ C
     if (lane == 0) {
       bool ok = true;
       const int n = ring_count(nloc);
-      for (int j = pp; j < n && ok; j += 2) {
+      int j = pp;
+      for (; j < n && ok; j += 2) {
         int unit, tl;
         ring_unit(j, nloc, unit, tl);
         const uint32_t s = (uint32_t)j % kStages, round = (uint32_t)j / kStages;
@@ -190,6 +193,12 @@ encode_fused_kernel(const __grid_constant__ EncArgs a, const __grid_constant__ C
         tc::bulk_g2s(st + kXBytes, a.pack + a.off[unit], a.bytes[unit], &full[s]);
       }
       if (!ok) atomicOr(&g_enc_error, 1u);
+      // before the CTA leaves, this producer's last copies have landed (ring
+      // positions j - 2, j - 4, ... down to j - kStages; a stage belongs to
+      // one producer since kStages is even)
+      static_assert(kStages % 2 == 0, "a ring stage must belong to one producer");
+      for (int v = j - 2; v >= 0 && v >= j - kStages; v -= 2)
+        tc::mbar_wait(&full[(uint32_t)v % kStages], ((uint32_t)v / kStages) & 1, kLimit);
     }
   } else if (warp == kEpiWarps) {
     // ---------------------------------------------------------------- MMA issuer
@@ -276,7 +285,12 @@ encode_fused_kernel(const __grid_constant__ EncArgs a, const __grid_constant__ C
         commit(&accL0[k & 1]);
       }
     }
-    if (!ok && lane == 0) atomicOr(&g_enc_error, 2u);
+    if (!ok) {  // the MMAs issued so far finish before TMEM is released
+      if (lane == 0) atomicOr(&g_enc_error, 2u);
+      if (tc::elect_one()) tc::commit(drain);
+      __syncwarp();
+      tc::mbar_wait(drain, 0, kLimit);
+    }
   } else {
     // ---------------------------------------------------------------- epilogue
     const int q = warp & 3, qq = warp >> 2;
@@ -489,10 +503,10 @@ lgs_status launch_encode_fused(const lgs_ae_weights* w, const uint16_t* x, int64
   return LGS_OK;
 }
 
-unsigned encode_error_word() {
+unsigned encode_error_word(bool clear) {
   unsigned v = 0, zero = 0;
   if (cudaMemcpyFromSymbol(&v, g_enc_error, sizeof(v)) != cudaSuccess) return 0;
-  cudaMemcpyToSymbol(g_enc_error, &zero, sizeof(zero));
+  if (clear && v) cudaMemcpyToSymbol(g_enc_error, &zero, sizeof(zero));
   return v;
 }
 

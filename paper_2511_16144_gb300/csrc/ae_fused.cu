@@ -146,9 +146,9 @@ __device__ unsigned g_fused_error;
 constexpr int kEpiWarps = 16;
 constexpr int kFusedThreads = (kEpiWarps + 3) * 32;   // + MMA warp + two producer warps
 // barriers: full[kStages], empty[kStages], accH, accT, opH, opT, ybar[2],
-// dyfree, then the TMEM slot
-constexpr uint32_t kBarBytes = (2 * kStages + 7) * 8 + 4;
-constexpr uint32_t SM_BIAS = SM_BAR + 128;             // b4 | b5 | b6 | b7 (960 floats)
+// dyfree, drain, then the TMEM slot
+constexpr uint32_t kBarBytes = (2 * kStages + 8) * 8 + 4;
+constexpr uint32_t SM_BIAS = SM_BAR + 144;             // b4 | b5 | b6 | b7 (960 floats)
 constexpr uint32_t SM_ALL = SM_BIAS + 960 * 4;
 static_assert(kBarBytes <= SM_BIAS - SM_BAR, "barrier block overlaps the biases");
 static_assert(SM_ALL <= 232448, "shared-memory map exceeds 227 KB");
@@ -190,7 +190,8 @@ decode_fused_kernel(const __grid_constant__ FusedArgs a) {
   uint64_t* opT = opH + 1;              // epilogue -> MMA: a dy chunk / d3 / d2 / d1 / dz done
   uint64_t* ybar = opT + 1;             // [2] output chunk ready in TMEM buffer c & 1
   uint64_t* dyfree = ybar + 2;          // the backward product of the last dy chunk is done
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(dyfree + 1);
+  uint64_t* drain = dyfree + 1;         // a give-up waits here for the MMAs already issued
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(drain + 1);
   float* sb = reinterpret_cast<float*>(sm + SM_BIAS);
   const float* sb4 = sb;
   const float* sb5 = sb + 64;
@@ -213,6 +214,7 @@ decode_fused_kernel(const __grid_constant__ FusedArgs a) {
     tc::mbar_init(&ybar[0], 1);
     tc::mbar_init(&ybar[1], 1);
     tc::mbar_init(dyfree, 1);
+    tc::mbar_init(drain, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   tc::fence_before();
@@ -245,6 +247,12 @@ decode_fused_kernel(const __grid_constant__ FusedArgs a) {
         }
       }
       if (!ok) atomicOr(&g_fused_error, 1u);
+      // before the CTA leaves, this producer's last copies have landed: the
+      // stages of the last kStages units are its own (kStages is even), and
+      // the MMA warp has waited for them already unless it gave up
+      static_assert(kStages % 2 == 0, "a ring stage must belong to one producer");
+      for (uint32_t v = u > kStages ? u - kStages : 0; v < u; v++)
+        if ((v & 1) == pp) tc::mbar_wait(&full[v % kStages], (v / kStages) & 1, kLimit);
     }
   } else if (warp == kEpiWarps) {
     // ---------------------------------------------------------------- MMA issuer
@@ -345,7 +353,12 @@ decode_fused_kernel(const __grid_constant__ FusedArgs a) {
         f3();
       }
     }
-    if (!ok && lane == 0) atomicOr(&g_fused_error, 2u);
+    if (!ok) {  // the MMAs issued so far finish before TMEM is released
+      if (lane == 0) atomicOr(&g_fused_error, 2u);
+      if (tc::elect_one()) tc::commit(drain);
+      __syncwarp();
+      tc::mbar_wait(drain, 0, kLimit);
+    }
   } else {
     // ---------------------------------------------------------------- epilogue
     // warp w reads TMEM lane quadrant w % 4 (rows 32 (w % 4) ..) and the
@@ -714,10 +727,10 @@ lgs_status launch_decode_fused(const lgs_ae_weights* w, const float* z, int64_t 
   return LGS_OK;
 }
 
-unsigned fused_error_word() {
+unsigned fused_error_word(bool clear) {
   unsigned v = 0, zero = 0;
   if (cudaMemcpyFromSymbol(&v, g_fused_error, sizeof(v)) != cudaSuccess) return 0;
-  cudaMemcpyToSymbol(g_fused_error, &zero, sizeof(zero));
+  if (clear && v) cudaMemcpyToSymbol(g_fused_error, &zero, sizeof(zero));
   return v;
 }
 

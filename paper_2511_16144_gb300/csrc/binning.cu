@@ -27,6 +27,10 @@
 
 namespace lgs {
 
+// Largest instance count a call needed beyond its capacity (LGS_ERR_CAPACITY
+// of lgs_sync_status); 0 = none.
+__device__ unsigned long long g_capacity_k;
+
 namespace {
 
 constexpr int kSegMax = 4096;          // keys a block sorts in shared memory
@@ -98,6 +102,7 @@ tile_scan_kernel(const uint32_t* __restrict__ counts, uint32_t n_tiles_all,
     carry = 0;
     *n_instances = K;
     *sort_n = fits ? K : 0;
+    if (!fits) atomicMax(&g_capacity_k, (unsigned long long)K);
   }
   __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -523,6 +528,14 @@ int grid_items(int64_t m) {
 }
 
 }  // namespace
+
+unsigned long long capacity_word(bool clear) {
+  unsigned long long v = 0, zero = 0;
+  if (cudaMemcpyFromSymbol(&v, g_capacity_k, sizeof(v)) != cudaSuccess) return 0;
+  if (clear && v) cudaMemcpyToSymbol(g_capacity_k, &zero, sizeof(zero));
+  return v;
+}
+
 }  // namespace lgs
 
 using namespace lgs;

@@ -23,15 +23,15 @@ size_t decode_pack_bytes();
 lgs_status launch_decode_fused(const lgs_ae_weights* w, const float* z, int64_t P,
                                const uint16_t* target, float weight, float* loss, float* dz,
                                void* pack, cudaStream_t s);
-// Reads and clears the fused kernel's timeout word.
-unsigned fused_error_word();
+// Reads (and with clear, clears) the fused decoder's timeout word.
+unsigned fused_error_word(bool clear = true);
 // Fused encoder z = E(x) (x bf16 [P,512] -> z f32 [P,16]); `pack` is
 // encode_pack_bytes() of scratch for the packed weights.
 size_t encode_pack_bytes();
 lgs_status launch_encode_fused(const lgs_ae_weights* w, const uint16_t* x, int64_t P, float* z,
                                void* pack, cudaStream_t s);
-// Reads and clears the fused encoder's timeout word.
-unsigned encode_error_word();
+// Reads (and with clear, clears) the fused encoder's timeout word.
+unsigned encode_error_word(bool clear = true);
 // Streaming multiprocessors of the current device.
 int sm_count();
 // A 3-D TMA tensor map that views a row-major bf16 matrix [rows, K] as
@@ -59,7 +59,13 @@ bool make_swizzled_map(CUtensorMap* map, const void* base, int64_t rows, int K, 
 size_t sort_pairs_scratch(int64_t n);
 bool sort_pairs(uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t* v1, int64_t n, int nbits,
                 void* scratch, cudaStream_t s);
-// Reads and clears the binning sort's look-back timeout word.
-unsigned sort_error_word();
+// Reads (and with clear, clears) the radix sort's look-back timeout word.
+unsigned sort_error_word(bool clear = true);
+// Reads (and with clear, clears) the smallest Gaussian index gs_project
+// found with a non-finite parameter (UINT64_MAX = none).
+unsigned long long nonfinite_word(bool clear);
+// Reads (and with clear, clears) the largest instance count gs_bin_sort
+// needed beyond its capacity (0 = none).
+unsigned long long capacity_word(bool clear);
 
 }  // namespace lgs

@@ -5,10 +5,17 @@
 // transform, local affine (Jacobian) approximation of the perspective map,
 // 2D covariance with a 0.3 px^2 low-pass dilation, its inverse (the conic)
 // and the tile rectangle of the support where o exp(power) >= 1/255.
+#include <cmath>
+#include <string>
+
 #include "common.cuh"
 #include "kernels.cuh"
 
 namespace lgs {
+
+// Smallest index of a Gaussian with a non-finite parameter (LGS_ERR_NONFINITE
+// of lgs_sync_status); all ones = none.
+__device__ unsigned long long g_nonfinite = ~0ull;
 
 struct ProjState {
   float qn[4], qnorm;
@@ -128,11 +135,17 @@ __global__ void project_kernel(const float* __restrict__ means, const float4* __
     const lgs_camera& cam = cams.cam[c];
     float p[3] = {means[3 * i], means[3 * i + 1], means[3 * i + 2]};
     float ls[3] = {log_scales[3 * i], log_scales[3 * i + 1], log_scales[3 * i + 2]};
+    const float4 q = quats[i];
+    const float lg = logits[i];
+    const bool finite = isfinite(p[0]) && isfinite(p[1]) && isfinite(p[2]) && isfinite(ls[0]) &&
+                        isfinite(ls[1]) && isfinite(ls[2]) && isfinite(q.x) && isfinite(q.y) &&
+                        isfinite(q.z) && isfinite(q.w) && isfinite(lg);
+    if (!finite && c == 0) atomicMin(&g_nonfinite, (unsigned long long)i);
     ProjState P;
-    project_state(p, quats[i], ls, logits[i], cam, P);
+    project_state(p, q, ls, lg, cam, P);
     ushort4 r = make_ushort4(0, 0, 0, 0);
     float4 a = make_float4(0.f, 0.f, 0.f, 0.f), b = a;
-    if (P.valid && support_rect(P, cam, r)) {
+    if (finite && P.valid && support_rect(P, cam, r)) {
       a = make_float4(P.u, P.v, P.conic[0], P.conic[1]);
       b = make_float4(P.conic[2], P.o, P.t[2], 0.f);
     } else {
@@ -368,6 +381,14 @@ lgs_status fill_cams(const lgs_camera* cams_host, int n_cams, CamBlock& cb) {
   LGS_CHECK_ARG(n_cams >= 1 && n_cams <= LGS_MAX_CAMS, "n_cams out of range");
   for (int c = 0; c < n_cams; c++) {
     const lgs_camera& k = cams_host[c];
+    bool finite = std::isfinite(k.fx) && std::isfinite(k.fy) && std::isfinite(k.cx) &&
+                  std::isfinite(k.cy) && std::isfinite(k.znear);
+    for (int j = 0; j < 12; j++) finite = finite && std::isfinite(k.viewmat[j]);
+    if (!finite) {
+      set_error(std::string(__func__) + ": camera " + std::to_string(c) +
+                " has a non-finite value");
+      return LGS_ERR_NONFINITE;
+    }
     LGS_CHECK_ARG(k.width > 0 && k.height > 0 && k.width <= 65535 * kTile &&
                       k.height <= 65535 * kTile,
                   "bad image size");
@@ -375,6 +396,13 @@ lgs_status fill_cams(const lgs_camera* cams_host, int n_cams, CamBlock& cb) {
     cb.cam[c] = k;
   }
   return LGS_OK;
+}
+
+unsigned long long nonfinite_word(bool clear) {
+  unsigned long long v = ~0ull, none = ~0ull;
+  if (cudaMemcpyFromSymbol(&v, g_nonfinite, sizeof(v)) != cudaSuccess) return ~0ull;
+  if (clear && v != none) cudaMemcpyToSymbol(g_nonfinite, &none, sizeof(none));
+  return v;
 }
 
 }  // namespace lgs

@@ -90,8 +90,11 @@ __global__ void prune_gather_kernel(const float* __restrict__ means,
   for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n;
        t += (int64_t)gridDim.x * blockDim.x) {
     const uint32_t i = order[t];
-    sp[t] = make_float4(means[3 * (int64_t)i], means[3 * (int64_t)i + 1],
-                        means[3 * (int64_t)i + 2], logits[i]);
+    // an index out of range only follows a sort whose look-back gave up
+    // (LGS_ERR_TIMEOUT): park it at infinity, where it has no neighbours
+    sp[t] = i < n ? make_float4(means[3 * (int64_t)i], means[3 * (int64_t)i + 1],
+                                means[3 * (int64_t)i + 2], logits[i])
+                  : make_float4(INFINITY, INFINITY, INFINITY, 0.f);
   }
 }
 
@@ -121,6 +124,7 @@ __global__ void __launch_bounds__(128)
   for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n;
        t += (int64_t)gridDim.x * blockDim.x) {
     const uint32_t i = sidx[t];
+    if (i >= n) continue;  // see prune_gather_kernel
     const float4 pi = sp[t];
     const uint32_t key = skey[t];
     const uint32_t cx = key % grid.g[0];
@@ -152,7 +156,7 @@ __global__ void __launch_bounds__(128)
               __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy2, dy2)), __fmul_rn(dz2, dz2));
           if (!(__fsqrt_rn(d2) < tau)) continue;
           const uint32_t j = sidx[u];
-          if (!closer(d2, j, bd[kKnnMax - 1], bj[kKnnMax - 1])) continue;
+          if (j >= n || !closer(d2, j, bd[kKnnMax - 1], bj[kKnnMax - 1])) continue;
           // insert into the sorted list: e[s-1] <= new < e[s]
 #pragma unroll
           for (int s = kKnnMax - 1; s > 0; s--) {

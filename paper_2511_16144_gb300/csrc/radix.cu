@@ -7,7 +7,13 @@
 // all earlier tiles by decoupled look-back (walking back over published
 // aggregates until an inclusive prefix is found).  One histogram kernel per
 // sort gives every pass's global digit offsets.  Spins are bounded: a wait
-// that gives up sets the device error word instead of hanging.
+// that gives up sets the device error word instead of hanging, and the block
+// goes on with the counts it has, which are never more than the true prefix,
+// so every store stays in bounds (a later pass that reads the resulting
+// unordered keys guards its stores the same way).
+#include <algorithm>
+#include <atomic>
+
 #include "common.cuh"
 #include "kernels.cuh"
 
@@ -20,7 +26,8 @@ constexpr int kOsItemsSmall = 4;
 constexpr int64_t kOsSmallMax = 1 << 20;
 constexpr int kRadix = 256;
 constexpr uint32_t kFlagAgg = 1u << 30, kFlagInc = 2u << 30, kValMask = (1u << 30) - 1;
-constexpr uint32_t kSpinLimit = 1u << 22;
+constexpr uint32_t kSpinLimit = 1u << 22;  // default polling rounds before a look-back gives up
+static std::atomic<uint32_t> g_spin_limit{kSpinLimit};  // lgs_set_sort_wait_limit
 
 __device__ unsigned g_sort_error;  // a look-back gave up
 
@@ -47,7 +54,8 @@ __device__ __forceinline__ void st_relaxed(uint32_t* p, uint32_t v) {
 // consecutive tiles are `stride` words apart.  Loads 16 predecessors per
 // round so a long chain of aggregates costs few dependent round trips.
 constexpr int kLookAhead = 16;
-__device__ __forceinline__ uint32_t look_back(const uint32_t* col, int64_t stride, int64_t j) {
+__device__ __forceinline__ uint32_t look_back(const uint32_t* col, int64_t stride, int64_t j,
+                                              uint32_t spin_limit) {
   uint32_t prefix = 0, spins = 0;
   while (j >= 0) {
     uint32_t v[kLookAhead];
@@ -69,7 +77,7 @@ __device__ __forceinline__ uint32_t look_back(const uint32_t* col, int64_t strid
     }
     if (done) break;
     j -= q;
-    if (q < kLookAhead && ++spins > kSpinLimit) {  // stalled on an unpublished tile
+    if (q < kLookAhead && ++spins > spin_limit) {  // stalled on an unpublished tile
       atomicOr(&g_sort_error, 1u);
       break;
     }
@@ -156,7 +164,7 @@ __global__ void __launch_bounds__(kOsThreads)
 onesweep_kernel(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin,
                 uint32_t* __restrict__ kout, uint32_t* __restrict__ vout, const int64_t* n_dev,
                 int64_t n_host, int shift, uint32_t mask, const uint32_t* __restrict__ ghist,
-                uint32_t* status, uint32_t* counter) {
+                uint32_t* status, uint32_t* counter, uint32_t spin_limit) {
   __shared__ uint32_t wcnt[kOsThreads / 32][kRadix];
   __shared__ uint32_t dstart[kRadix];
   __shared__ uint32_t goff[kRadix];
@@ -212,7 +220,7 @@ onesweep_kernel(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ v
     st_relaxed(st + d, tot | kFlagInc);
   } else {
     st_relaxed(st + d, tot | kFlagAgg);
-    prefix = look_back(status + d, kRadix, (int64_t)tile - 1);
+    prefix = look_back(status + d, kRadix, (int64_t)tile - 1, spin_limit);
     st_relaxed(st + d, (prefix + tot) | kFlagInc);
   }
   goff[d] = gbase + prefix;
@@ -233,8 +241,10 @@ onesweep_kernel(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ v
     const uint32_t k = sk[j];
     const uint32_t dd = (k >> shift) & mask;
     const uint32_t o = goff[dd] + (uint32_t)j - dstart[dd];
-    kout[o] = k;
-    vout[o] = sv[j];
+    if (o < n) {  // always, unless an earlier look-back gave up (keys then unordered)
+      kout[o] = k;
+      vout[o] = sv[j];
+    }
   }
 }
 
@@ -263,16 +273,17 @@ static bool onesweep_passes(uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t* 
     hist_kernel<<<(unsigned)std::min<int64_t>(ntile * 2, 152 * 4), 256, 0, s>>>(k0, n_dev, n_max,
                                                                              hp, ghist);
   const bool small = os_items(n_max) == kOsItemsSmall;
+  const uint32_t spin = g_spin_limit.load(std::memory_order_relaxed);
   bool flipped = false;
   for (int p = 0; p < npass; p++) {
     if (small)
       onesweep_kernel<kOsItemsSmall><<<(unsigned)ntile, kOsThreads, 0, s>>>(
           k0, v0, k1, v1, n_dev, n_max, hp.shift[p], hp.mask[p], ghist + p * kRadix, status[p],
-          counters + p);
+          counters + p, spin);
     else
       onesweep_kernel<kOsItems><<<(unsigned)ntile, kOsThreads, 0, s>>>(
           k0, v0, k1, v1, n_dev, n_max, hp.shift[p], hp.mask[p], ghist + p * kRadix, status[p],
-          counters + p);
+          counters + p, spin);
     std::swap(k0, k1);
     std::swap(v0, v1);
     flipped = !flipped;
@@ -303,10 +314,16 @@ bool sort_pairs(uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t* v1, int64_t 
 }  // namespace lgs
 
 namespace lgs {
-unsigned sort_error_word() {
+unsigned sort_error_word(bool clear) {
   unsigned v = 0, zero = 0;
   if (cudaMemcpyFromSymbol(&v, g_sort_error, sizeof(v)) != cudaSuccess) return 0;
-  cudaMemcpyToSymbol(g_sort_error, &zero, sizeof(zero));
+  if (clear && v) cudaMemcpyToSymbol(g_sort_error, &zero, sizeof(zero));
   return v;
 }
 }  // namespace lgs
+
+extern "C" void lgs_set_sort_wait_limit(int64_t polls) {
+  const uint32_t v = polls <= 0 ? lgs::kSpinLimit
+                                : (uint32_t)std::min<int64_t>(polls, (int64_t)0xffffffff);
+  lgs::g_spin_limit.store(v, std::memory_order_relaxed);
+}

@@ -15,11 +15,17 @@
 // (16 MiB); every GPU on which the library is loaded holds it until the
 // process exits.  Host code cannot use the symbol's name as a device address,
 // so the first call on each device looks the address up with
-// cudaGetSymbolAddress (with that device current) and caches it; that first
-// call should therefore come before any stream capture.  Every call shares
-// the array and leaves its last contents behind: the wrapped call zeroes the
-// part it uses before accumulating, and two calls whose work overlaps on the
-// GPU (different streams, no ordering) race on it.
+// cudaGetSymbolAddress (with that device current) and caches it together
+// with the unique ID of the device's current context; that first call should
+// therefore come before any stream capture.  A later call in another context
+// of the device (after cudaDeviceReset, the array is loaded anew) looks the
+// address up again, and should likewise not be the first call inside a
+// capture.  Every call shares the array and leaves its last contents behind:
+// the wrapped call zeroes the part it uses before accumulating, and two
+// calls whose work overlaps on the GPU (different streams, no ordering) race
+// on it.
+#include <cuda.h>
+
 #include <mutex>
 
 #include "common.cuh"
@@ -34,17 +40,48 @@ __device__ __align__(256) float g_static_grad2d[kStaticRecords * LGS_PROJ_STRIDE
 
 static std::mutex g_static_mu;
 static float* g_static_ptr[kMaxDevices];
+static unsigned long long g_static_ctx[kMaxDevices];  // context the address belongs to
 
-// Device address of g_static_grad2d on the current device (looked up once).
+// Unique ID of the calling thread's current context (0: none is current, or
+// the driver entry points are unavailable).
+static unsigned long long current_context_id() {
+  using GetCurrent = CUresult (*)(CUcontext*);
+  using GetId = CUresult (*)(CUcontext, unsigned long long*);
+  static GetCurrent get_current = nullptr;
+  static GetId get_id = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    cudaDriverEntryPointQueryResult q;
+    void* p = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 4000, cudaEnableDefault, &q) ==
+            cudaSuccess && q == cudaDriverEntryPointSuccess)
+      get_current = reinterpret_cast<GetCurrent>(p);
+    p = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess && q == cudaDriverEntryPointSuccess)
+      get_id = reinterpret_cast<GetId>(p);
+  });
+  CUcontext ctx = nullptr;
+  unsigned long long id = 0;
+  if (!get_current || !get_id || get_current(&ctx) != CUDA_SUCCESS || !ctx ||
+      get_id(ctx, &id) != CUDA_SUCCESS)
+    return 0;
+  return id;
+}
+
+// Device address of g_static_grad2d on the current device, looked up on the
+// first call and again when the device's current context has changed.
 static lgs_status static_scratch(float** out) {
   int dev = -1;
   LGS_CHECK_CUDA(cudaGetDevice(&dev));
   LGS_CHECK_ARG(dev >= 0 && dev < kMaxDevices, "device index out of range");
   std::lock_guard<std::mutex> lock(g_static_mu);
-  if (g_static_ptr[dev] == nullptr) {
+  const unsigned long long ctx = current_context_id();
+  if (g_static_ptr[dev] == nullptr || ctx == 0 || ctx != g_static_ctx[dev]) {
     void* p = nullptr;
-    LGS_CHECK_CUDA(cudaGetSymbolAddress(&p, g_static_grad2d));
+    LGS_CHECK_CUDA(cudaGetSymbolAddress(&p, g_static_grad2d));  // makes the context current
     g_static_ptr[dev] = static_cast<float*>(p);
+    g_static_ctx[dev] = current_context_id();
   }
   *out = g_static_ptr[dev];
   return LGS_OK;

@@ -20,12 +20,19 @@ MAX_CAMS = 16
 TILE = 16
 PROJ_STRIDE = 8
 F32, BF16 = 0, 1
+# lgs_status
+OK, ERR_INVALID, ERR_CAPACITY, ERR_NONFINITE, ERR_TIMEOUT, ERR_CUDA = 0, 1, 2, 3, 4, 5
 
 _lib = None
 
 
 class LgsError(RuntimeError):
-    """A liblgs call returned a non-zero lgs_status."""
+    """A liblgs call returned a non-zero lgs_status (``status``; ``detail``
+    for a device-side error reported by lgs_sync_status)."""
+
+    def __init__(self, msg, status=None, detail=None):
+        super().__init__(msg)
+        self.status, self.detail = status, detail
 
 
 AE_LAYERS = 8
@@ -84,6 +91,8 @@ def load():
         "ae_train_step": ([P, P, P, I64, I32, F, P, P, SZ, P], I32),
         "ae_pack": ([P, I32, I32, P], I32),
         "lgs_device_error": ([P], I32),
+        "lgs_sync_status": ([P, P], I32),
+        "lgs_set_sort_wait_limit": ([I64], None),
         "lgs_graph_kernel_nodes": ([P], I64),
         "lgs_zero": ([P, SZ, P], I32),
         "gs_render_bwd_static_capacity": ([], I64),
@@ -115,7 +124,8 @@ def exported_symbols():
     """Names of the C entry points this binding declares."""
     return ["lgs_version", "lgs_last_error", "gs_project", "gs_bin_sort_workspace", "gs_bin_sort",
             "gs_render_fwd", "gs_render_bwd", "lgs_l1_loss", "ae_workspace_bytes", "ae_encode",
-            "ae_decode", "ae_train_step", "ae_pack", "lgs_device_error", "lgs_graph_kernel_nodes", "lgs_zero",
+            "ae_decode", "ae_train_step", "ae_pack", "lgs_device_error", "lgs_sync_status",
+            "lgs_set_sort_wait_limit", "lgs_graph_kernel_nodes", "lgs_zero",
             "gs_render_bwd_static_capacity", "gs_render_bwd_static", "gs_prune_workspace",
             "gs_prune", "gs_compact_workspace", "gs_compact_index", "gs_gather_rows",
             "lgs_dssim_workspace", "lgs_dssim_loss", "gs_pose_grad", "lgs_codebook_workspace",
@@ -126,7 +136,7 @@ def exported_symbols():
 def _check(status, what):
     if status != 0:
         msg = load().lgs_last_error().decode()
-        raise LgsError(f"{what} failed with status {status}: {msg}")
+        raise LgsError(f"{what} failed with status {status}: {msg}", status)
 
 
 def _p(t):
@@ -350,6 +360,31 @@ def lgs_device_error():
     _check(load().lgs_device_error(ctypes.byref(code)), "lgs_device_error")
     return code.value
 
+
+
+def lgs_sync_status(stream=None):
+    """(status, detail) of the device-side work: synchronises the current
+    stream (or ``stream``) and returns one recorded error and its detail,
+    clearing it (OK, 0 when none is pending)."""
+    lib = load()
+    d = ctypes.c_int64(0)
+    st = lib.lgs_sync_status(_stream() if stream is None else stream, ctypes.byref(d))
+    return int(st), int(d.value)
+
+
+def check_device(what="device work"):
+    """Raises LgsError for every error the device recorded (after
+    synchronising the current stream)."""
+    st, detail = lgs_sync_status()
+    if st != OK:
+        msg = load().lgs_last_error().decode()
+        raise LgsError(f"{what}: status {st} (detail {detail}): {msg}", st, detail)
+
+
+def lgs_set_sort_wait_limit(polls):
+    """Polling rounds before the pruning sort's look-back gives up (<= 0:
+    the default)."""
+    load().lgs_set_sort_wait_limit(int(polls))
 
 def prune_params(lo, hi, k=8, tau_dist=0.05, tau_sim=0.9, min_opacity=0.005,
                  max_scale=float("inf")):

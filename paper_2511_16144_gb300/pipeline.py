@@ -176,6 +176,16 @@ class MappingStep:
         main.wait_event(join)
         part["backward"]()
 
+    def check(self):
+        """Synchronises the current stream and raises LgsError for an error
+        the device recorded while running the step: above all
+        LGS_ERR_CAPACITY when a frame needs more instances than the bin
+        buffer (sized once, from the first frame) holds -- its ranges are
+        then empty and the step renders background with zero gradients --
+        with the count it needs as ``detail`` (rebuild the step with that
+        capacity)."""
+        lgs.check_device("mapping step")
+
     def count_blended(self):
         """Number blended per pixel for the last forward (re-runs the forward
         with the counting output)."""

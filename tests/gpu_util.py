@@ -35,3 +35,17 @@ def grad_close(g, ref, rel=1e-3, name=""):
     bad = np.abs(g - ref) > rel * np.maximum(np.abs(ref), floor)
     assert bad.mean() <= 1e-3, f"{name}: {bad.sum()} of {bad.size} entries off"
     return err / max(nr, 1e-30)
+
+
+def decided_target(dec_rounded, z_rounded, rng, delta=0.05):
+    """An F_gt for the gradient of Eq. 2 whose every sign(y - F_gt) is
+    decided with room to spare: F_gt = y* - s delta, with y* the oracle's
+    decoder output for z and s a random sign, rounded to BF16.  The L1
+    gradient is a sign, so wherever |y - F_gt| is below the rounding of the
+    BF16 activations (about 4e-3 |y|) the GPU and the oracle may take
+    opposite signs at a tie; with this target every difference is near
+    delta, and dz compares the arithmetic alone."""
+    from oracle import ae
+    y = ae.decode(dec_rounded, z_rounded)
+    s = rng.choice(np.array([-1.0, 1.0]), size=y.shape)
+    return bf16_round(y - s * delta)

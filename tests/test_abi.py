@@ -21,7 +21,7 @@ def declared_symbols():
     for h in sorted(os.listdir(os.path.join(ROOT, "include"))):
         if h.endswith(".h"):
             text = open(os.path.join(ROOT, "include", h)).read()
-            names += re.findall(r"^(?:lgs_status|size_t|int64_t|const char\*)\s+(\w+)\s*\(",
+            names += re.findall(r"^(?:lgs_status|size_t|int64_t|void|const char\*)\s+(\w+)\s*\(",
                                 text, re.M)
     return names
 
@@ -70,6 +70,15 @@ def test_host_argument_checks(lib_path):
     assert lib.gs_bin_sort_workspace(1000, 2, 40, 30, 100000) > 0
     # an empty call is a no-op that succeeds
     assert lib.lgs_l1_loss(None, None, 0, 0, 1.0, None, None, None) == 0
+    # a camera with a NaN or an infinite value is refused on the host
+    for field, bad in (("cx", float("nan")), ("viewmat", [1, 0, 0, 0, 0, 1, 0, float("inf"),
+                                                           0, 0, 1, 0])):
+        kw = dict(fx=100.0, fy=100.0, cx=32.0, cy=24.0, width=64, height=48,
+                  viewmat=[1, 0, 0, 0, 0, 1, 0, 0, 0, 0, 1, 0], znear=0.2)
+        kw[field] = bad
+        badcam = lgs.cameras([type("C", (), kw)()])
+        assert lib.gs_project(fake, fake, fake, fake, 10, badcam, 1, fake, fake, None) == 3
+        assert b"non-finite" in lib.lgs_last_error()
 
 
 def test_prune_host_argument_checks(lib_path):
@@ -102,3 +111,22 @@ def test_prune_host_argument_checks(lib_path):
     assert lib.gs_gather_rows(odd2, 10, 8, fake, fake, None) == 1
     assert lib.gs_gather_rows(None, 0, 12, None, None, None) == 0
     assert lib.gs_compact_index(fake, 10, fake, fake, fake, 8, None) == 1
+
+
+def test_status_codes_without_a_device(lib_path):
+    """lgs_sync_status reports a failed synchronisation as LGS_ERR_CUDA (here:
+    no device) with detail 0; the wait-limit hook takes any value."""
+    from paper_2511_16144_gb300 import lgs
+    lib = lgs.load()
+    d = ctypes.c_int64(-7)
+    assert lib.lgs_sync_status(None, ctypes.byref(d)) == 5
+    assert d.value == 0
+    assert lib.lgs_sync_status(None, None) == 5
+    lib.lgs_set_sort_wait_limit(3)
+    lib.lgs_set_sort_wait_limit(0)
+    assert (lgs.OK, lgs.ERR_INVALID, lgs.ERR_CAPACITY, lgs.ERR_NONFINITE, lgs.ERR_TIMEOUT,
+            lgs.ERR_CUDA) == (0, 1, 2, 3, 4, 5)
+    text = open(os.path.join(ROOT, "include", "lgs.h")).read()
+    for name, v in (("LGS_OK", 0), ("LGS_ERR_INVALID", 1), ("LGS_ERR_CAPACITY", 2),
+                    ("LGS_ERR_NONFINITE", 3), ("LGS_ERR_TIMEOUT", 4), ("LGS_ERR_CUDA", 5)):
+        assert re.search(rf"{name}\s*=\s*{v}\b", text), name

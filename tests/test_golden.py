@@ -54,6 +54,42 @@ def test_eq4_inequalities_are_strict():
                         **kw).tolist() == [0, 2]
 
 
+def _bias_only(widths, rng):
+    """Layers with zero weights and random biases: the network's output is
+    the last bias whatever the input, so a loss on it has a closed form."""
+    return [[np.zeros((b, a)), rng.standard_normal(b)] for a, b in zip(widths[:-1], widths[1:])]
+
+
+def test_eq2_and_eq3_are_l1_losses():
+    """Eq. 2 (distillation through the decoder) and Eq. 3 (encoder
+    adaptation) as the oracle computes them are the mean absolute error, with
+    the sign as gradient: checked on two pixels where the networks reduce to
+    their last bias (the L2 value differs, so a squared loss would fail)."""
+    from oracle import ae
+    c = _json("paper_constants.json")
+    assert c["distillation_loss"]["value"] == "L1"
+    assert c["encoder_adaptation_loss"]["value"] == "L1"
+    rng = np.random.default_rng(5)
+    dec = _bias_only((16, 64, 128, 256, 512), rng)
+    enc = _bias_only((512, 256, 128, 64, 16), rng)
+    f_render = rng.standard_normal((2, 16))
+    f_gt = rng.standard_normal((2, 512))
+    loss, dz = ae.distill(dec, f_render, f_gt)
+    y = dec[-1][1]
+    assert np.isclose(loss, np.abs(y[None] - f_gt).mean(), rtol=1e-14, atol=0)
+    assert not np.isclose(loss, ((y[None] - f_gt) ** 2).mean())
+    assert np.all(dz == 0)  # nothing reaches z through zero weights
+    x = rng.standard_normal((2, 512))
+    state = ae.new_state(enc, dec)
+    loss3, grads = ae.train_step(enc, dec, state, x, f_render, "enc_adapt", lr=0.0)
+    z = enc[-1][1]
+    assert np.isclose(loss3, np.abs(z[None] - f_render).mean(), rtol=1e-14, atol=0)
+    # the latent bias gradient: the sum over pixels of sign(z - F_render) / (2 * 16)
+    np.testing.assert_allclose(grads[3][1], np.sign(z[None] - f_render).sum(0) / 32.0,
+                               rtol=1e-14, atol=0)
+    assert all(g is None for g in grads[4:])  # the decoder is frozen in Eq. 3
+
+
 def _compare(got, ref, path="fixture"):
     if isinstance(ref, dict):
         assert set(got) >= set(ref) - {"_about"}, path

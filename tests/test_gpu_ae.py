@@ -6,11 +6,14 @@ import pytest
 import torch
 
 from paper_2511_16144_gb300 import synth
-from tests.gpu_util import bf16_round
+from tests.gpu_util import bf16_round, decided_target
 
 pytestmark = pytest.mark.gpu
 
 REL = 1e-2  # norm-relative: BF16 activations between layers, FP32 accumulation
+# weight and bias gradients, norm-relative per layer: the measured errors are
+# 1e-4 to 1.3e-3, so this is a few times the BF16 rounding they carry
+GREL = 5e-3
 
 
 @pytest.fixture(scope="module")
@@ -88,10 +91,18 @@ def test_decode_and_distillation_match_oracle(lgs):
     zr = bf16_round(z)  # the GPU feeds z to the first GEMM as BF16
     yr = ae.decode(rounded(dec), zr)
     assert rel_err(y, yr) < REL
+    # Eq. 2 against embedding targets: the loss (its gradient is a sign, so
+    # ties between y and F_gt are compared below with a decided target)
     loss, dz = model.distill(zt, torch.from_numpy(t).cuda().bfloat16(), weight=0.7)
     lr_, dzr = ae.distill(rounded(dec), zr, bf16_round(t))
     assert abs(loss.item() - 0.7 * lr_) <= 1e-3 * 0.7 * lr_
-    assert rel_err(dz.cpu().numpy(), 0.7 * dzr) < 2 * REL
+    td = decided_target(rounded(dec), zr, rng)
+    loss, dz = model.distill(zt, torch.from_numpy(td).cuda().bfloat16(), weight=0.7)
+    lr_, dzr = ae.distill(rounded(dec), zr, td)
+    assert abs(loss.item() - 0.7 * lr_) <= 1e-3 * 0.7 * lr_
+    e = rel_err(dz.cpu().numpy(), 0.7 * dzr)
+    print(f"dz rel err {e:.2e}")
+    assert e < REL, e
 
 
 def test_fused_distillation_many_tiles(lgs):
@@ -108,7 +119,14 @@ def test_fused_distillation_many_tiles(lgs):
     loss, dz = model.distill(torch.from_numpy(z).cuda(), torch.from_numpy(t).cuda().bfloat16())
     l_ref, dz_ref = ae.distill(rounded(dec), bf16_round(z), bf16_round(t))
     assert abs(loss.item() - l_ref) <= 1e-3 * l_ref
-    assert rel_err(dz.cpu().numpy(), dz_ref) < 2 * REL
+    # dz with every sign of Eq. 2's gradient decided (see decided_target)
+    t = decided_target(rounded(dec), bf16_round(z), rng)
+    loss, dz = model.distill(torch.from_numpy(z).cuda(), torch.from_numpy(t).cuda().bfloat16())
+    l_ref, dz_ref = ae.distill(rounded(dec), bf16_round(z), t)
+    assert abs(loss.item() - l_ref) <= 1e-3 * l_ref
+    e = rel_err(dz.cpu().numpy(), dz_ref)
+    print(f"fused dz rel err {e:.2e}")
+    assert e < REL, e
     # a second call on the same workspace gives the same answer
     loss2, dz2 = model.distill(torch.from_numpy(z).cuda(), torch.from_numpy(t).cuda().bfloat16())
     assert abs(loss2.item() - loss.item()) <= 1e-5 * loss.item()
@@ -142,8 +160,10 @@ def test_train_step_gradients_and_update(lgs, mode):
             assert g_ref[l] is None
             torch.testing.assert_close(model.W[l], W0[l], rtol=0, atol=0)
             continue
-        assert rel_err(gW, g_ref[l][0]) < 3 * REL, (l, rel_err(gW, g_ref[l][0]))
-        assert rel_err(gb, g_ref[l][1]) < 3 * REL, (l, rel_err(gb, g_ref[l][1]))
+        ew, eb = rel_err(gW, g_ref[l][0]), rel_err(gb, g_ref[l][1])
+        print(f"{mode} layer {l}: dW {ew:.2e} db {eb:.2e}")
+        assert ew < GREL, (l, ew)
+        assert eb < GREL, (l, eb)
         # first Adam step: W1 = W0 - lr g / (|g| + eps), from the GPU's own gradient
         g = model.gW[l]
         exp = W0[l] - 1e-3 * g / (g.abs() + 1e-8)
@@ -174,8 +194,35 @@ def test_train_step_full_batch(lgs):
                                  lr=0.0)
     assert abs(loss.item() - l_ref) <= 1e-2 * abs(l_ref)
     for l in range(8):
-        assert rel_err(model.gW[l].cpu().numpy(), g_ref[l][0]) < 3 * REL, l
-        assert rel_err(model.gb[l].cpu().numpy(), g_ref[l][1]) < 3 * REL, l
+        ew = rel_err(model.gW[l].cpu().numpy(), g_ref[l][0])
+        eb = rel_err(model.gb[l].cpu().numpy(), g_ref[l][1])
+        print(f"full batch layer {l}: dW {ew:.2e} db {eb:.2e}")
+        assert ew < GREL, (l, ew)
+        assert eb < GREL, (l, eb)
+    assert lgs.lgs_device_error() == 0
+
+
+def test_training_is_bit_reproducible(lgs):
+    """The weight gradients are summed in a fixed order, so two runs from
+    the same initial weights on the same batches end bit-identical (both
+    modes, a ragged pixel count and the benchmark's batch)."""
+    from paper_2511_16144_gb300.ae import AutoEncoder
+    enc, dec = synth.ae_init(seed=3010)
+    rng = np.random.default_rng(12)
+    batches = [torch.from_numpy(synth.unit_rows(rng.standard_normal((P, 512))).astype(np.float32))
+               .cuda().bfloat16() for P in (65536, 9001, 65536)]
+    target = torch.from_numpy(rng.standard_normal((9001, 16)).astype(np.float32)).cuda()
+    runs = []
+    for _ in range(2):
+        model = AutoEncoder(enc, dec)
+        losses = [model.train_step(batches[0], lr=1e-3),
+                  model.train_step(batches[1], target, mode=lgs.AE_ENC_ADAPT, lr=1e-3),
+                  model.train_step(batches[2], lr=1e-3)]
+        torch.cuda.synchronize()
+        runs.append(([w.clone() for w in model.W] + [b.clone() for b in model.b] +
+                     [g.clone() for g in model.gW], [float(l.item()) for l in losses]))
+    for a, b in zip(runs[0][0], runs[1][0]):
+        assert torch.equal(a, b)
     assert lgs.lgs_device_error() == 0
 
 

@@ -4,7 +4,7 @@ Setup (the benchmark's frame): 300k Gaussians in the 6x6x3 m room with
 spatially coherent 512-d semantics (64 3D Voronoi cells); the plain path
 renders all 512 channels for 8 keyframes at 640x480, and those rendered maps
 are the autoencoder's online training data (200 Adam steps of 64k pixels,
-lr 3e-3, L2 + (1 - cos)).  The Gaussians' 16-d features are the encoder prior
+lr 5e-3, L2 + (1 - cos)).  The Gaussians' 16-d features are the encoder prior
 E(g_i) (Sec. III-B.2); the 16-d render is decoded by D and compared with the
 plain 512-channel render pixel by pixel (1 - cos over pixels with a
 non-zero reference).
@@ -53,7 +53,7 @@ def train_ae(frames, seed, steps=200):
     gen = torch.Generator(device="cuda").manual_seed(seed)
     for _ in range(steps):
         idx = torch.randint(0, data.shape[0], (65536,), device="cuda", generator=gen)
-        model.train_step(data[idx].contiguous(), lr=3e-3)
+        model.train_step(data[idx].contiguous(), lr=5e-3)
     return model
 
 
@@ -102,8 +102,8 @@ def test_trained_autoencoder_gain():
                       for c, ref in zip(cams[::3], frames[::3])])
     print(f"decoded cosine error: trained {trained:.4f}; untrained {untrained:.4f}, "
           f"linear+pinv {linear:.4f}, other-scene encoder {frozen:.4f}")
-    # the absolute bound leaves room for run-to-run spread: the weight-gradient
-    # partial sums are added atomically in no fixed order, so the trained
-    # model differs slightly between runs (0.019-0.020 seen on one build)
-    assert trained <= 0.025, trained
+    # the target of the learned part: mean (1 - cos) of the decoded 16-d
+    # render against the plain 512-channel render at most 0.02 (training is
+    # bit-reproducible, so this is one fixed number per build)
+    assert trained <= 0.02, trained
     assert trained < 0.1 * min(untrained, linear, frozen)

@@ -16,9 +16,10 @@
 //      (a block reserves one range per tile, then fills it with shared-
 //      memory atomics; the order inside a segment is arbitrary);
 //   4. one block per tile sorts its segment's 64-bit (depth bits, index)
-//      keys with a stable LSD radix sort -- in shared memory up to kSegMax
-//      keys, chunk by chunk from global memory beyond -- and writes the
-//      Gaussian indices.
+//      keys with a stable LSD radix sort in shared memory and writes the
+//      Gaussian indices: 256-thread blocks take the segments of up to 4,096
+//      keys, 1024-thread blocks the longer ones (listed by step 2) up to
+//      12,288 keys, and chunk by chunk from global memory beyond.
 // Depths are positive floats, so their bit patterns order like the values.
 #include <algorithm>
 
@@ -33,20 +34,27 @@ __device__ unsigned long long g_capacity_k;
 
 namespace {
 
-constexpr int kSegMax = 4096;          // keys a block sorts in shared memory
+constexpr int kSegMax = 4096;          // keys a 256-thread block sorts in shared memory
 constexpr int kSegThreads = 256;
+constexpr int kLargeThreads = 1024;    // blocks for the longer segments
+constexpr int kLargeItems = 12;        // keys per thread: 12,288 in shared memory
+constexpr int kLargeBlocks = 2 * 152;  // persistent grid over the list of long segments
 constexpr int kSmemTiles = 32768;      // per-block tile tables (4 B each) up to this many tiles
 constexpr int kItemBlocks = 2 * 152;   // blocks of the count and emit passes
 constexpr int kScanThreads = 1024;
 
 __device__ __forceinline__ bool rect_empty(const ushort4& r) { return r.z <= r.x || r.w <= r.y; }
 
-// Items of block b: a contiguous chunk, so a block's per-tile tables cover
-// few tiles densely.
-__device__ __forceinline__ void item_chunk(int64_t m, int64_t& i0, int64_t& i1) {
-  const int64_t per = (m + gridDim.x - 1) / gridDim.x;
-  i0 = (int64_t)blockIdx.x * per;
-  i1 = i0 + per < m ? i0 + per : m;
+// Items of block b, camera by camera: for camera c, chunk b of that
+// camera's n items [c n, (c + 1) n).  A block's per-tile tables so cover few
+// tiles densely, and all blocks emit into the tiles of one camera at a time:
+// the segments being filled stay within L2, which merges the scattered
+// 8-byte writes into whole sectors before they reach DRAM.
+__device__ __forceinline__ void cam_chunk(uint32_t n, uint32_t c, int64_t& i0, int64_t& i1) {
+  const int64_t per = ((int64_t)n + gridDim.x - 1) / gridDim.x;
+  const int64_t a = (int64_t)blockIdx.x * per;
+  i0 = (int64_t)c * n + (a < (int64_t)n ? a : (int64_t)n);
+  i1 = (int64_t)c * n + (a + per < (int64_t)n ? a + per : (int64_t)n);
 }
 
 // 1. per-tile instance counts and K.
@@ -61,19 +69,22 @@ tile_count_kernel(const ushort4* __restrict__ rect, int64_t m, uint32_t n, int t
     __syncthreads();
   }
   unsigned long long k = 0;
-  int64_t i0, i1;
-  item_chunk(m, i0, i1);
-  for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
-    const ushort4 r = rect[i];
-    if (rect_empty(r)) continue;
-    const uint32_t base = (uint32_t)(i / n) * tiles;
-    for (uint32_t y = r.y; y < r.w; y++)
-      for (uint32_t x = r.x; x < r.z; x++) {
-        const uint32_t t = base + y * (uint32_t)tiles_x + x;
-        if (local) atomicAdd(&s_cnt[t], 1u);
-        else atomicAdd(&counts[t], 1u);
-      }
-    k += (unsigned long long)(r.z - r.x) * (r.w - r.y);
+  const uint32_t n_cams = (uint32_t)(m / n);
+  for (uint32_t c = 0; c < n_cams; c++) {
+    int64_t i0, i1;
+    cam_chunk(n, c, i0, i1);
+    const uint32_t base = c * tiles;
+    for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
+      const ushort4 r = rect[i];
+      if (rect_empty(r)) continue;
+      for (uint32_t y = r.y; y < r.w; y++)
+        for (uint32_t x = r.x; x < r.z; x++) {
+          const uint32_t t = base + y * (uint32_t)tiles_x + x;
+          if (local) atomicAdd(&s_cnt[t], 1u);
+          else atomicAdd(&counts[t], 1u);
+        }
+      k += (unsigned long long)(r.z - r.x) * (r.w - r.y);
+    }
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) k += __shfl_xor_sync(0xffffffffu, k, o);
@@ -93,7 +104,8 @@ __global__ void __launch_bounds__(kScanThreads)
 tile_scan_kernel(const uint32_t* __restrict__ counts, uint32_t n_tiles_all,
                  const unsigned long long* __restrict__ total, int64_t capacity,
                  uint2* __restrict__ ranges, uint32_t* __restrict__ cursor,
-                 int64_t* __restrict__ n_instances, int64_t* __restrict__ sort_n) {
+                 int64_t* __restrict__ n_instances, int64_t* __restrict__ sort_n,
+                 uint32_t* __restrict__ long_tiles, uint32_t* __restrict__ n_long) {
   __shared__ uint32_t ws[32];
   __shared__ uint32_t carry;
   const int64_t K = (int64_t)*total;
@@ -132,6 +144,7 @@ tile_scan_kernel(const uint32_t* __restrict__ counts, uint32_t n_tiles_all,
       const uint32_t start = incl - v;
       ranges[t] = fits && v ? make_uint2(start, incl) : make_uint2(0u, 0u);
       cursor[t] = start;
+      if (fits && v > (uint32_t)kSegMax) long_tiles[atomicAdd(n_long, 1u)] = t;
     }
     __syncthreads();
     if (threadIdx.x == kScanThreads - 1) carry = incl;
@@ -179,26 +192,29 @@ tile_emit_kernel(const float4* __restrict__ proj, const ushort4* __restrict__ re
   extern __shared__ uint32_t s_cur[];  // [n_tiles_all] next slot of this block
   if (*sort_n == 0) return;  // nothing fits (or nothing visible)
   const bool local = n_tiles_all <= (uint32_t)kSmemTiles;
-  int64_t i0, i1;
-  item_chunk(m, i0, i1);
   if (local) {
     for (uint32_t t = threadIdx.x; t < n_tiles_all; t += blockDim.x)
       s_cur[t] = block_base[(size_t)t * gridDim.x + blockIdx.x];
     __syncthreads();
   }
-  for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
-    const ushort4 r = rect[i];
-    if (rect_empty(r)) continue;
-    const uint32_t c = (uint32_t)(i / n);
+  const uint32_t n_cams = (uint32_t)(m / n);
+  for (uint32_t c = 0; c < n_cams; c++) {
+    int64_t i0, i1;
+    cam_chunk(n, c, i0, i1);
     const uint32_t base = c * tiles;
-    const unsigned long long key =
-        ((unsigned long long)__float_as_uint(proj[2 * i + 1].z) << 32) | (uint32_t)(i - (int64_t)c * n);
-    for (uint32_t y = r.y; y < r.w; y++)
-      for (uint32_t x = r.x; x < r.z; x++) {
-        const uint32_t t = base + y * (uint32_t)tiles_x + x;
-        const uint32_t pos = local ? atomicAdd(&s_cur[t], 1u) : atomicAdd(&cursor[t], 1u);
-        seg[pos] = key;
-      }
+    for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
+      const ushort4 r = rect[i];
+      if (rect_empty(r)) continue;
+      const unsigned long long key =
+          ((unsigned long long)__float_as_uint(proj[2 * i + 1].z) << 32) |
+          (uint32_t)(i - (int64_t)c * n);
+      for (uint32_t y = r.y; y < r.w; y++)
+        for (uint32_t x = r.x; x < r.z; x++) {
+          const uint32_t t = base + y * (uint32_t)tiles_x + x;
+          const uint32_t pos = local ? atomicAdd(&s_cur[t], 1u) : atomicAdd(&cursor[t], 1u);
+          seg[pos] = key;
+        }
+    }
   }
 }
 
@@ -222,31 +238,49 @@ __device__ __forceinline__ uint32_t digit_peers(uint32_t d) {
   return peers;
 }
 
-// 4. one block per tile sorts its segment of 64-bit (depth bits, index)
-// keys.  Up to kSegMax keys: a stable LSD radix sort in shared memory, 8 bits
-// a pass, skipping the digits all keys share; each warp holds R consecutive
-// runs of 32 keys (R = keys / 512 rounded up), ranks them per digit with
-// match-any in position order, and a per-digit scan over the warps places
-// them.  Longer segments are sorted the same way from global memory (below).
-constexpr int kSegWarps = kSegThreads / 32;
-constexpr int kSegItems = kSegMax / kSegThreads;
+// 4. each segment of 64-bit (depth bits, index) keys is sorted by one block:
+// a stable LSD radix sort, 8 bits a pass, skipping the digits all keys share;
+// each warp holds R consecutive runs of 32 keys, ranks them per digit with
+// per-bit ballots in position order, and a per-digit scan over the warps
+// places them.  Segments of up to kSegMax keys are sorted by 256-thread
+// blocks, one per tile; longer ones by 1024-thread blocks that take them from
+// a list (kLargeMax keys in shared memory), and the rare segment beyond that
+// the same way from global memory.
+template <int T, int I>
+struct SegSmem {
+  static constexpr int W = T / 32;
+  static constexpr int G = W / 8;  // groups of 8 warps (T = 256 G threads)
+  static constexpr int MAXK = T * I;
+  unsigned long long sk[T * I];
+  uint16_t wcnt[W][256];  // counts, then offsets (<= MAXK < 2^16)
+  uint32_t gsum[G][256];  // per digit, the count of each group of 8 warps
+  uint32_t dstart[256];
+  uint32_t wsum[8];
+  unsigned long long s_or[W], s_and[W], s_max[W];
+};
+// Equal depths in a sorted segment form runs that are ordered by index in
+// place when no run is longer than this; otherwise the segment is sorted
+// again on all eight digits.
+constexpr int kRunMax = 32;
+static_assert(kSegMax < 65536 && kLargeThreads * kLargeItems < 65536, "wcnt is 16-bit");
 
-// Segments over kSegMax keys: the same stable LSD radix sort with the keys in
-// global memory (ping-pong between the segment and its scratch copy, both
-// L2-resident).  Each pass counts the digit over the whole segment, then
-// scatters it kSegMax keys at a time in position order: within a chunk the
-// warps rank their keys as above, and running per-digit offsets carry over
-// from chunk to chunk, which keeps the pass stable.
-__device__ __noinline__ void big_segment_sort(unsigned long long* src, unsigned long long* dst, uint32_t cnt,
-                                 uint32_t tile, uint32_t* __restrict__ ids,
-                                 uint64_t* __restrict__ keys_opt, uint16_t (*wcnt)[256],
-                                 uint32_t* dstart, uint32_t* wsum, unsigned long long* s_or,
-                                 unsigned long long* s_and, uint32_t* tab) {
+// Segments longer than a block's shared memory: the same stable LSD radix
+// sort with the keys in global memory (ping-pong between the segment and its
+// scratch copy, both L2-resident).  Each pass counts the digit over the whole
+// segment, then scatters it MAXK keys at a time in position order: within a
+// chunk the warps rank their keys as above, and running per-digit offsets
+// carry over from chunk to chunk, which keeps the pass stable.
+template <int T, int I>
+__device__ __noinline__ void big_segment_sort(unsigned long long* src, unsigned long long* dst,
+                                              uint32_t cnt, uint32_t tile,
+                                              uint32_t* __restrict__ ids,
+                                              uint64_t* __restrict__ keys_opt, SegSmem<T, I>& S) {
+  constexpr int W = T / 32, CH = T * I;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  uint32_t* hist = tab;        // [256] digit counts of the segment
-  uint32_t* run = tab + 256;   // [256] next output slot of each digit
+  uint32_t* hist = reinterpret_cast<uint32_t*>(S.sk);  // [256] digit counts of the segment
+  uint32_t* run = hist + 256;                          // [256] next output slot of each digit
   unsigned long long o = 0, a = ~0ull;
-  for (uint32_t i = threadIdx.x; i < cnt; i += kSegThreads) {
+  for (uint32_t i = threadIdx.x; i < cnt; i += T) {
     o |= src[i];
     a &= src[i];
   }
@@ -256,21 +290,21 @@ __device__ __noinline__ void big_segment_sort(unsigned long long* src, unsigned 
     a &= __shfl_xor_sync(0xffffffffu, a, d);
   }
   if (lane == 0) {
-    s_or[warp] = o;
-    s_and[warp] = a;
+    S.s_or[warp] = o;
+    S.s_and[warp] = a;
   }
   __syncthreads();
   unsigned long long oo = 0, aa = ~0ull;
-  for (int w = 0; w < kSegWarps; w++) {
-    oo |= s_or[w];
-    aa &= s_and[w];
+  for (int w = 0; w < W; w++) {
+    oo |= S.s_or[w];
+    aa &= S.s_and[w];
   }
   const unsigned long long diff = oo ^ aa;
   auto pass = [&](int shift) {
     if (((diff >> shift) & 0xffull) == 0) return;  // uniform over the block
-    for (int d = threadIdx.x; d < 256; d += kSegThreads) hist[d] = 0;
+    for (int d = threadIdx.x; d < 256; d += T) hist[d] = 0;
     __syncthreads();
-    for (uint32_t i = threadIdx.x; i < cnt; i += kSegThreads)
+    for (uint32_t i = threadIdx.x; i < cnt; i += T)
       atomicAdd(&hist[(uint32_t)(src[i] >> shift) & 0xffu], 1u);
     __syncthreads();
     if (threadIdx.x < 256) {  // exclusive scan of the digit counts
@@ -281,57 +315,57 @@ __device__ __noinline__ void big_segment_sort(unsigned long long* src, unsigned 
         const uint32_t y = __shfl_up_sync(0xffffffffu, x, q);
         if (lane >= q) x += y;
       }
-      if (lane == 31) wsum[warp] = x;
+      if (lane == 31) S.wsum[warp] = x;
       run[threadIdx.x] = x - v;
     }
     __syncthreads();
     if (threadIdx.x < 256) {
       uint32_t add = 0;
-      for (int w = 0; w < warp; w++) add += wsum[w];
+      for (int w = 0; w < warp; w++) add += S.wsum[w];
       run[threadIdx.x] += add;
     }
     __syncthreads();
-    for (uint32_t c0 = 0; c0 < cnt; c0 += kSegMax) {
-      for (int i = threadIdx.x; i < kSegWarps * 256; i += kSegThreads) (&wcnt[0][0])[i] = 0;
+    for (uint32_t c0 = 0; c0 < cnt; c0 += CH) {
+      for (int i = threadIdx.x; i < W * 256; i += T) (&S.wcnt[0][0])[i] = 0;
       __syncthreads();
-      const uint32_t base = c0 + (uint32_t)warp * 32u * kSegItems;
-      unsigned long long key[kSegItems];
-      uint32_t rank[kSegItems];
+      const uint32_t base = c0 + (uint32_t)warp * 32u * I;
+      unsigned long long key[I];
+      uint32_t rank[I];
 #pragma unroll
-      for (int r = 0; r < kSegItems; r++) {
+      for (int r = 0; r < I; r++) {
         const uint32_t p = base + r * 32 + lane;
         const bool valid = p < cnt;
         key[r] = valid ? src[p] : 0ull;
         const uint32_t d = valid ? (uint32_t)(key[r] >> shift) & 0xffu : 256u + lane;
         const uint32_t peers = digit_peers<9>(d);  // lanes past the end stay alone
-        const uint32_t prior = valid ? wcnt[warp][d] : 0u;
+        const uint32_t prior = valid ? S.wcnt[warp][d] : 0u;
         rank[r] = prior + __popc(peers & lane_lt());
         __syncwarp();
-        if (valid && lane == __ffs(peers) - 1) wcnt[warp][d] = (uint16_t)(prior + __popc(peers));
+        if (valid && lane == __ffs(peers) - 1) S.wcnt[warp][d] = (uint16_t)(prior + __popc(peers));
         __syncwarp();
       }
       __syncthreads();
       if (threadIdx.x < 256) {  // per digit: this chunk's warps in order
         const int d = threadIdx.x;
         uint32_t tot = 0;
-        for (int w = 0; w < kSegWarps; w++) {
-          const uint32_t c = wcnt[w][d];
-          wcnt[w][d] = (uint16_t)tot;
+        for (int w = 0; w < W; w++) {
+          const uint32_t c = S.wcnt[w][d];
+          S.wcnt[w][d] = (uint16_t)tot;
           tot += c;
         }
-        dstart[d] = tot;
+        S.dstart[d] = tot;
       }
       __syncthreads();
 #pragma unroll
-      for (int r = 0; r < kSegItems; r++) {
+      for (int r = 0; r < I; r++) {
         const uint32_t p = base + r * 32 + lane;
         if (p < cnt) {
           const uint32_t d = (uint32_t)(key[r] >> shift) & 0xffu;
-          dst[run[d] + wcnt[warp][d] + rank[r]] = key[r];
+          dst[run[d] + S.wcnt[warp][d] + rank[r]] = key[r];
         }
       }
       __syncthreads();
-      if (threadIdx.x < 256) run[threadIdx.x] += dstart[threadIdx.x];
+      if (threadIdx.x < 256) run[threadIdx.x] += S.dstart[threadIdx.x];
       __syncthreads();
     }
     unsigned long long* t = src;
@@ -341,47 +375,35 @@ __device__ __noinline__ void big_segment_sort(unsigned long long* src, unsigned 
   };
   for (int sh = 32; sh < 64; sh += 8) pass(sh);  // depth digits
   bool tie = false;
-  for (uint32_t i = threadIdx.x + 1; i < cnt; i += kSegThreads)
+  for (uint32_t i = threadIdx.x + 1; i < cnt; i += T)
     tie |= (src[i] >> 32) == (src[i - 1] >> 32);
   if (__syncthreads_or(tie))
     for (int sh = 0; sh < 64; sh += 8) pass(sh);  // equal depths: order by index too
-  for (uint32_t i = threadIdx.x; i < cnt; i += kSegThreads) {
+  for (uint32_t i = threadIdx.x; i < cnt; i += T) {
     const unsigned long long key = src[i];
     ids[i] = (uint32_t)key;
     if (keys_opt) keys_opt[i] = ((uint64_t)tile << 32) | (key >> 32);
   }
 }
 
-__global__ void __launch_bounds__(kSegThreads, 3)
-tile_sort_kernel(const uint2* __restrict__ ranges, unsigned long long* __restrict__ seg,
-                 unsigned long long* __restrict__ scratch, uint32_t* __restrict__ ids,
-                 uint64_t* __restrict__ keys_opt) {
-  __shared__ unsigned long long sk[kSegMax];
-  __shared__ uint16_t wcnt[kSegWarps][256];  // counts, then offsets (<= kSegMax)
-  __shared__ uint32_t dstart[256];
-  __shared__ uint32_t wsum[8];
-  __shared__ unsigned long long s_or[kSegWarps], s_and[kSegWarps], s_max[kSegWarps];
-  const uint32_t tile = blockIdx.x;
-  const uint2 rg = ranges[tile];
-  const uint32_t cnt = rg.y - rg.x;
-  if (cnt == 0) return;
+// One segment of cnt <= T * I keys (seg[0, cnt)), sorted in shared memory;
+// writes the Gaussian indices (and the keys) of the sorted order.
+template <int T, int I>
+__device__ void smem_segment_sort(const unsigned long long* __restrict__ seg, uint32_t cnt,
+                                  uint32_t tile, uint32_t* __restrict__ ids,
+                                  uint64_t* __restrict__ keys_opt, SegSmem<T, I>& S) {
+  constexpr int W = T / 32;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  if (cnt > (uint32_t)kSegMax) {
-    big_segment_sort(seg + rg.x, scratch + rg.x, cnt, tile, ids + rg.x,
-                     keys_opt ? keys_opt + rg.x : nullptr, wcnt, dstart, wsum, s_or, s_and,
-                     reinterpret_cast<uint32_t*>(sk));
-    return;
-  }
-  const int R = (int)((cnt + kSegThreads - 1) / kSegThreads);
+  const int R = (int)((cnt + T - 1) / T);
   const uint32_t base = (uint32_t)warp * 32u * (uint32_t)R;  // this warp's first position
-  unsigned long long key[kSegItems];
+  unsigned long long key[I];
   unsigned long long o = 0, a = ~0ull, mx = 0;
 #pragma unroll
-  for (int r = 0; r < kSegItems; r++) {
+  for (int r = 0; r < I; r++) {
     const uint32_t p = base + r * 32 + lane;
     key[r] = 0;
     if (r < R && p < cnt) {
-      key[r] = seg[rg.x + p];
+      key[r] = seg[p];
       o |= key[r];
       a &= key[r];
       mx = key[r] > mx ? key[r] : mx;
@@ -396,18 +418,18 @@ tile_sort_kernel(const uint2* __restrict__ ranges, unsigned long long* __restric
     mx = m2 > mx ? m2 : mx;
   }
   if (lane == 0) {
-    s_or[warp] = o;
-    s_and[warp] = a;
-    s_max[warp] = mx;
+    S.s_or[warp] = o;
+    S.s_and[warp] = a;
+    S.s_max[warp] = mx;
   }
   __syncthreads();
   unsigned long long diff = 0, kmax = 0;
   {
     unsigned long long oo = 0, aa = ~0ull;
-    for (int w = 0; w < kSegWarps; w++) {
-      oo |= s_or[w];
-      aa &= s_and[w];
-      kmax = s_max[w] > kmax ? s_max[w] : kmax;
+    for (int w = 0; w < W; w++) {
+      oo |= S.s_or[w];
+      aa &= S.s_and[w];
+      kmax = S.s_max[w] > kmax ? S.s_max[w] : kmax;
     }
     diff = oo ^ aa;
   }
@@ -415,94 +437,180 @@ tile_sort_kernel(const uint2* __restrict__ ranges, unsigned long long* __restric
   // skipped digit with the real keys and, being later in position, stay
   // behind the real copy in a stable sort
 #pragma unroll
-  for (int r = 0; r < kSegItems; r++)
+  for (int r = 0; r < I; r++)
     if (!(r < R && base + r * 32 + lane < cnt)) key[r] = kmax;
   // one stable pass on the 8-bit digit at `shift` (skipped when every key
   // has the same digit there)
   auto pass = [&](int shift) {
     if (((diff >> shift) & 0xffull) == 0) return;  // uniform over the block
-    for (int i = threadIdx.x; i < kSegWarps * 256; i += kSegThreads) (&wcnt[0][0])[i] = 0;
+    for (int i = threadIdx.x; i < W * 256; i += T) (&S.wcnt[0][0])[i] = 0;
     __syncthreads();
-    uint32_t rank[kSegItems];
+    uint32_t rank[I];
 #pragma unroll
-    for (int r = 0; r < kSegItems; r++) {
+    for (int r = 0; r < I; r++) {
       if (r < R) {  // uniform over the block
         const uint32_t d = (uint32_t)(key[r] >> shift) & 0xffu;
         const uint32_t peers = digit_peers<8>(d);
-        const uint32_t prior = wcnt[warp][d];
+        const uint32_t prior = S.wcnt[warp][d];
         rank[r] = prior + __popc(peers & lane_lt());
         __syncwarp();
-        if (lane == __ffs(peers) - 1) wcnt[warp][d] = (uint16_t)(prior + __popc(peers));
+        if (lane == __ffs(peers) - 1) S.wcnt[warp][d] = (uint16_t)(prior + __popc(peers));
         __syncwarp();
       }
     }
     __syncthreads();
-    if (threadIdx.x < 256) {  // per digit: warps in order, then digits in order
-      const int d = threadIdx.x;
-      uint32_t tot = 0;
-      for (int w = 0; w < kSegWarps; w++) {
-        const uint32_t c = wcnt[w][d];
-        wcnt[w][d] = (uint16_t)tot;
+    // per digit: warps in order -- thread (d, g) takes the 8 warps of group
+    // g, then the groups' offsets are added -- then digits in order
+    constexpr int G = SegSmem<T, I>::G;
+    static_assert(T == 256 * G, "one thread per (digit, group of 8 warps)");
+    uint32_t tot = 0;
+    {
+      const int d = threadIdx.x & 255, gg = threadIdx.x >> 8;
+      for (int w = 8 * gg; w < 8 * gg + 8; w++) {
+        const uint32_t c = S.wcnt[w][d];
+        S.wcnt[w][d] = (uint16_t)tot;
         tot += c;
       }
+      if (G > 1) S.gsum[gg][d] = tot;
+    }
+    if (G > 1) {
+      __syncthreads();
+      const int d = threadIdx.x & 255, gg = threadIdx.x >> 8;
+      uint32_t off = 0;
+      for (int q = 0; q < gg; q++) off += S.gsum[q][d];
+      if (off)
+        for (int w = 8 * gg; w < 8 * gg + 8; w++) S.wcnt[w][d] = (uint16_t)(S.wcnt[w][d] + off);
+      if (gg == 0)
+        for (int q = 1; q < G; q++) tot += S.gsum[q][d];
+    }
+    if (threadIdx.x < 256) {
+      const int d = threadIdx.x;
       uint32_t x = tot;
 #pragma unroll
       for (int q = 1; q < 32; q <<= 1) {
         const uint32_t y = __shfl_up_sync(0xffffffffu, x, q);
         if (lane >= q) x += y;
       }
-      if (lane == 31) wsum[warp] = x;
-      dstart[d] = x - tot;  // exclusive within this warp's 32 digits
+      if (lane == 31) S.wsum[warp] = x;
+      S.dstart[d] = x - tot;  // exclusive within this warp's 32 digits
     }
     __syncthreads();
     if (threadIdx.x < 256) {
       uint32_t add = 0;
-      for (int w = 0; w < warp; w++) add += wsum[w];
-      dstart[threadIdx.x] += add;
+      for (int w = 0; w < warp; w++) add += S.wsum[w];
+      S.dstart[threadIdx.x] += add;
     }
     __syncthreads();
 #pragma unroll
-    for (int r = 0; r < kSegItems; r++)
+    for (int r = 0; r < I; r++)
       if (r < R) {
         const uint32_t d = (uint32_t)(key[r] >> shift) & 0xffu;
-        sk[dstart[d] + wcnt[warp][d] + rank[r]] = key[r];
+        S.sk[S.dstart[d] + S.wcnt[warp][d] + rank[r]] = key[r];
       }
     __syncthreads();
 #pragma unroll
-    for (int r = 0; r < kSegItems; r++)
-      if (r < R) key[r] = sk[base + r * 32 + lane];
+    for (int r = 0; r < I; r++)
+      if (r < R) key[r] = S.sk[base + r * 32 + lane];
     __syncthreads();
   };
-  // the depth digits alone order the keys unless two share a depth; only
-  // then is the segment sorted again on all eight digits (index ones first)
+  // the depth digits alone order the keys unless two share a depth: each run
+  // of equal depths (contiguous now, in emission order) is then put in index
+  // order in place by the thread that holds its first key (an insertion sort
+  // of the full keys), unless some run is longer than kRunMax, in which case
+  // the segment is sorted again on all eight digits (index ones first)
   for (int sh = 32; sh < 64; sh += 8) pass(sh);
 #pragma unroll
-  for (int r = 0; r < kSegItems; r++)  // the current order (also when no pass ran)
-    if (r < R) sk[base + r * 32 + lane] = key[r];
+  for (int r = 0; r < I; r++)  // the current order (also when no pass ran)
+    if (r < R) S.sk[base + r * 32 + lane] = key[r];
   __syncthreads();
-  bool tie = false;
+  bool tie = false, long_run = false;
 #pragma unroll
-  for (int r = 0; r < kSegItems; r++) {
+  for (int r = 0; r < I; r++) {
     const uint32_t p = base + r * 32 + lane;
-    if (r < R && p > 0 && p < cnt) tie |= (key[r] >> 32) == (sk[p - 1] >> 32);
+    if (!(r < R && p < cnt)) continue;
+    const uint32_t dz = (uint32_t)(key[r] >> 32);
+    const bool first = p == 0 || (uint32_t)(S.sk[p - 1] >> 32) != dz;
+    if (!first || p + 1 >= cnt || (uint32_t)(S.sk[p + 1] >> 32) != dz) continue;
+    // a run starts at p: only its depth bits are read by other threads, and
+    // those stay put while it is reordered
+    tie = true;
+    uint32_t e = p + 1;
+    while (e < cnt && e - p <= (uint32_t)kRunMax && (uint32_t)(S.sk[e] >> 32) == dz) e++;
+    if (e - p > (uint32_t)kRunMax) {
+      long_run = true;
+      continue;
+    }
+    for (uint32_t i = p + 1; i < e; i++) {
+      const unsigned long long v = S.sk[i];
+      uint32_t j = i;
+      for (; j > p && S.sk[j - 1] > v; j--) S.sk[j] = S.sk[j - 1];
+      S.sk[j] = v;
+    }
   }
-  if (__syncthreads_or(tie)) {
+  if (__syncthreads_or(long_run)) {
     for (int sh = 0; sh < 64; sh += 8) pass(sh);
+  } else if (__syncthreads_or(tie)) {
+#pragma unroll
+    for (int r = 0; r < I; r++)
+      if (r < R) key[r] = S.sk[base + r * 32 + lane];
   }
 #pragma unroll
-  for (int r = 0; r < kSegItems; r++) {
+  for (int r = 0; r < I; r++) {
     const uint32_t p = base + r * 32 + lane;
     if (r < R && p < cnt) {
-      ids[rg.x + p] = (uint32_t)key[r];
-      if (keys_opt) keys_opt[rg.x + p] = ((uint64_t)tile << 32) | (key[r] >> 32);
+      ids[p] = (uint32_t)key[r];
+      if (keys_opt) keys_opt[p] = ((uint64_t)tile << 32) | (key[r] >> 32);
     }
+  }
+}
+
+// 4a. tiles of at most kSegMax instances, one 256-thread block each (longer
+// ones are left to tile_sort_large_kernel).
+__global__ void __launch_bounds__(kSegThreads, 3)
+tile_sort_kernel(const uint2* __restrict__ ranges, const unsigned long long* __restrict__ seg,
+                 uint32_t* __restrict__ ids, uint64_t* __restrict__ keys_opt) {
+  using SS = SegSmem<kSegThreads, kSegMax / kSegThreads>;
+  extern __shared__ __align__(16) unsigned char seg_smem[];
+  SS& S = *reinterpret_cast<SS*>(seg_smem);
+  const uint32_t tile = blockIdx.x;
+  const uint2 rg = ranges[tile];
+  const uint32_t cnt = rg.y - rg.x;
+  if (cnt == 0 || cnt > (uint32_t)kSegMax) return;
+  smem_segment_sort<kSegThreads, kSegMax / kSegThreads>(seg + rg.x, cnt, tile, ids + rg.x,
+                                                         keys_opt ? keys_opt + rg.x : nullptr, S);
+}
+
+// 4b. the tiles with more than kSegMax instances, from the list tile_scan
+// made: up to kLargeMax keys in shared memory, beyond that from global memory.
+__global__ void __launch_bounds__(kLargeThreads, 1)
+tile_sort_large_kernel(const uint2* __restrict__ ranges, const uint32_t* __restrict__ long_tiles,
+                       const uint32_t* __restrict__ n_long, unsigned long long* __restrict__ seg,
+                       unsigned long long* __restrict__ scratch, uint32_t* __restrict__ ids,
+                       uint64_t* __restrict__ keys_opt) {
+  using SS = SegSmem<kLargeThreads, kLargeItems>;
+  extern __shared__ __align__(16) unsigned char seg_smem[];
+  SS& S = *reinterpret_cast<SS*>(seg_smem);
+  const uint32_t nl = *n_long;
+  for (uint32_t i = blockIdx.x; i < nl; i += gridDim.x) {
+    const uint32_t tile = long_tiles[i];
+    const uint2 rg = ranges[tile];
+    const uint32_t cnt = rg.y - rg.x;
+    if (cnt <= (uint32_t)SS::MAXK)
+      smem_segment_sort<kLargeThreads, kLargeItems>(seg + rg.x, cnt, tile, ids + rg.x,
+                                                    keys_opt ? keys_opt + rg.x : nullptr, S);
+    else
+      big_segment_sort<kLargeThreads, kLargeItems>(seg + rg.x, scratch + rg.x, cnt, tile,
+                                                   ids + rg.x, keys_opt ? keys_opt + rg.x : nullptr,
+                                                   S);
+    __syncthreads();  // the shared tables are reused by the next tile
   }
 }
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 struct BinLayout {
-  size_t counts, cursor, total, sort_n, zero_end, block_counts, block_base, seg, scratch, size;
+  size_t counts, cursor, total, n_long, sort_n, zero_end, block_counts, block_base, long_tiles,
+      seg, scratch, size;
 };
 
 BinLayout bin_layout(uint64_t n_tiles_all, int64_t capacity) {
@@ -511,12 +619,14 @@ BinLayout bin_layout(uint64_t n_tiles_all, int64_t capacity) {
   auto take = [&](size_t b) { size_t at = o; o += align256(b > 0 ? b : 1); return at; };
   L.counts = take(4 * n_tiles_all);
   L.total = take(8);
-  L.zero_end = o;  // counts and total start at zero
+  L.n_long = take(4);
+  L.zero_end = o;  // counts, total and the long-tile count start at zero
   L.sort_n = take(8);
   L.cursor = take(4 * n_tiles_all);
   const bool local = n_tiles_all <= (uint64_t)kSmemTiles;
   L.block_counts = take(local ? 4 * (size_t)kItemBlocks * n_tiles_all : 0);
   L.block_base = take(local ? 4 * (size_t)kItemBlocks * n_tiles_all : 0);
+  L.long_tiles = take(4 * n_tiles_all);
   L.seg = take(8 * (size_t)capacity);
   L.scratch = take(8 * (size_t)capacity);
   L.size = o;
@@ -590,8 +700,11 @@ extern "C" lgs_status gs_bin_sort(const float* proj, const uint16_t* rect, int64
   const int nblk = grid_items(m);
   tile_count_kernel<<<nblk, 256, cnt_smem, s>>>((const ushort4*)rect, m, (uint32_t)n, tiles_x,
                                                 tiles, n_tiles_all, counts, block_counts, total);
+  uint32_t* long_tiles = (uint32_t*)(ws + L.long_tiles);
+  uint32_t* n_long = (uint32_t*)(ws + L.n_long);
   tile_scan_kernel<<<1, kScanThreads, 0, s>>>(counts, n_tiles_all, total, capacity,
-                                              (uint2*)ranges, cursor, n_instances_dev, sort_n);
+                                              (uint2*)ranges, cursor, n_instances_dev, sort_n,
+                                              long_tiles, n_long);
   if (capacity == 0) {
     LGS_CHECK_LAUNCH();
     return LGS_OK;
@@ -602,8 +715,18 @@ extern "C" lgs_status gs_bin_sort(const float* proj, const uint16_t* rect, int64
   tile_emit_kernel<<<nblk, 256, cnt_smem, s>>>((const float4*)proj, (const ushort4*)rect, m,
                                                (uint32_t)n, tiles_x, tiles, n_tiles_all, sort_n,
                                                block_base, cursor, seg);
-  tile_sort_kernel<<<n_tiles_all, kSegThreads, 0, s>>>(
-      (const uint2*)ranges, seg, (unsigned long long*)(ws + L.scratch), ids, keys_opt);
+  using SmallSmem = SegSmem<kSegThreads, kSegMax / kSegThreads>;
+  using LargeSmem = SegSmem<kLargeThreads, kLargeItems>;
+  LGS_CHECK_CUDA(set_smem_limit(reinterpret_cast<const void*>(tile_sort_kernel),
+                                (int)sizeof(SmallSmem)));
+  LGS_CHECK_CUDA(set_smem_limit(reinterpret_cast<const void*>(tile_sort_large_kernel),
+                                (int)sizeof(LargeSmem)));
+  tile_sort_kernel<<<n_tiles_all, kSegThreads, sizeof(SmallSmem), s>>>((const uint2*)ranges, seg,
+                                                                       ids, keys_opt);
+  tile_sort_large_kernel<<<std::min<uint32_t>(n_tiles_all, kLargeBlocks), kLargeThreads,
+                           sizeof(LargeSmem), s>>>((const uint2*)ranges, long_tiles, n_long, seg,
+                                                   (unsigned long long*)(ws + L.scratch), ids,
+                                                   keys_opt);
   LGS_CHECK_LAUNCH();
   return LGS_OK;
 }

@@ -93,6 +93,41 @@ def test_bin_sort_bit_exact(lgs, oracle_lib, n, ncams, tx, ty, seed):
         np.testing.assert_array_equal(_np(bufs.ranges).view(np.uint32), ref["ranges"])
 
 
+@pytest.mark.parametrize("tie_frac", [0.0, 0.1])
+def test_bin_sort_long_segments_bit_exact(lgs, oracle_lib, tie_frac):
+    """Tiles with more instances than a 256-thread block sorts in shared
+    memory: 5,000 and exactly 12,288 (the 1024-thread blocks' shared-memory
+    limit), 12,289 and 30,000 (chunk by chunk from global memory), all in
+    the third camera, next to two cameras of ordinary tiles; with and without
+    equal depths."""
+    rng = np.random.default_rng(31)
+    ncams, tx, ty, n = 3, 9, 7, 60000
+    rect, depth = synth.synthetic_projected(rng, n, ncams, tx, ty, max_extent=3,
+                                            tie_frac=tie_frac)
+    sizes = [(0, 5000), (3, 12288), (10, 12289), (40, 30000)]  # (tile, instances)
+    rect[2 * n:] = 0  # camera 2: only the long tiles
+    i0 = 2 * n
+    for t, cnt in sizes:
+        x, y = t % tx, t // tx
+        rect[i0:i0 + cnt] = [x, y, x + 1, y + 1]
+        i0 += cnt
+    proj = np.zeros((ncams * n, 8), np.float32)
+    proj[:, 6] = depth
+    ref = oracle_lib.bin_sort(rect, depth, n, ncams, tx, ty)
+    k = len(ref["ids"])
+    counts = (ref["ranges"][:, 1] - ref["ranges"][:, 0]).reshape(ncams, -1)
+    assert [int(counts[2, t]) for t, _ in sizes] == [c for _, c in sizes]
+    bufs = lgs.BinBuffers(n, ncams, tx, ty, k, "cuda", want_keys=True)
+    for _ in range(2):  # the second call reuses the workspace
+        lgs.gs_bin_sort(torch.from_numpy(proj).cuda(),
+                        torch.from_numpy(rect.astype(np.int16)).cuda(), bufs)
+        torch.cuda.synchronize()
+        assert int(bufs.k_dev.item()) == k
+        np.testing.assert_array_equal(_np(bufs.ids)[:k].view(np.uint32), ref["ids"])
+        np.testing.assert_array_equal(_np(bufs.keys)[:k].view(np.uint64), ref["keys"])
+        np.testing.assert_array_equal(_np(bufs.ranges).view(np.uint32), ref["ranges"])
+
+
 def test_bin_sort_empty_and_overflow(lgs, oracle_lib):
     n, ncams, tx, ty = 4000, 2, 20, 10
     rect, depth, proj = _bin_inputs(n, ncams, tx, ty, 11, empty=True)

@@ -43,6 +43,10 @@ def parse():
     ap.add_argument("--no-plain", action="store_true", help="skip the plain 512-d path")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle cpu_baseline")
     ap.add_argument("--ae-steps", type=int, default=200)
+    ap.add_argument("--no-window", action="store_true",
+                    help="skip the 8-keyframe window workload")
+    ap.add_argument("--no-outdoor", action="store_true",
+                    help="skip the outdoor-scale workload (2M Gaussians, 8 x 1200x680)")
     ap.add_argument("--profile", action="store_true",
                     help="run warmup + steps eager mapping steps and exit (for ncu)")
     ap.add_argument("--profile-ae", action="store_true",
@@ -216,7 +220,7 @@ def run_gpu(args, rank, world):
     torch.cuda.synchronize()
     ae_train_s = time.time() - t0
     ae_losses = [float(l.item()) for l in ae_losses] or [float("nan")]
-    del train, frames
+    del train
     f16 = model.encode(g512_bf)
     s16_bf = DeviceScene(geom.means, geom.quats, geom.log_scales, geom.opacity_logits,
                          colors_bf, f16.bfloat16().contiguous())
@@ -229,42 +233,8 @@ def run_gpu(args, rank, world):
 
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
 
-    def timed(step, k, warm, clocks=None, events_inside=None):
-        """Captures step.run in a CUDA graph; returns per-replay ms (L2
-        flushed before each replay, outside the timed events)."""
-        s = torch.cuda.Stream(device=dev)
-        s.wait_stream(torch.cuda.current_stream())
-        with torch.cuda.stream(s):
-            step.run()  # eager once (also sets kernel attributes)
-        torch.cuda.current_stream().wait_stream(s)
-        torch.cuda.synchronize()
-        g = torch.cuda.CUDAGraph()
-        with torch.cuda.graph(g):
-            step.run()
-        torch.cuda.synchronize()
-        nodes = kernel_nodes(step.run)
-        for _ in range(warm):
-            flush.fill_(1.0)
-            g.replay()
-        torch.cuda.synchronize()
-        times = []
-        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-              for _ in range(k)]
-        if world > 1:
-            torch.distributed.barrier()
-        torch.cuda.synchronize()
-        ctx = clocks if clocks is not None else _Null()
-        with ctx:
-            for i in range(k):
-                flush.fill_(1.0)
-                ev[i][0].record()
-                g.replay()
-                ev[i][1].record()
-            torch.cuda.synchronize()
-        if world > 1:
-            torch.distributed.barrier()
-        times = [a.elapsed_time(b) for a, b in ev]
-        return times, g, nodes
+    def timed(step, k, warm, clocks=None):
+        return timed_graph_steps(step.run, k, warm, flush, world, clocks)
 
     step16 = MappingStep(s16_bf, cams, rgb_t, dep_t, f_gt, model=model)
     if args.profile:
@@ -275,6 +245,7 @@ def run_gpu(args, rank, world):
         return
     clocks = Clocks(torch.cuda.current_device())
     t16, g16, nodes16 = timed(step16, args.steps, args.warmup, clocks)
+    step16.check()  # the bins held every instance of every timed step
     k_inst = int(step16.k_dev.item())
     ms16 = float(np.mean(t16))
     total_ms = max_over_ranks(float(sum(t16)), world, dev)
@@ -333,6 +304,10 @@ def run_gpu(args, rank, world):
                "reference": "plain 512-channel FP32 render of the same Gaussians"}
     del y, ref
 
+    window = None if args.no_window else measure_window(W, s16_bf, frames, model, flush, dev,
+                                                        world)
+    del frames
+
     # end to end through the C ABI with host buffers: per step the keyframe's
     # targets (RGB, depth, F_gt) go host -> device from pinned memory and the
     # loss comes back
@@ -346,7 +321,11 @@ def run_gpu(args, rank, world):
                           capacity=step16.bufs.capacity)
     _, g16b, _ = timed(step16b, 1, 1)
     e2e = measure_e2e([step16, step16b], [g16, g16b], args.steps, args.warmup)
-    del step16b
+    del step16b, g16b, step16f
+    outdoor = None
+    if not args.no_outdoor:
+        del g16
+        outdoor = measure_outdoor(args, flush, dev, world)
 
     if rank == 0:
         peaks, kind = measured_peaks()
@@ -366,7 +345,11 @@ def run_gpu(args, rank, world):
             "roofline": rf, "rooflines": kern, "work_counts": counts,
             "e2e": e2e,
             "clocks": clocks.summary(),
+            "speedup_16d_over_plain_512": plain["speedup_of_16d"] if plain else None,
+            "decoded_cosine_error_mean": cos_err["mean"] if cos_err else None,
             "plain_512": plain, "decoded_cosine_error": cos_err, "variants": extra,
+            "workloads": {"indoor-window-8x640x480-300k": window,
+                          "outdoor-8x1200x680-2M": outdoor},
             "prune": prune, "feature_dim_sweep": sweep, "dssim_and_pose": extras,
             "per_call_ms": calls,
             "ae_pretrain": {"steps": args.ae_steps, "loss_first": ae_losses[0],
@@ -375,6 +358,179 @@ def run_gpu(args, rank, world):
             "cpu_baseline": cpu,
         }
         print(json.dumps(line), flush=True)
+
+
+def step_report(step, run, k, warm, flush, world, pixels):
+    """Times one composed step (graph replays) and its call groups; returns
+    the per-step figures, the per-call rooflines and the work counts."""
+    t, _, nodes = timed_graph_steps(run, k, warm, flush, world)
+    step.check()  # LGS_ERR_CAPACITY etc. would have emptied the bins
+    ms = float(np.mean(t))
+    calls = per_call_times(step, flush, reps=3)
+    kern, counts = rooflines(step, calls)
+    return {"ms_per_step": ms, "value": pixels / 1e6 / (ms / 1e3), "unit": "Mpix/s",
+            "kernels_per_step": nodes, "per_call_ms": calls, "rooflines": kern,
+            "work_counts": counts}
+
+
+def measure_window(W, s16_bf, f_gt_frames, model, flush, dev, world, k=20, warm=3):
+    """The differentiable mapping window: the 8 arc keyframes of the room
+    (640x480, 300k Gaussians) in one launch, 2.46 Mpx per step.  Two
+    variants: the window's own loss, L1 on RGB + 0.1 L1 on depth + L1 on the
+    16-d feature against a 16-d target (no decoder), and the production path
+    with the feature term through the frozen decoder against the 512-d F_gt
+    of every keyframe (Eq. 2)."""
+    import torch
+    from paper_2511_16144_gb300 import synth
+    from paper_2511_16144_gb300.pipeline import MappingStep
+    cams = W["cams"]
+    tg = synth.targets(cams, feat_dim=16, seed=2100)
+    rgb8 = torch.from_numpy(np.stack([t[0] for t in tg])).to(dev)
+    dep8 = torch.from_numpy(np.stack([t[1] for t in tg])).to(dev)
+    f16 = torch.from_numpy(np.stack([t[2] for t in tg]).reshape(-1, 16)).to(dev).bfloat16()
+    pixels = len(cams) * cams[0].width * cams[0].height
+    out = {"workload": "indoor-window-8x640x480-300k", "cameras": len(cams), "pixels": pixels}
+    st = MappingStep(s16_bf, cams, rgb8, dep8, f16, model=None)
+    out["l1_16d"] = step_report(st, st.run, k, warm, flush, world, pixels)
+    out["instances"] = int(st.k_dev.item())
+    cap = st.bufs.capacity
+    del st
+    f_gt8 = torch.cat(f_gt_frames).contiguous()
+    st = MappingStep(s16_bf, cams, rgb8, dep8, f_gt8, model=model, capacity=cap)
+    out["decoded"] = step_report(st, st.run, k, warm, flush, world, pixels)
+    del st, f_gt8
+    return out
+
+
+def measure_outdoor(args, flush, dev, world, k=8, warm=3):
+    """The outdoor-scale window: 2M Gaussians in a 40x40x8 m volume, 8
+    keyframes of 1200x680 (6.53 Mpx), BF16 channels, the 16-d render with the
+    feature term through the decoder (Eq. 2), plus one online autoencoder
+    step (RECON, 65,536 pixels of the window's maps) per window; against the
+    plain path that renders all 512 channels, with the decoded 16-d
+    features' cosine error against the plain FP32 render of the first
+    keyframe.  The 512-d semantic field is generated on the device (same
+    recipe as the room's, 64 Voronoi cells of the volume)."""
+    import torch
+    from paper_2511_16144_gb300 import lgs, synth
+    from paper_2511_16144_gb300.ae import AutoEncoder
+    from paper_2511_16144_gb300.pipeline import MappingStep
+    from paper_2511_16144_gb300.render import DeviceScene, Frame
+    t0 = time.time()
+    scene, cams = synth.outdoor()
+    geom = DeviceScene.from_host(scene, device=dev)
+    colors_bf = geom.colors.bfloat16()
+    g512 = synth.semantic_features_device(geom.means, (0.0, 0.0, 0.0), (40.0, 40.0, 8.0),
+                                          seed=1006, out_dtype=torch.bfloat16)
+    s512 = DeviceScene(geom.means, geom.quats, geom.log_scales, geom.opacity_logits,
+                       colors_bf, g512)
+    frames = [Frame(s512, [c]).out["feat"][0].reshape(-1, 512).bfloat16() for c in cams]
+    enc, dec = synth.ae_init(seed=3004)
+    model = AutoEncoder(enc, dec, device=dev)
+    train = torch.cat(frames)
+    gen = torch.Generator(device=dev).manual_seed(11)
+    for _ in range(args.ae_steps):
+        idx = torch.randint(0, train.shape[0], (65536,), device=dev, generator=gen)
+        model.train_step(train[idx].contiguous(), lr=5e-3)
+    batch = train[torch.randint(0, train.shape[0], (65536,), device=dev, generator=gen)].contiguous()
+    del train
+    f16 = model.encode(g512)
+    s16 = DeviceScene(geom.means, geom.quats, geom.log_scales, geom.opacity_logits, colors_bf,
+                      f16.bfloat16().contiguous())
+    tg = synth.targets(cams, feat_dim=16, seed=2200)
+    rgb8 = torch.from_numpy(np.stack([t[0] for t in tg])).to(dev)
+    dep8 = torch.from_numpy(np.stack([t[1] for t in tg])).to(dev)
+    f_gt8 = torch.cat(frames).contiguous()
+    del frames
+    pixels = len(cams) * cams[0].width * cams[0].height
+    setup_s = time.time() - t0
+    out = {"workload": "outdoor-8x1200x680-2M", "gaussians": scene.n, "cameras": len(cams),
+           "pixels": pixels, "channels": "bf16", "setup_s": setup_s}
+    # decoded features of the first keyframe against the plain FP32 render
+    st = MappingStep(s16, cams[:1], rgb8[:1].contiguous(), dep8[:1].contiguous(),
+                     f_gt8[:cams[0].width * cams[0].height], model=model)
+    st.run()
+    torch.cuda.synchronize()
+    y = model.decode(st.out["feat"].reshape(-1, 16).contiguous())
+    del st
+    g32 = DeviceScene(geom.means, geom.quats, geom.log_scales, geom.opacity_logits, geom.colors,
+                      g512.float())
+    ref = Frame(g32, cams[:1]).out["feat"][0].reshape(-1, 512)
+    del g32
+    nr = ref.norm(dim=1)
+    keep = nr > 1e-6
+    cos = (y * ref).sum(1)[keep] / (y.norm(dim=1)[keep] * nr[keep]).clamp_min(1e-30)
+    out["decoded_cosine_error"] = {"mean": float((1 - cos).mean().item()),
+                                   "excluded_pixels": int((~keep).sum().item()),
+                                   "keyframe": 0}
+    del y, ref
+    step = MappingStep(s16, cams, rgb8, dep8, f_gt8, model=model)
+    ae_loss = torch.zeros(1, device=dev)
+
+    def run16():
+        step.run()
+        model.train_step(batch, lr=1e-4, loss=ae_loss)  # one online AE step per window
+
+    out["decoded"] = step_report(step, run16, k, warm, flush, world, pixels)
+    out["instances"] = int(step.k_dev.item())
+    cap = step.bufs.capacity
+    t_ae, _, _ = timed_graph_steps(lambda: model.train_step(batch, lr=1e-4, loss=ae_loss), 5, 2,
+                                   flush, world)
+    out["decoded"]["ae_train_step_ms"] = float(np.mean(t_ae))
+    del step
+    if not args.no_plain:
+        plain = MappingStep(s512, cams, rgb8, dep8, f_gt8, model=None, capacity=cap)
+        t, _, _ = timed_graph_steps(plain.run, 3, 1, flush, world)
+        plain.check()
+        ms = float(np.mean(t))
+        out["plain_512"] = {"ms_per_step": ms, "value": pixels / 1e6 / (ms / 1e3),
+                            "channels": "bf16", "feat_dim": 512}
+        out["speedup_16d_over_plain_512"] = out["decoded"]["value"] / out["plain_512"]["value"]
+        del plain
+    lgs.check_device("outdoor workload")
+    return out
+
+
+
+def timed_graph_steps(run, k, warm, flush, world, clocks=None):
+    """Captures run() (one step's enqueues) in a CUDA graph and replays it:
+    warm untimed replays, then k replays each between CUDA events on the
+    launching stream, L2 flushed before every replay outside the events.
+    Returns (per-replay ms, graph, kernel nodes of one step)."""
+    import torch
+    dev = torch.cuda.current_device()
+    s = torch.cuda.Stream(device=dev)
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        run()  # eager once (also sets kernel attributes and workspaces)
+    torch.cuda.current_stream().wait_stream(s)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        run()
+    torch.cuda.synchronize()
+    nodes = kernel_nodes(run)
+    for _ in range(warm):
+        flush.fill_(1.0)
+        g.replay()
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(k)]
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    ctx = clocks if clocks is not None else _Null()
+    with ctx:
+        for i in range(k):
+            flush.fill_(1.0)
+            ev[i][0].record()
+            g.replay()
+            ev[i][1].record()
+        torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    return [a.elapsed_time(b) for a, b in ev], g, nodes
+
 
 
 class _Null:
@@ -435,9 +591,35 @@ def per_call_times(step, flush, reps=5):
 
 # ncu DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) per launch
 # of each call group at this workload, from the capture summarised under
-# profiles/; None once the kernel has changed since the capture.
-TRAFFIC = {"gs_project": 13216768, "gs_bin_sort": 31381760, "gs_render_fwd": 3332864,
-           "l1_losses": 9845248, "ae_decode": 349998592, "gs_render_bwd": 41834240}
+# profiles/, with a digest of the sources of that call group's kernels at
+# capture time: a figure whose sources have changed since is reported as
+# None instead of a stale number.
+TRAFFIC_SOURCES = {
+    "gs_project": ("project.cu", "common.cuh", "kernels.cuh"),
+    "gs_bin_sort": ("binning.cu", "common.cuh", "kernels.cuh"),
+    "gs_render_fwd": ("render.cu", "common.cuh", "kernels.cuh"),
+    "l1_losses": ("api.cu", "common.cuh"),
+    "ae_decode": ("ae_fused.cu", "tc05.cuh", "common.cuh", "kernels.cuh"),
+    "gs_render_bwd": ("render.cu", "project.cu", "common.cuh", "kernels.cuh"),
+}
+TRAFFIC = {}  # call group -> (bytes per launch, source digest)
+
+
+def source_digest(group):
+    """First 12 hex digits of the SHA-256 of the sources of a call group."""
+    import hashlib
+    h = hashlib.sha256()
+    for f in TRAFFIC_SOURCES[group]:
+        with open(os.path.join(ROOT, "paper_2511_16144_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:12]
+
+
+def current_traffic(group):
+    entry = TRAFFIC.get(group)
+    if entry is None or entry[1] != source_digest(group):
+        return None
+    return entry[0]
 
 
 def rooflines(step, calls):
@@ -447,7 +629,9 @@ def rooflines(step, calls):
     times the units one launch processes):
       gs_project    HBM  44 B per Gaussian read + 40 B per (camera, Gaussian) written
       gs_bin_sort   HBM  36 B per instance (emit write + one read/write pass of
-                         12-byte records) + 8 B per tile range
+                         12-byte records) + 8 B per tile range + 40 B per
+                         (camera, Gaussian) record read (rect and the tile
+                         test's projected record)
       gs_render_fwd ALU  10 FLOP per evaluated (pixel, instance) pair E +
                          2 (4 + d) + 4 per blended pair B
       l1_losses     HBM  48 B per pixel (RGB and depth: prediction, target, gradient)
@@ -467,7 +651,7 @@ def rooflines(step, calls):
     hbm, tc = float(peaks["hbm_gbs"]), float(peaks["bf16_tflops"])
     work = {
         "gs_project": ("hbm", 44.0 * n + 40.0 * c * n),
-        "gs_bin_sort": ("hbm", 36.0 * K + 8.0 * tiles),
+        "gs_bin_sort": ("hbm", 36.0 * K + 8.0 * tiles + 40.0 * c * n),
         "gs_render_fwd": ("alu", 10.0 * E + (2.0 * (4 + d) + 4.0) * B),
         "l1_losses": ("hbm", 48.0 * P),
         "ae_decode": ("tensor", 2.0 * 346112.0 * P),
@@ -482,7 +666,7 @@ def rooflines(step, calls):
             achieved = units / (ms / 1e3) / 1e12
             peak, unit = (tc, "TFLOP/s") if bound == "tensor" else (alu, "TFLOP/s")
         out[name] = {"bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
-                     "frac": achieved / peak, "traffic": TRAFFIC.get(name),
+                     "frac": achieved / peak, "traffic": current_traffic(name),
                      "work_per_launch": units, "ms_per_launch": ms,
                      "peak_source": ("fp32 lanes: " + FP32_PEAK_NOTE) if bound == "alu"
                      else kind + (" bf16 burst" if bound == "tensor" else " copy")}

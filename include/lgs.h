@@ -147,7 +147,10 @@ void lgs_set_sort_wait_limit(int64_t polls);
  *   float32 device arrays.
  * cams_host [n_cams]: host array, 1 <= n_cams <= LGS_MAX_CAMS.
  * proj [n_cams*n, 8] (16-byte aligned): per (camera, Gaussian) record
- *   (u, v, conic a, conic b, conic c, opacity, depth tz, 0); zero when culled.
+ *   (u, v, conic a, conic b, conic c, opacity, depth tz, cut); zero when
+ *   culled.  cut = 2 ln(255 o) 1.001 + 0.01 bounds q = a dx^2 + 2 b dx dy +
+ *   c dy^2 (= -2 power) over every pixel with o e^power >= 1/255, with a
+ *   margin for FP32 rounding; gs_bin_sort's tile test uses it.
  * rect [n_cams*n, 4] uint16 (8-byte aligned): covered tiles
  *   [x0, y0, x1, y1) on the 16x16 grid, x1 == x0 and y1 == y0 when culled.
  * ---------------------------------------------------------------------- */
@@ -158,11 +161,18 @@ lgs_status gs_project(const float* means, const float* quats, const float* log_s
 /* ------------------------------------------------------------------------
  * gs_bin_sort -- 16x16 tile binning, instances ordered by depth within each tile.
  *
- * Each (camera c, Gaussian i) emits one instance per covered tile; the
- * instances are ordered by the 64-bit key ((c * tiles + tile) << 32) |
- * bits(float depth), ties by ascending Gaussian index (a stable sort of the
- * emission order).  This is the front-to-back order of Sec. III-B.1's
- * alpha compositing within every tile.
+ * Each (camera c, Gaussian i) emits one instance per tile of its rect that
+ * its ellipse reaches: the minimum of q(d) = a dx^2 + 2 b dx dy + c dy^2,
+ * d = (u - x, v - y), over the tile's pixel-centre square [16 tx + 0.5,
+ * 16 tx + 15.5] x [16 ty + 0.5, 16 ty + 15.5] is at most the record's cut
+ * (0 when the mean is inside, else the least of the four edges' 1-D
+ * minima, in FP32 with round-to-nearest operations in a fixed order).  No
+ * pixel that passes the 1/255 skip test is in a tile left out, so the tiled
+ * render equals the per-pixel one.  The instances are ordered by the 64-bit
+ * key ((c * tiles + tile) << 32) | bits(float depth), ties by ascending
+ * Gaussian index (a stable sort of the emission order).  This is the
+ * front-to-back order of Sec. III-B.1's alpha compositing within every
+ * tile.
  *
  * proj, rect: gs_project outputs for n Gaussians and n_cams cameras.
  * tiles_x, tiles_y: grid size (ceil(W/16), ceil(H/16)); n_cams * tiles_x *

@@ -68,9 +68,9 @@ def _load():
     lib.lgso_render_bwd.argtypes = [I64, I32, P, P, P, P, P, P, P, P, I32, I32, I32, I32,
                                     P, P, P, P, P, P, P, P, P, P]
     lib.lgso_project_bwd.argtypes = [I64, P, P, P, P, P, P, P, P, P, P]
-    lib.lgso_bin_count.argtypes = [I64, I32, P]
+    lib.lgso_bin_count.argtypes = [I64, I32, P, P]
     lib.lgso_bin_count.restype = I64
-    lib.lgso_bin_sort.argtypes = [I64, I32, I32, I32, P, P, P, P, P]
+    lib.lgso_bin_sort.argtypes = [I64, I32, I32, I32, P, P, P, P, P, P]
     lib.lgso_num_threads.restype = I32
     lib.lgso_pose_grad.argtypes = [I64, P, P, P, P, P, P, P]
     F32 = ctypes.c_float
@@ -205,23 +205,28 @@ def project_backward(scene, cam, dproj) -> dict:
     return out
 
 
-def bin_sort(rect, depth, n, ncams, tiles_x, tiles_y) -> dict:
-    """Binning definition: emit one key per (camera, Gaussian, covered tile)
+def bin_sort(rect, depth, n, ncams, tiles_x, tiles_y, proj=None) -> dict:
+    """Binning definition: emit one key per (camera, Gaussian, reached tile)
     in (camera, index, row-major tile) order, key = ((camera * tiles + tile)
     << 32) | bits(float32 depth); stable sort by key; per-tile ranges.
 
     ``rect`` int32 [ncams*n, 4] = tile rect [x0, y0, x1, y1); ``depth`` float32
-    [ncams*n].  Returns keys (uint64 [K]), ids (uint32 [K]) and ranges
-    (uint32 [ncams*tiles, 2])."""
+    [ncams*n]; ``proj`` float32 [ncams*n, 8] = the projected records (u, v,
+    a, b, c, o, tz, cut): a tile of the rect is reached when the ellipse
+    a dx^2 + 2 b dx dy + c dy^2 <= cut meets its pixel-centre square, decided
+    in FP32 as the GPU decides it (None: every tile of the rect).  Returns keys
+    (uint64 [K]), ids (uint32 [K]) and ranges (uint32 [ncams*tiles, 2])."""
     lib = _load()
     r = np.ascontiguousarray(np.asarray(rect, dtype=np.int32).reshape(-1, 4))
     z = np.ascontiguousarray(np.asarray(depth, dtype=np.float32).reshape(-1))
-    k = int(lib.lgso_bin_count(n, ncams, _ptr(r)))
+    pr = None if proj is None else np.ascontiguousarray(
+        np.asarray(proj, dtype=np.float32).reshape(-1, 8))
+    k = int(lib.lgso_bin_count(n, ncams, _ptr(r), None if pr is None else _ptr(pr)))
     keys = np.zeros(k, np.uint64)
     ids = np.zeros(k, np.uint32)
     ranges = np.zeros((ncams * tiles_x * tiles_y, 2), np.uint32)
-    lib.lgso_bin_sort(n, ncams, tiles_x, tiles_y, _ptr(r), _ptr(z), _ptr(keys), _ptr(ids),
-                      _ptr(ranges))
+    lib.lgso_bin_sort(n, ncams, tiles_x, tiles_y, _ptr(r), _ptr(z),
+                      None if pr is None else _ptr(pr), _ptr(keys), _ptr(ids), _ptr(ranges))
     return dict(keys=keys, ids=ids, ranges=ranges)
 
 

@@ -521,12 +521,55 @@ int lgso_project_bwd(int64_t n, const double* means, const double* quats, const 
 /* ---------------------------------------------------------------------- */
 /* binning                                                                 */
 
-int64_t lgso_bin_count(int64_t n, int ncams, const int32_t* rect) {
-  int64_t k = 0;
-  for (int64_t i = 0; i < (int64_t)ncams * n; i++) {
-    const int32_t* r = rect + 4 * i;
-    if (r[2] > r[0] && r[3] > r[1]) k += (int64_t)(r[2] - r[0]) * (r[3] - r[1]);
+/* Whether a projected record reaches tile (tx, ty): its ellipse
+   q(d) = a dx^2 + 2 b dx dy + c dy^2 <= cut, d = (u - x, v - y), meets the
+   tile's pixel-centre square [16 tx + 0.5, 16 tx + 15.5] x [16 ty + 0.5,
+   16 ty + 15.5].  The minimum of the convex q over the square is 0 when the
+   mean is inside; otherwise it lies on one of the four edges, where q is a
+   1-D quadratic whose minimiser (-b X / c, or -b Y / a, formed with the
+   reciprocal of c or a) is clamped to the edge.  The decision turns
+   a float into a bit, so it is taken in FP32 in one fixed order of
+   operations, each rounded (compiled without contraction), as the GPU takes
+   it.  rec = (u, v, a, b, c, o, tz, cut) as gs_project writes it. */
+static int tile_hit32(const float* rec, int tx, int ty) {
+  const float u = rec[0], v = rec[1], a = rec[2], b = rec[3], c = rec[4], cut = rec[7];
+  const float ia = 1.0f / a, ic = 1.0f / c;  /* the edge minimisers use reciprocals */
+  const float xa = (float)(16 * tx) + 0.5f, xb = (float)(16 * tx) + 15.5f;
+  const float ya = (float)(16 * ty) + 0.5f, yb = (float)(16 * ty) + 15.5f;
+  const float dx0 = u - xb, dx1 = u - xa, dy0 = v - yb, dy1 = v - ya;
+  if (dx0 <= 0.f && dx1 >= 0.f && dy0 <= 0.f && dy1 >= 0.f) return 1;
+  const float b2 = 2.f * b;
+  float best = INFINITY;
+  for (int e = 0; e < 4; e++) {
+    float X, Y;
+    if (e < 2) {  /* the edges dx = dx0 and dx = dx1 */
+      X = e ? dx1 : dx0;
+      Y = fminf(fmaxf(-(b * X) * ic, dy0), dy1);
+    } else {      /* the edges dy = dy0 and dy = dy1 */
+      Y = e == 3 ? dy1 : dy0;
+      X = fminf(fmaxf(-(b * Y) * ia, dx0), dx1);
+    }
+    const float t1 = (a * X) * X, t2 = (b2 * X) * Y, t3 = (c * Y) * Y;
+    const float q = (t1 + t2) + t3;
+    best = fminf(best, q);
   }
+  return best <= cut;
+}
+
+/* Instances of record i: the tiles of its rect that its ellipse reaches
+   (proj NULL: every tile of the rect). */
+static int64_t record_instances(const int32_t* r, const float* rec) {
+  int64_t k = 0;
+  if (!(r[2] > r[0] && r[3] > r[1])) return 0;
+  for (int ty = r[1]; ty < r[3]; ty++)
+    for (int tx = r[0]; tx < r[2]; tx++) k += !rec || tile_hit32(rec, tx, ty);
+  return k;
+}
+
+int64_t lgso_bin_count(int64_t n, int ncams, const int32_t* rect, const float* proj) {
+  int64_t k = 0;
+  for (int64_t i = 0; i < (int64_t)ncams * n; i++)
+    k += record_instances(rect + 4 * i, proj ? proj + 8 * i : NULL);
   return k;
 }
 
@@ -550,18 +593,21 @@ static void merge_sort_kv(kv* a, int64_t n) {
 }
 
 int lgso_bin_sort(int64_t n, int ncams, int tiles_x, int tiles_y, const int32_t* rect,
-                  const float* depth, uint64_t* keys, uint32_t* ids, uint32_t* ranges) {
+                  const float* depth, const float* proj, uint64_t* keys, uint32_t* ids,
+                  uint32_t* ranges) {
   int64_t ntiles = (int64_t)tiles_x * tiles_y;
-  int64_t k = lgso_bin_count(n, ncams, rect);
+  int64_t k = lgso_bin_count(n, ncams, rect, proj);
   kv* a = (kv*)malloc(sizeof(kv) * (k ? k : 1));
   int64_t o = 0;
   for (int c = 0; c < ncams; c++)
     for (int64_t i = 0; i < n; i++) {
       const int32_t* r = rect + 4 * ((int64_t)c * n + i);
+      const float* rec = proj ? proj + 8 * ((int64_t)c * n + i) : NULL;
       uint32_t bits;
       memcpy(&bits, &depth[(int64_t)c * n + i], 4);
       for (int ty = r[1]; ty < r[3]; ty++)
         for (int tx = r[0]; tx < r[2]; tx++) {
+          if (rec && !tile_hit32(rec, tx, ty)) continue;
           uint64_t tile = (uint64_t)c * ntiles + (uint64_t)ty * tiles_x + tx;
           a[o].key = (tile << 32) | bits;
           a[o].id = (uint32_t)i;

@@ -369,6 +369,8 @@ decode_fused_kernel(const __grid_constant__ FusedArgs a) {
     uint32_t nH = 0, nT = 0;
     bool ok = true;
     float lsum = 0.f;
+    const uint32_t sbf = (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(a.scale));
+    const uint32_t s2bf = sbf | (sbf << 16);  // BF16 scale in both halves
     auto wait_acc = [&](uint64_t* bar, uint32_t& n) {
       ok = ok && tc::mbar_wait(bar, n & 1, kLimit);
       n++;
@@ -511,6 +513,7 @@ decode_fused_kernel(const __grid_constant__ FusedArgs a) {
         // first is computed); dy = +-scale or 0, packed to BF16 at once
         uint4 dy[4];
         uint32_t ya[16], yb[16];
+        float lc = 0.f;  // this chunk's sum of |d|
         const uint32_t ty = tb + 256 + 128 * (c & 1) + 32 * qq;
         tc::tmem_ld16_issue(ty, ya);
         tc::tmem_wait16(ya);
@@ -531,13 +534,22 @@ decode_fused_kernel(const __grid_constant__ FusedArgs a) {
                   __fadd2_rn(f2(__uint_as_float(yv[i]), __uint_as_float(yv[i + 1])),
                              *reinterpret_cast<const float2*>(sb7 + n0 + 16 * h + i)),
                   f2(-tt.x, -tt.y));
-              const float d0 = dd.x, d1 = dd.y;
-              if (valid) lsum += fabsf(d0) + fabsf(d1);
-              o2[e] = __floats2bfloat162_rn(
-                  valid ? (d0 > 0.f ? a.scale : (d0 < 0.f ? -a.scale : 0.f)) : 0.f,
-                  valid ? (d1 > 0.f ? a.scale : (d1 < 0.f ? -a.scale : 0.f)) : 0.f);
+              lc += fabsf(dd.x) + fabsf(dd.y);
+              // BF16 pair of sign(d) * scale: d's sign bits applied to the
+              // BF16 pattern of scale, a zero half where d is exactly 0
+              uint32_t w = (__byte_perm(__float_as_uint(dd.x), __float_as_uint(dd.y), 0x7632) &
+                            0x80008000u) ^ s2bf;
+              if (dd.x == 0.f) w &= 0xffff0000u;
+              if (dd.y == 0.f) w &= 0x0000ffffu;
+              reinterpret_cast<uint32_t*>(o2)[e] = w;
             }
           }
+        }
+        if (valid) {
+          lsum += lc;
+        } else {  // rows past the end carry no loss and no gradient
+#pragma unroll
+          for (int kk = 0; kk < 4; kk++) dy[kk] = make_uint4(0u, 0u, 0u, 0u);
         }
         if (c > 0) {  // the previous chunk's product has read the dy buffer
           ok = ok && tc::mbar_wait(dyfree, (c - 1) & 1, kLimit);

@@ -1,5 +1,6 @@
 // 16x16 tile binning: every (camera, Gaussian) item emits one instance per
-// tile its support rect covers, and each tile's instances are ordered by
+// tile of its support rect that its ellipse q(d) <= cut reaches (tile_hit),
+// and each tile's instances are ordered by
 // depth, ties by Gaussian index -- the front-to-back order alpha compositing
 // needs (LEGO-SLAM Sec. III-B.1, the standard 3DGS pipeline).  The result is
 // the same as a stable sort of the keys ((camera * tiles + tile) << 32) |
@@ -45,6 +46,109 @@ constexpr int kScanThreads = 1024;
 
 __device__ __forceinline__ bool rect_empty(const ushort4& r) { return r.z <= r.x || r.w <= r.y; }
 
+// The ellipse of a visible projected record as the tile test reads it: mean,
+// conic (a, b, c), the reciprocals of a and c (IEEE, once per record), the
+// cutoff, and the depth (the emitted key).  r0 = (u, v, a, b), r1 = (c, o,
+// tz, cut); a, c > 0.
+struct Ell {
+  float u, v, a, b, c, ia, ic, cut, tz;
+};
+__device__ __forceinline__ Ell ell_of(const float4& r0, const float4& r1) {
+  return Ell{r0.x, r0.y, r0.z, r0.w, r1.x, __frcp_rn(r0.z), __frcp_rn(r1.x), r1.w, r1.z};
+}
+
+// Whether the ellipse q(d) = a dx^2 + 2 b dx dy + c dy^2 <= cut, d = (u - x,
+// v - y), meets the pixel-centre square [16 tx + 0.5, 16 tx + 15.5] x
+// [16 ty + 0.5, 16 ty + 15.5] of tile (tx, ty): zero if the mean is inside,
+// else the smallest q over the four edges, each a 1-D quadratic whose
+// minimiser (-b X / c on an edge dx = X, -b Y / a on an edge dy = Y, taken
+// as a product with the reciprocal) is clamped to the edge.  FP32 with a
+// fixed order of round-to-nearest operations (no contraction), so the
+// oracle takes the same decision bit for bit.
+__device__ __forceinline__ bool tile_hit(const Ell& E, uint32_t tx, uint32_t ty) {
+  const float xa = (float)(16u * tx) + 0.5f, xb = (float)(16u * tx) + 15.5f;
+  const float ya = (float)(16u * ty) + 0.5f, yb = (float)(16u * ty) + 15.5f;
+  const float dx0 = __fsub_rn(E.u, xb), dx1 = __fsub_rn(E.u, xa);
+  const float dy0 = __fsub_rn(E.v, yb), dy1 = __fsub_rn(E.v, ya);
+  if (dx0 <= 0.f && dx1 >= 0.f && dy0 <= 0.f && dy1 >= 0.f) return true;
+  const float b2 = __fmul_rn(2.f, E.b);
+  auto q = [&](float X, float Y) {
+    return __fadd_rn(__fadd_rn(__fmul_rn(__fmul_rn(E.a, X), X), __fmul_rn(__fmul_rn(b2, X), Y)),
+                     __fmul_rn(__fmul_rn(E.c, Y), Y));
+  };
+  float best = INFINITY;
+#pragma unroll
+  for (int e = 0; e < 2; e++) {
+    const float X = e ? dx1 : dx0;
+    const float Y = fminf(fmaxf(__fmul_rn(-__fmul_rn(E.b, X), E.ic), dy0), dy1);
+    best = fminf(best, q(X, Y));
+  }
+#pragma unroll
+  for (int e = 0; e < 2; e++) {
+    const float Y = e ? dy1 : dy0;
+    const float X = fminf(fmaxf(__fmul_rn(-__fmul_rn(E.b, Y), E.ia), dx0), dx1);
+    best = fminf(best, q(X, Y));
+  }
+  return best <= E.cut;
+}
+
+// Calls fn(i, t, E) for every (item, tile) pair of the items [i0, i1) whose
+// ellipse reaches the tile (t = tile index within the camera).  The rect
+// tiles of each group of 32 consecutive items are flattened (item order,
+// then row-major tile order) and spread evenly over the warp's lanes, so a
+// few large splats do not hold a whole warp back; each pair finds its item
+// by a binary search over the group's running tile counts and reads the
+// item's fields from the owning lane.
+template <typename F>
+__device__ __forceinline__ void for_each_hit(const float4* __restrict__ proj,
+                                             const ushort4* __restrict__ rect, int64_t i0,
+                                             int64_t i1, int tiles_x, F&& fn) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int64_t g = i0 + (int64_t)warp * 32; g < i1; g += (int64_t)nw * 32) {
+    const int64_t i = g + lane;
+    ushort4 r = make_ushort4(0, 0, 0, 0);
+    if (i < i1) r = rect[i];
+    const uint32_t w = r.z > r.x ? (uint32_t)(r.z - r.x) : 0u;
+    const uint32_t area = r.w > r.y ? w * (uint32_t)(r.w - r.y) : 0u;
+    uint32_t incl = area;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += y;
+    }
+    const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
+    if (total == 0) continue;
+    Ell E{0.f, 0.f, 1.f, 0.f, 1.f, 1.f, 1.f, 0.f, 0.f};
+    if (area) E = ell_of(proj[2 * i], proj[2 * i + 1]);
+    const uint32_t excl = incl - area;
+    const uint32_t xy = (uint32_t)r.x | ((uint32_t)r.y << 16);
+    for (uint32_t j0 = 0; j0 < total; j0 += 32) {
+      const uint32_t j = j0 + (uint32_t)lane;
+      int k = 0;  // the first lane whose running count exceeds j
+#pragma unroll
+      for (int step = 16; step > 0; step >>= 1)
+        if (__shfl_sync(0xffffffffu, incl, k + step - 1) <= j) k += step;
+      Ell F;
+      F.u = __shfl_sync(0xffffffffu, E.u, k);
+      F.v = __shfl_sync(0xffffffffu, E.v, k);
+      F.a = __shfl_sync(0xffffffffu, E.a, k);
+      F.b = __shfl_sync(0xffffffffu, E.b, k);
+      F.c = __shfl_sync(0xffffffffu, E.c, k);
+      F.ia = __shfl_sync(0xffffffffu, E.ia, k);
+      F.ic = __shfl_sync(0xffffffffu, E.ic, k);
+      F.cut = __shfl_sync(0xffffffffu, E.cut, k);
+      F.tz = __shfl_sync(0xffffffffu, E.tz, k);
+      const uint32_t kxy = __shfl_sync(0xffffffffu, xy, k);
+      const uint32_t kw = __shfl_sync(0xffffffffu, w, k);
+      const uint32_t local = j - __shfl_sync(0xffffffffu, excl, k);
+      if (j < total) {
+        const uint32_t ty = (kxy >> 16) + local / kw, tx = (kxy & 0xffffu) + local % kw;
+        if (tile_hit(F, tx, ty)) fn(g + k, ty * (uint32_t)tiles_x + tx, F);
+      }
+    }
+  }
+}
+
 // Items of block b, camera by camera: for camera c, chunk b of that
 // camera's n items [c n, (c + 1) n).  A block's per-tile tables so cover few
 // tiles densely, and all blocks emit into the tiles of one camera at a time:
@@ -59,9 +163,10 @@ __device__ __forceinline__ void cam_chunk(uint32_t n, uint32_t c, int64_t& i0, i
 
 // 1. per-tile instance counts and K.
 __global__ void __launch_bounds__(256)
-tile_count_kernel(const ushort4* __restrict__ rect, int64_t m, uint32_t n, int tiles_x,
-                  uint32_t tiles, uint32_t n_tiles_all, uint32_t* __restrict__ counts,
-                  uint32_t* __restrict__ block_counts, unsigned long long* __restrict__ total) {
+tile_count_kernel(const float4* __restrict__ proj, const ushort4* __restrict__ rect, int64_t m,
+                  uint32_t n, int tiles_x, uint32_t tiles, uint32_t n_tiles_all,
+                  uint32_t* __restrict__ counts, uint32_t* __restrict__ block_counts,
+                  unsigned long long* __restrict__ total) {
   extern __shared__ uint32_t s_cnt[];  // n_tiles_all entries when they fit
   const bool local = n_tiles_all <= (uint32_t)kSmemTiles;
   if (local) {
@@ -74,17 +179,12 @@ tile_count_kernel(const ushort4* __restrict__ rect, int64_t m, uint32_t n, int t
     int64_t i0, i1;
     cam_chunk(n, c, i0, i1);
     const uint32_t base = c * tiles;
-    for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
-      const ushort4 r = rect[i];
-      if (rect_empty(r)) continue;
-      for (uint32_t y = r.y; y < r.w; y++)
-        for (uint32_t x = r.x; x < r.z; x++) {
-          const uint32_t t = base + y * (uint32_t)tiles_x + x;
-          if (local) atomicAdd(&s_cnt[t], 1u);
-          else atomicAdd(&counts[t], 1u);
-        }
-      k += (unsigned long long)(r.z - r.x) * (r.w - r.y);
-    }
+    for_each_hit(proj, rect, i0, i1, tiles_x, [&](int64_t, uint32_t tt, const Ell&) {
+      const uint32_t t = base + tt;
+      if (local) atomicAdd(&s_cnt[t], 1u);
+      else atomicAdd(&counts[t], 1u);
+      k++;
+    });
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) k += __shfl_xor_sync(0xffffffffu, k, o);
@@ -202,19 +302,12 @@ tile_emit_kernel(const float4* __restrict__ proj, const ushort4* __restrict__ re
     int64_t i0, i1;
     cam_chunk(n, c, i0, i1);
     const uint32_t base = c * tiles;
-    for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
-      const ushort4 r = rect[i];
-      if (rect_empty(r)) continue;
-      const unsigned long long key =
-          ((unsigned long long)__float_as_uint(proj[2 * i + 1].z) << 32) |
-          (uint32_t)(i - (int64_t)c * n);
-      for (uint32_t y = r.y; y < r.w; y++)
-        for (uint32_t x = r.x; x < r.z; x++) {
-          const uint32_t t = base + y * (uint32_t)tiles_x + x;
-          const uint32_t pos = local ? atomicAdd(&s_cur[t], 1u) : atomicAdd(&cursor[t], 1u);
-          seg[pos] = key;
-        }
-    }
+    const int64_t item0 = (int64_t)c * n;
+    for_each_hit(proj, rect, i0, i1, tiles_x, [&](int64_t i, uint32_t tt, const Ell& E) {
+      const uint32_t t = base + tt;
+      const uint32_t pos = local ? atomicAdd(&s_cur[t], 1u) : atomicAdd(&cursor[t], 1u);
+      seg[pos] = ((unsigned long long)__float_as_uint(E.tz) << 32) | (uint32_t)(i - item0);
+    });
   }
 }
 
@@ -698,8 +791,9 @@ extern "C" lgs_status gs_bin_sort(const float* proj, const uint16_t* rect, int64
   uint32_t* block_counts = (uint32_t*)(ws + L.block_counts);
   uint32_t* block_base = (uint32_t*)(ws + L.block_base);
   const int nblk = grid_items(m);
-  tile_count_kernel<<<nblk, 256, cnt_smem, s>>>((const ushort4*)rect, m, (uint32_t)n, tiles_x,
-                                                tiles, n_tiles_all, counts, block_counts, total);
+  tile_count_kernel<<<nblk, 256, cnt_smem, s>>>((const float4*)proj, (const ushort4*)rect, m,
+                                                (uint32_t)n, tiles_x, tiles, n_tiles_all, counts,
+                                                block_counts, total);
   uint32_t* long_tiles = (uint32_t*)(ws + L.long_tiles);
   uint32_t* n_long = (uint32_t*)(ws + L.n_long);
   tile_scan_kernel<<<1, kScanThreads, 0, s>>>(counts, n_tiles_all, total, capacity,

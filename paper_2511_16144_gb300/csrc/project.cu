@@ -147,7 +147,11 @@ __global__ void project_kernel(const float* __restrict__ means, const float4* __
     float4 a = make_float4(0.f, 0.f, 0.f, 0.f), b = a;
     if (finite && P.valid && support_rect(P, cam, r)) {
       a = make_float4(P.u, P.v, P.conic[0], P.conic[1]);
-      b = make_float4(P.conic[2], P.o, P.t[2], 0.f);
+      // the cutoff of the tile test: a pixel with o e^power >= 1/255 has
+      // q = -2 power <= 2 ln(255 o); the margin covers the FP32 rounding of
+      // q here and in the renderer (power, exponential)
+      const float cut = fmaf(2.f * logf(255.f * P.o), 1.001f, 1e-2f);
+      b = make_float4(P.conic[2], P.o, P.t[2], cut);
     } else {
       r = make_ushort4(0, 0, 0, 0);
     }

@@ -245,6 +245,60 @@ def semantic_features(means, lo, hi, n_cells=64, dim=512, noise=0.02, seed=1005)
     return unit_rows(g).astype(np.float32)
 
 
+def synthetic_records(rng, rect, depth, opacity_range=(0.01, 1.0)):
+    """Projected records (u, v, a, b, c, o, tz, cut) for binning inputs (no
+    projection arithmetic): the mean uniform over the rect's pixel span
+    widened by 8 px, a random positive-definite conic (principal standard
+    deviations 1-40 px at a random angle), opacity uniform in
+    ``opacity_range``, depth as given and the tile-test cutoff
+    2 ln(255 o) 1.001 + 0.01.  float32 [m, 8]."""
+    m = rect.shape[0]
+    x0, y0, x1, y1 = (rect[:, k].astype(np.float64) for k in range(4))
+    u = 16.0 * x0 - 8.0 + rng.random(m) * (16.0 * np.maximum(x1 - x0, 1) + 16.0)
+    v = 16.0 * y0 - 8.0 + rng.random(m) * (16.0 * np.maximum(y1 - y0, 1) + 16.0)
+    s1 = np.exp(rng.uniform(np.log(1.0), np.log(40.0), m))
+    s2 = np.exp(rng.uniform(np.log(1.0), np.log(40.0), m))
+    th = rng.uniform(0.0, np.pi, m)
+    ct, st = np.cos(th), np.sin(th)
+    # conic = R diag(1/s1^2, 1/s2^2) R^T
+    a = ct * ct / s1 ** 2 + st * st / s2 ** 2
+    b = ct * st * (1.0 / s1 ** 2 - 1.0 / s2 ** 2)
+    c = st * st / s1 ** 2 + ct * ct / s2 ** 2
+    o = rng.uniform(*opacity_range, m)
+    cut = 2.0 * np.log(255.0 * o) * 1.001 + 0.01
+    rec = np.stack([u, v, a, b, c, o, np.asarray(depth, np.float64), cut], -1)
+    return rec.astype(np.float32)
+
+
+def semantic_features_device(means, lo, hi, n_cells=64, dim=512, noise=0.02, seed=1005,
+                             out_dtype=None):
+    """The recipe of :func:`semantic_features` generated on the device of
+    ``means`` (a torch tensor [N, 3]) with torch's seeded generator, for maps
+    too large to build on the host (2M Gaussians x 512 channels): seeds and
+    centroids as there, nearest seed per Gaussian (ties to the lower index),
+    centroid plus N(0, noise^2) noise, renormalised.  The noise stream differs
+    from the host version's.  Returns [N, dim] in ``out_dtype`` (default
+    float32), built in chunks of 2^18 rows."""
+    import torch
+    rng = np.random.default_rng(seed)
+    lo, hi = np.asarray(lo, np.float64), np.asarray(hi, np.float64)
+    seeds = lo + (hi - lo) * rng.random((n_cells, 3))
+    cent = unit_rows(rng.standard_normal((n_cells, dim)))
+    dev = means.device
+    sd = torch.as_tensor(seeds, dtype=torch.float64, device=dev)
+    ct = torch.as_tensor(cent, dtype=torch.float32, device=dev)
+    gen = torch.Generator(device=dev).manual_seed(seed)
+    n = int(means.shape[0])
+    out = torch.empty((n, dim), dtype=out_dtype or torch.float32, device=dev)
+    for a in range(0, n, 1 << 18):
+        m = means[a:a + (1 << 18)].double()
+        d = ((m[:, None, :] - sd[None]) ** 2).sum(-1)           # [rows, n_cells]
+        best = torch.argmin(d, dim=1)                            # first minimum
+        g = ct[best] + noise * torch.randn((m.shape[0], dim), device=dev, generator=gen)
+        out[a:a + m.shape[0]] = (g / g.norm(dim=1, keepdim=True)).to(out.dtype)
+    return out
+
+
 def ae_init(widths_enc=(512, 256, 128, 64, 16), widths_dec=(16, 64, 128, 256, 512),
             seed: int = 3003):
     """Initial autoencoder weights, each layer (W [out, in], b [out]) ~

@@ -65,13 +65,14 @@ def test_project_matches_oracle(lgs, oracle_lib):
 # ---------------------------------------------------------------- binning
 
 def _bin_inputs(n, ncams, tx, ty, seed, tie_frac=0.1, empty=False):
+    """Seeded rects and depths with projected records whose ellipses reach
+    part of each rect (the tile test decides which tiles are binned)."""
     rng = np.random.default_rng(seed)
     rect, depth = synth.synthetic_projected(rng, n, ncams, tx, ty, max_extent=6,
                                             tie_frac=tie_frac)
     if empty:
         rect[:, 2] = rect[:, 0]
-    proj = np.zeros((ncams * n, 8), np.float32)
-    proj[:, 6] = depth
+    proj = synth.synthetic_records(rng, rect, depth)
     return rect, depth, proj
 
 
@@ -80,8 +81,11 @@ def _bin_inputs(n, ncams, tx, ty, seed, tie_frac=0.1, empty=False):
                                                 (70000, 2, 75, 43, 4), (3, 16, 2, 2, 5)])
 def test_bin_sort_bit_exact(lgs, oracle_lib, n, ncams, tx, ty, seed):
     rect, depth, proj = _bin_inputs(n, ncams, tx, ty, seed)
-    ref = oracle_lib.bin_sort(rect, depth, n, ncams, tx, ty)
+    ref = oracle_lib.bin_sort(rect, depth, n, ncams, tx, ty, proj=proj)
     k = len(ref["ids"])
+    if n > 100:  # the tile test drops part of the rects' tiles
+        area = ((rect[:, 2] - rect[:, 0]) * (rect[:, 3] - rect[:, 1])).sum()
+        assert 0 < k < area
     for cap in (k, k + 4099):
         bufs = lgs.BinBuffers(n, ncams, tx, ty, cap, "cuda", want_keys=True)
         lgs.gs_bin_sort(torch.from_numpy(proj).cuda(), torch.from_numpy(rect.astype(np.int16)).cuda(),
@@ -106,14 +110,14 @@ def test_bin_sort_long_segments_bit_exact(lgs, oracle_lib, tie_frac):
                                             tie_frac=tie_frac)
     sizes = [(0, 5000), (3, 12288), (10, 12289), (40, 30000)]  # (tile, instances)
     rect[2 * n:] = 0  # camera 2: only the long tiles
+    proj = synth.synthetic_records(rng, rect, depth)
     i0 = 2 * n
     for t, cnt in sizes:
         x, y = t % tx, t // tx
         rect[i0:i0 + cnt] = [x, y, x + 1, y + 1]
+        proj[i0:i0 + cnt, 0:2] = [16 * x + 8, 16 * y + 8]  # the mean inside: always reached
         i0 += cnt
-    proj = np.zeros((ncams * n, 8), np.float32)
-    proj[:, 6] = depth
-    ref = oracle_lib.bin_sort(rect, depth, n, ncams, tx, ty)
+    ref = oracle_lib.bin_sort(rect, depth, n, ncams, tx, ty, proj=proj)
     k = len(ref["ids"])
     counts = (ref["ranges"][:, 1] - ref["ranges"][:, 0]).reshape(ncams, -1)
     assert [int(counts[2, t]) for t, _ in sizes] == [c for _, c in sizes]
@@ -139,7 +143,7 @@ def test_bin_sort_empty_and_overflow(lgs, oracle_lib):
     assert int(_np(bufs.ranges).sum()) == 0
     # capacity one short of K: K is still reported, nothing is sorted
     rect, depth, proj = _bin_inputs(n, ncams, tx, ty, 12)
-    k = len(oracle_lib.bin_sort(rect, depth, n, ncams, tx, ty)["ids"])
+    k = len(oracle_lib.bin_sort(rect, depth, n, ncams, tx, ty, proj=proj)["ids"])
     bufs = lgs.BinBuffers(n, ncams, tx, ty, k - 1, "cuda")
     bufs.ranges.fill_(7)
     lgs.gs_bin_sort(torch.from_numpy(proj).cuda(), torch.from_numpy(rect.astype(np.int16)).cuda(),

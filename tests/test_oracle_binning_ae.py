@@ -50,6 +50,105 @@ def test_bin_sort_brute_force(oracle_lib, seed, n, ncams, tx, ty):
             assert tuple(out["ranges"][t]) == (0, 0)
 
 
+def _kept_pairs(out, n, ncams, tx, ty):
+    """(item, tile) pairs of a binning result (item = camera * n + index)."""
+    tiles = (out["keys"] >> np.uint64(32)).astype(np.int64)
+    cams = tiles // (tx * ty)
+    return set(zip((cams * n + out["ids"].astype(np.int64)).tolist(), tiles.tolist()))
+
+
+def _box_min_q(rec, t, tx):
+    """min over the tile's pixel-centre square of a dx^2 + 2 b dx dy + c dy^2,
+    d = (u - x, v - y), as a bounded linear least-squares problem (q = |L^T d|^2
+    with L L^T the conic), solved by scipy in float64."""
+    from scipy.optimize import lsq_linear
+    u, v, a, b, c = (float(x) for x in rec[:5])
+    x, y = t % tx, t // tx
+    Q = np.array([[a, b], [b, c]])
+    L = np.linalg.cholesky(Q)
+    lo = [u - (16 * x + 15.5), v - (16 * y + 15.5)]
+    hi = [u - (16 * x + 0.5), v - (16 * y + 0.5)]
+    r = lsq_linear(L.T, np.zeros(2), bounds=(lo, hi), tol=1e-14, lsq_solver="exact")
+    d = r.x
+    return float(d @ Q @ d)
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_bin_sort_tile_test(oracle_lib, seed):
+    """A tile of a record's rect is binned exactly when the record's ellipse
+    q(d) <= cut meets the tile's pixel-centre square: the minimum of q over the
+    square, found independently by bounded least squares, is below the cut
+    (1e-5 relative band for the FP32 decision); the kept instances come out in
+    the brute-force order."""
+    rng = np.random.default_rng(40 + seed)
+    n, ncams, tx, ty = 150, 2, 9, 7
+    rect, depth = synth.synthetic_projected(rng, n, ncams, tx, ty, max_extent=4, tie_frac=0.2)
+    rec = synth.synthetic_records(rng, rect, depth)
+    out = oracle_lib.bin_sort(rect, depth, n, ncams, tx, ty, proj=rec)
+    kept = _kept_pairs(out, n, ncams, tx, ty)
+    n_in, n_out = 0, 0
+    for i in range(ncams * n):
+        x0, y0, x1, y1 = rect[i]
+        cam = i // n
+        for yy in range(y0, y1):
+            for xx in range(x0, x1):
+                t = yy * tx + xx
+                qmin = _box_min_q(rec[i], t, tx)
+                cut = float(rec[i, 7])
+                inside = (i, cam * tx * ty + t) in kept
+                if qmin < cut * (1 - 1e-5) - 1e-6:
+                    assert inside, (i, t, qmin, cut)
+                    n_in += 1
+                elif qmin > cut * (1 + 1e-5) + 1e-6:
+                    assert not inside, (i, t, qmin, cut)
+                    n_out += 1
+    assert n_in > 100 and n_out > 100, (n_in, n_out)  # both sides exercised
+    # order: the brute-force sort of the kept instances
+    ref = [r for r in brute_force_bins(rect, depth, n, ncams, tx, ty)
+           if ((r[0] // (tx * ty)) * n + r[3], r[0]) in kept]
+    np.testing.assert_array_equal(out["ids"], [r[3] for r in ref])
+    np.testing.assert_array_equal(out["keys"] >> np.uint64(32), [r[0] for r in ref])
+
+
+def test_tile_test_keeps_every_contributing_pixel(oracle_lib):
+    """Conservative: every pixel where a Gaussian passes the skip threshold
+    (o exp(power) >= 1/255, FP64 projection) lies in a tile binned for it,
+    with the records rounded to FP32 and the cutoff formed as the GPU forms
+    it."""
+    scene, cams = synth.tiny()
+    cam = cams[0]
+    o = oracle_lib.project(scene, cam)
+    valid = o["valid"] == 1
+    n = scene.n
+    rec = np.zeros((n, 8), np.float32)
+    rec[:, 0:2] = o["mean2d"]
+    rec[:, 2:5] = o["conic"]
+    rec[:, 5] = o["opacity"]
+    rec[:, 6] = o["depth"]
+    op32 = rec[:, 5]
+    with np.errstate(divide="ignore"):
+        rec[:, 7] = (np.float32(2) * np.log(np.float32(255) * op32)).astype(np.float32) * \
+            np.float32(1.001) + np.float32(0.01)
+    rect = np.where(valid[:, None], o["rect"], 0).astype(np.int32)
+    tx, ty = (cam.width + 15) // 16, (cam.height + 15) // 16
+    out = oracle_lib.bin_sort(rect, rec[:, 6], n, 1, tx, ty, proj=rec)
+    kept = _kept_pairs(out, n, 1, tx, ty)
+    assert len(kept) < int(((rect[:, 2] - rect[:, 0]) * (rect[:, 3] - rect[:, 1])).sum())
+    ys, xs = np.mgrid[0:cam.height, 0:cam.width]
+    px, py = xs + 0.5, ys + 0.5
+    checked = 0
+    for i in np.nonzero(valid)[0]:
+        a, b, c = o["conic"][i]
+        dx, dy = o["mean2d"][i, 0] - px, o["mean2d"][i, 1] - py
+        power = -0.5 * (a * dx * dx + c * dy * dy) - b * dx * dy
+        hit = o["opacity"][i] * np.exp(np.minimum(power, 0.0)) >= 1.0 / 255.0
+        hit &= power <= 0.0
+        for t in np.unique((ys[hit] // 16) * tx + xs[hit] // 16):
+            assert (i, int(t)) in kept, (i, t)
+            checked += 1
+    assert checked > 1000
+
+
 def test_bin_sort_invariants_and_ties(oracle_lib):
     rng = np.random.default_rng(7)
     n, ncams, tx, ty = 3000, 2, 12, 9

@@ -406,8 +406,9 @@ def measure_outdoor(args, flush, dev, world, k=8, warm=3):
     """The outdoor-scale window: 2M Gaussians in a 40x40x8 m volume, 8
     keyframes of 1200x680 (6.53 Mpx), BF16 channels, the 16-d render with the
     feature term through the decoder (Eq. 2), plus one online autoencoder
-    step (RECON, 65,536 pixels of the window's maps) per window; against the
-    plain path that renders all 512 channels, with the decoded 16-d
+    step (RECON, 65,536 pixels of the window's maps) per window, after a
+    pretraining of twice the room's steps; against the plain path that
+    renders all 512 channels, with the decoded 16-d
     features' cosine error against the plain FP32 render of the first
     keyframe.  The 512-d semantic field is generated on the device (same
     recipe as the room's, 64 Voronoi cells of the volume)."""
@@ -429,7 +430,8 @@ def measure_outdoor(args, flush, dev, world, k=8, warm=3):
     model = AutoEncoder(enc, dec, device=dev)
     train = torch.cat(frames)
     gen = torch.Generator(device=dev).manual_seed(11)
-    for _ in range(args.ae_steps):
+    # the outdoor window's maps hold 2.7x the room's pixels: twice the steps
+    for _ in range(2 * args.ae_steps):
         idx = torch.randint(0, train.shape[0], (65536,), device=dev, generator=gen)
         model.train_step(train[idx].contiguous(), lr=5e-3)
     batch = train[torch.randint(0, train.shape[0], (65536,), device=dev, generator=gen)].contiguous()
@@ -602,7 +604,14 @@ TRAFFIC_SOURCES = {
     "ae_decode": ("ae_fused.cu", "tc05.cuh", "common.cuh", "kernels.cuh"),
     "gs_render_bwd": ("render.cu", "project.cu", "common.cuh", "kernels.cuh"),
 }
-TRAFFIC = {}  # call group -> (bytes per launch, source digest)
+TRAFFIC = {  # call group -> (bytes per launch, source digest)
+    "gs_project": (13216256, "b0870be7d414"),
+    "gs_bin_sort": (33331200, "6e6478235036"),
+    "gs_render_fwd": (5515520, "ae3ca3e45e19"),
+    "l1_losses": (9849088, "792f0809c2a4"),
+    "ae_decode": (350366976, "d33ac27a21a1"),
+    "gs_render_bwd": (41208064, "83aa7b383d4a"),
+}
 
 
 def source_digest(group):

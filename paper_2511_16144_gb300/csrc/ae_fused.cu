@@ -146,9 +146,10 @@ __device__ unsigned g_fused_error;
 constexpr int kEpiWarps = 16;
 constexpr int kFusedThreads = (kEpiWarps + 3) * 32;   // + MMA warp + two producer warps
 // barriers: full[kStages], empty[kStages], accH, accT, opH, opT, ybar[2],
-// dyfree, drain, then the TMEM slot
-constexpr uint32_t kBarBytes = (2 * kStages + 8) * 8 + 4;
-constexpr uint32_t SM_BIAS = SM_BAR + 144;             // b4 | b5 | b6 | b7 (960 floats)
+// dyfree, drain, the slice barriers sh2[2], sh3[4], sd2[2], sd3[4], then the
+// TMEM slot
+constexpr uint32_t kBarBytes = (2 * kStages + 20) * 8 + 4;
+constexpr uint32_t SM_BIAS = SM_BAR + 240;             // b4 | b5 | b6 | b7 (960 floats)
 constexpr uint32_t SM_ALL = SM_BIAS + 960 * 4;
 static_assert(kBarBytes <= SM_BIAS - SM_BAR, "barrier block overlaps the biases");
 static_assert(SM_ALL <= 232448, "shared-memory map exceeds 227 KB");
@@ -191,7 +192,13 @@ decode_fused_kernel(const __grid_constant__ FusedArgs a) {
   uint64_t* ybar = opT + 1;             // [2] output chunk ready in TMEM buffer c & 1
   uint64_t* dyfree = ybar + 2;          // the backward product of the last dy chunk is done
   uint64_t* drain = dyfree + 1;         // a give-up waits here for the MMAs already issued
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(drain + 1);
+  // epilogue -> MMA, one phase per tile: 64-column slice s of h2 / h3 / d2 / d3
+  // written (the next GEMM's K-slices start as soon as theirs are in)
+  uint64_t* sh2 = drain + 1;            // [2]
+  uint64_t* sh3 = sh2 + 2;              // [4]
+  uint64_t* sd2 = sh3 + 4;              // [2]
+  uint64_t* sd3 = sd2 + 2;              // [4]
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(sd3 + 4);
   float* sb = reinterpret_cast<float*>(sm + SM_BIAS);
   const float* sb4 = sb;
   const float* sb5 = sb + 64;
@@ -215,6 +222,7 @@ decode_fused_kernel(const __grid_constant__ FusedArgs a) {
     tc::mbar_init(&ybar[1], 1);
     tc::mbar_init(dyfree, 1);
     tc::mbar_init(drain, 1);
+    for (int i = 0; i < 12; i++) tc::mbar_init(&sh2[i], kEpiWarps);  // sh2 .. sd3
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   tc::fence_before();
@@ -271,6 +279,11 @@ decode_fused_kernel(const __grid_constant__ FusedArgs a) {
       if (ok && tc::elect_one()) tc::commit(bar);
       __syncwarp();
     };
+    // a slice barrier completes once per tile: parity = the tile's parity
+    auto wait_slice = [&](uint64_t* bar, uint32_t parity) {
+      ok = ok && __all_sync(0xffffffffu, tc::mbar_wait(bar, parity, kLimit));
+      tc::fence_after();
+    };
     // one weight unit: B = ring stage, A = activation tile at a_off (width
     // a_kw) from column k0, D = TMEM column dcol, N = n, K = kc
     auto unit = [&](uint32_t a_off, int a_kw, int k0, int kc, int n, uint32_t dcol, bool fresh) {
@@ -293,7 +306,10 @@ decode_fused_kernel(const __grid_constant__ FusedArgs a) {
     // forward hidden layers into TMEM columns 256-511 (z in buffer zb)
     auto f1 = [&](uint32_t zb) { unit(zb, 16, 0, 16, 64, 256, true); commit(accH); };
     auto f2 = [&]() { unit(SM_H1, 64, 0, 64, 128, 256, true); commit(accH); };
-    auto f3 = [&]() {
+    // F3 overwrites TMEM columns 256-511, where E2 reads F2's accumulator
+    // until its last slice: it waits for both slices of h2
+    auto f3 = [&](uint32_t parity) {
+      wait_slice(&sh2[1], parity);                                   // h2 staged
       for (int k = 0; k < 4; k++) unit(SM_H2, 128, 32 * k, 32, 256, 256, k == 0);
       commit(accH);
     };
@@ -302,20 +318,24 @@ decode_fused_kernel(const __grid_constant__ FusedArgs a) {
       f1(SM_Z);
       wait_on(opH, nopH);                                            // h1 staged
       f2();
-      wait_on(opH, nopH);                                            // h2 staged
-      f3();
+      f3(0);
     }
     int64_t k = 0;
     for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x, k++) {
       const bool next = t + gridDim.x < ntiles;
       const uint32_t zc = SM_Z + (uint32_t)(k & 1) * 4096, zn = SM_Z + (uint32_t)((k + 1) & 1) * 4096;
-      wait_on(opH, nopH);                                            // h3 staged
+      const uint32_t par = (uint32_t)(k & 1);
       if (k > 0) wait_on(opT, nopT);                                 // dz of the last tile read
       // output chunk c -> TMEM buffer c & 1, announced on ybar[c & 1]; each
-      // dy chunk's product is announced on dyfree (its buffer is free again)
+      // dy chunk's product is announced on dyfree (its buffer is free again).
+      // The first chunk's K-slices start as the slices of h3 land; it writes
+      // TMEM columns 256-383, which hold F3's columns 0-127 until E3 has read
+      // its slices 0 and 1, so its first MMA waits for slice 1
       auto f4 = [&](int c) {
-        for (int kk = 0; kk < 4; kk++)
+        for (int kk = 0; kk < 4; kk++) {
+          if (c == 0 && kk != 1) wait_slice(&sh3[kk == 0 ? 1 : kk], par);  // h3 slices staged
           unit(SM_H3, 256, 64 * kk, 64, 128, 256 + 128 * (c & 1), kk == 0);
+        }
         commit(&ybar[c & 1]);
       };
       f4(0);
@@ -329,16 +349,25 @@ decode_fused_kernel(const __grid_constant__ FusedArgs a) {
       }
       for (int kk = 0; kk < 4; kk++) unit(SM_H2, 128, 32 * kk, 32, 256, 256, kk == 0);  // R3
       commit(accT);
-      wait_on(opT, nopT);                                            // d3 written
-      for (int kk = 0; kk < 4; kk++) unit(SM_H3, 256, 64 * kk, 64, 128, 0, kk == 0);    // B2
+      // B2 writes TMEM columns 0-127, E5's dh3 input of slices 0 and 1: it
+      // starts after slice 1, its later K-slices as theirs land; R2 (columns
+      // 128-255) after the last
+      for (int kk = 0; kk < 4; kk++) {                                                   // B2
+        if (kk != 1) wait_slice(&sd3[kk == 0 ? 1 : kk], par);        // d3 slices written
+        unit(SM_H3, 256, 64 * kk, 64, 128, 0, kk == 0);
+      }
       unit(SM_H1, 64, 0, 64, 128, 128, true);                        // R2
       commit(accT);
       if (next) {
         wait_on(opH, nopH);                                          // next z staged
         f1(zn);
       }
-      wait_on(opT, nopT);                                            // d2 written
-      for (int kk = 0; kk < 2; kk++) unit(SM_H2, 128, 64 * kk, 64, 64, 0, kk == 0);      // B3
+      // B3 writes TMEM columns 0-63 (E6's slice 0 input); R1 (64-127) after
+      // slice 1
+      for (int kk = 0; kk < 2; kk++) {                                                   // B3
+        wait_slice(&sd2[kk], par);                                   // d2 slice written
+        unit(SM_H2, 128, 64 * kk, 64, 64, 0, kk == 0);
+      }
       unit(zc, 16, 0, 16, 64, 64, true);                             // R1
       commit(accT);
       if (next) {
@@ -348,10 +377,7 @@ decode_fused_kernel(const __grid_constant__ FusedArgs a) {
       wait_on(opT, nopT);                                            // d1 written
       unit(SM_DY, 64, 0, 64, 16, 0, true);                           // B4
       commit(accT);
-      if (next) {
-        wait_on(opH, nopH);                                          // next h2 staged
-        f3();
-      }
+      if (next) f3(par ^ 1u);
     }
     if (!ok) {  // the MMAs issued so far finish before TMEM is released
       if (lane == 0) atomicOr(&g_fused_error, 2u);
@@ -424,17 +450,20 @@ decode_fused_kernel(const __grid_constant__ FusedArgs a) {
     // GELU of NS consecutive 16-column slices from column c0 of the forward
     // accumulator into the BF16 tile (width kw); the next slice's TMEM load
     // is in flight while a slice is computed
-    auto gelu_slices = [&](auto ns, int c0, const float* bias, uint8_t* tile, int kw) {
+    // slice s of NS: columns c0 + 64 s .. + 15 of this warp (the four column
+    // quarters together write 64-column slice s, announced on bars[s])
+    auto gelu_slices = [&](auto ns, int c0, const float* bias, uint8_t* tile, int kw,
+                           uint64_t* bars) {
       constexpr int NS = decltype(ns)::value;
       uint32_t ra[16], rb[16];
       tc::tmem_ld16_issue(tb + 256 + c0, ra);
       tc::tmem_wait16(ra);
 #pragma unroll
       for (int s2 = 0; s2 < NS; s2++) {
-        const int cc = c0 + 16 * s2;
+        const int cc = c0 + 64 * s2;
         uint32_t* cur = (s2 & 1) ? rb : ra;
         uint32_t* nxt = (s2 & 1) ? ra : rb;
-        if (s2 + 1 < NS) tc::tmem_ld16_issue(tb + 256 + cc + 16, nxt);
+        if (s2 + 1 < NS) tc::tmem_ld16_issue(tb + 256 + cc + 64, nxt);
 #pragma unroll
         for (int i = 0; i < 16; i += 2) {
           const float2 g = gelu_tanh2(
@@ -444,18 +473,17 @@ decode_fused_kernel(const __grid_constant__ FusedArgs a) {
           v[i + 1] = g.y;
         }
         put_row<16>(tile, r, cc, kw, v);
+        arrive(&bars[s2]);
         if (s2 + 1 < NS) tc::tmem_wait16(nxt);
       }
     };
     auto e2 = [&]() {
       wait_acc(accH, nH);
-      gelu_slices(std::integral_constant<int, 2>(), 32 * qq, sb5, sm + SM_H2, 128);
-      arrive(opH);
+      gelu_slices(std::integral_constant<int, 2>(), 16 * qq, sb5, sm + SM_H2, 128, sh2);
     };
     auto e3 = [&]() {
       wait_acc(accH, nH);
-      gelu_slices(std::integral_constant<int, 4>(), 64 * qq, sb6, sm + SM_H3, 256);
-      arrive(opH);
+      gelu_slices(std::integral_constant<int, 4>(), 16 * qq, sb6, sm + SM_H3, 256, sh3);
     };
     // F_gt of output chunk c of tile t, loaded coalesced: slot i holds row
     // 8 i + lane / 4 of this warp's 32 rows, 16-byte piece lane % 4 of its
@@ -562,18 +590,19 @@ decode_fused_kernel(const __grid_constant__ FusedArgs a) {
       }
       ok = ok && tc::mbar_wait(dyfree, 1, kLimit);  // the last chunk's phase
       tc::fence_after();
-      // E5: d3 = dh3 * gelu'(pre3)
+      // E5: d3 = dh3 * gelu'(pre3), 64-column slice s by all 16 warps in step
+      // s (this warp: columns 16 qq + 64 s ..), each slice announced on sd3[s]
       wait_acc(accT, nT);
-      {  // the next 16 columns' loads are in flight while these are computed
+      {  // the next slice's loads are in flight while this one is computed
         uint32_t ra[32], rb[32];
-        tc::tmem_ld16x2_issue(tb + 64 * qq, tb + 256 + 64 * qq, ra);
+        tc::tmem_ld16x2_issue(tb + 16 * qq, tb + 256 + 16 * qq, ra);
         tc::tmem_wait32(ra);
 #pragma unroll
         for (int s2 = 0; s2 < 4; s2++) {
-          const int c0 = 64 * qq + 16 * s2;
+          const int c0 = 16 * qq + 64 * s2;
           uint32_t* cur = (s2 & 1) ? rb : ra;
           uint32_t* nxt = (s2 & 1) ? ra : rb;
-          if (s2 < 3) tc::tmem_ld16x2_issue(tb + c0 + 16, tb + 256 + c0 + 16, nxt);
+          if (s2 < 3) tc::tmem_ld16x2_issue(tb + c0 + 64, tb + 256 + c0 + 64, nxt);
 #pragma unroll
           for (int i = 0; i < 16; i += 2) {
             const float2 g = gelu_tanh_grad2(__fadd2_rn(
@@ -585,23 +614,23 @@ decode_fused_kernel(const __grid_constant__ FusedArgs a) {
             v[i + 1] = d.y;
           }
           put_row<16>(sm + SM_H3, r, c0, 256, v);
+          arrive(&sd3[s2]);
           if (s2 < 3) tc::tmem_wait32(nxt);
         }
       }
-      arrive(opT);
       if (next) stage_z(t + gridDim.x, SM_Z + (uint32_t)((k + 1) & 1) * 4096);
-      // E6: d2 = dh2 * gelu'(pre2)
+      // E6: d2 = dh2 * gelu'(pre2), 64-column slices as in E5, on sd2[s]
       wait_acc(accT, nT);
       {
         uint32_t ra[32], rb[32];
-        tc::tmem_ld16x2_issue(tb + 32 * qq, tb + 128 + 32 * qq, ra);
+        tc::tmem_ld16x2_issue(tb + 16 * qq, tb + 128 + 16 * qq, ra);
         tc::tmem_wait32(ra);
 #pragma unroll
         for (int s2 = 0; s2 < 2; s2++) {
-          const int c0 = 32 * qq + 16 * s2;
+          const int c0 = 16 * qq + 64 * s2;
           uint32_t* cur = (s2 & 1) ? rb : ra;
           uint32_t* nxt = (s2 & 1) ? ra : rb;
-          if (s2 < 1) tc::tmem_ld16x2_issue(tb + c0 + 16, tb + 128 + c0 + 16, nxt);
+          if (s2 < 1) tc::tmem_ld16x2_issue(tb + c0 + 64, tb + 128 + c0 + 64, nxt);
 #pragma unroll
           for (int i = 0; i < 16; i += 2) {
             const float2 g = gelu_tanh_grad2(__fadd2_rn(
@@ -613,10 +642,10 @@ decode_fused_kernel(const __grid_constant__ FusedArgs a) {
             v[i + 1] = d.y;
           }
           put_row<16>(sm + SM_H2, r, c0, 128, v);
+          arrive(&sd2[s2]);
           if (s2 < 1) tc::tmem_wait32(nxt);
         }
       }
-      arrive(opT);
       if (next) e1();
       // E7: d1 = dh1 * gelu'(pre1), into the dy buffer (free once R3 is done)
       wait_acc(accT, nT);

@@ -104,10 +104,14 @@ __device__ __forceinline__ void for_each_hit(const float4* __restrict__ proj,
                                              const ushort4* __restrict__ rect, int64_t i0,
                                              int64_t i1, int tiles_x, F&& fn) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int64_t g = i0 + (int64_t)warp * 32; g < i1; g += (int64_t)nw * 32) {
+  int64_t g = i0 + (int64_t)warp * 32;
+  ushort4 rn = make_ushort4(0, 0, 0, 0);
+  if (g + lane < i1) rn = rect[g + lane];
+  for (; g < i1; g += (int64_t)nw * 32) {
     const int64_t i = g + lane;
-    ushort4 r = make_ushort4(0, 0, 0, 0);
-    if (i < i1) r = rect[i];
+    const ushort4 r = rn;
+    rn = make_ushort4(0, 0, 0, 0);  // the next group's rects are in flight meanwhile
+    if (g + (int64_t)nw * 32 + lane < i1) rn = rect[g + (int64_t)nw * 32 + lane];
     const uint32_t w = r.z > r.x ? (uint32_t)(r.z - r.x) : 0u;
     const uint32_t area = r.w > r.y ? w * (uint32_t)(r.w - r.y) : 0u;
     uint32_t incl = area;

@@ -9,13 +9,17 @@
 // Because every tile's segment can be sorted on its own, there is no global
 // sort:
 //   1. count the instances of every tile (shared-memory histograms per
-//      block of contiguous items when the tiles fit, else global atomics)
-//      and the total K;
+//      block of contiguous items when a camera's tiles fit, else global
+//      atomics) and the total K, keeping for every rect of at most 32 tiles
+//      the mask of the tiles it hits;
 //   2. one block scans the counts into segment starts, writes the ranges and
 //      the write cursors (all ranges stay (0, 0) when K > capacity);
 //   3. every item appends (depth bits, index) to each of its tiles' segments
 //      (a block reserves one range per tile, then fills it with shared-
-//      memory atomics; the order inside a segment is arbitrary);
+//      memory atomics; the order inside a segment is arbitrary), the small
+//      rects from their masks;
+//   Both passes spread the (item, tile) pairs of each group of 256 items
+//   evenly over the block's threads.
 //   4. one block per tile sorts its segment's 64-bit (depth bits, index)
 //      keys with a stable LSD radix sort in shared memory and writes the
 //      Gaussian indices: 256-thread blocks take the segments of up to 4,096
@@ -41,7 +45,9 @@ constexpr int kLargeThreads = 1024;    // blocks for the longer segments
 constexpr int kLargeItems = 12;        // keys per thread: 12,288 in shared memory
 constexpr int kLargeBlocks = 2 * 152;  // persistent grid over the list of long segments
 constexpr int kSmemTiles = 32768;      // per-block tile tables (4 B each) up to this many tiles
-constexpr int kItemBlocks = 2 * 152;   // blocks of the count and emit passes
+constexpr int kItemThreads = 256;      // threads (and items per group) of the count and emit passes
+constexpr int kItemBlocks = 4 * 152;   // blocks of the count and emit passes
+constexpr int kMaskTiles = 32;         // rects of at most this many tiles keep a hit mask
 constexpr int kScanThreads = 1024;
 
 __device__ __forceinline__ bool rect_empty(const ushort4& r) { return r.z <= r.x || r.w <= r.y; }
@@ -92,64 +98,129 @@ __device__ __forceinline__ bool tile_hit(const Ell& E, uint32_t tx, uint32_t ty)
   return best <= E.cut;
 }
 
-// Calls fn(i, t, E) for every (item, tile) pair of the items [i0, i1) whose
-// ellipse reaches the tile (t = tile index within the camera).  The rect
-// tiles of each group of 32 consecutive items are flattened (item order,
-// then row-major tile order) and spread evenly over the warp's lanes, so a
-// few large splats do not hold a whole warp back; each pair finds its item
-// by a binary search over the group's running tile counts and reads the
-// item's fields from the owning lane.
-template <typename F>
-__device__ __forceinline__ void for_each_hit(const float4* __restrict__ proj,
+// One group of kItemThreads consecutive items staged in shared memory for
+// the block-wide pair expansion: each item's ellipse record, rect origin and
+// width in tiles, rect area, hit mask, and the group's running pair counts.
+struct GroupSmem {
+  float4 e0[kItemThreads];      // u, v, a, b
+  float4 e1[kItemThreads];      // c, 1/a, 1/c, cut
+  float tz[kItemThreads];       // depth (the emitted key)
+  uint32_t incl[kItemThreads];  // pairs of the items up to and including this one
+  uint32_t xy[kItemThreads];    // rect origin: x | y << 16
+  uint32_t w[kItemThreads];     // rect width in tiles
+  uint32_t area[kItemThreads];  // rect tiles
+  uint32_t mask[kItemThreads];  // hit bits over the rect tiles (rects of at most kMaskTiles)
+  uint32_t wsum[kItemThreads / 32];
+};
+
+__device__ __forceinline__ Ell staged_ell(const GroupSmem& S, int k) {
+  const float4 a = S.e0[k], b = S.e1[k];
+  return Ell{a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w, S.tz[k]};
+}
+
+// idx = q w + r for idx < 2^20: a product with the reciprocal of w, then one
+// exact integer correction (the product's error is below one).
+__device__ __forceinline__ void tile_of(uint32_t idx, uint32_t w, uint32_t area, uint32_t& q,
+                                        uint32_t& r) {
+  if (area >= (1u << 20)) {
+    q = idx / w;
+    r = idx - q * w;
+    return;
+  }
+  q = (uint32_t)__fmul_rn((float)idx, __frcp_rn((float)w));
+  int32_t rr = (int32_t)idx - (int32_t)(q * w);
+  if (rr < 0) {
+    q--;
+    rr += (int32_t)w;
+  } else if (rr >= (int32_t)w) {
+    q++;
+    rr -= (int32_t)w;
+  }
+  r = (uint32_t)rr;
+}
+
+// Position of the r-th set bit (from 0) of m; m has more than r set bits.
+__device__ __forceinline__ uint32_t nth_set_bit(uint32_t m, uint32_t r) {
+  uint32_t pos = 0;
+#pragma unroll
+  for (int s = 16; s > 0; s >>= 1) {
+    const uint32_t c = __popc(m & ((1u << s) - 1u));
+    if (r >= c) {
+      r -= c;
+      pos += s;
+      m >>= s;
+    }
+  }
+  return pos;
+}
+
+// Visits the pairs of the items [i0, i1), group by group of kItemThreads
+// items: every thread stages its item (stage(slot, i, area) returns the
+// item's pair count), the block scans the counts, and the pairs of the whole
+// group are spread evenly over the block's threads, each finding its item by
+// a binary search over the running counts -- so a splat over hundreds of
+// tiles is shared by all warps instead of holding one back.  pair(slot, p,
+// active, i) (pair p of item i) runs on every thread in every round (active false past the
+// group's last pair, so that warp votes see converged warps); done(slot, i)
+// runs once per item after its group.
+template <typename Stage, typename Pair, typename Done>
+__device__ __forceinline__ void expand_items(const float4* __restrict__ proj,
                                              const ushort4* __restrict__ rect, int64_t i0,
-                                             int64_t i1, int tiles_x, F&& fn) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  int64_t g = i0 + (int64_t)warp * 32;
+                                             int64_t i1, GroupSmem& S, Stage&& stage, Pair&& pair,
+                                             Done&& done) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   ushort4 rn = make_ushort4(0, 0, 0, 0);
-  if (g + lane < i1) rn = rect[g + lane];
-  for (; g < i1; g += (int64_t)nw * 32) {
-    const int64_t i = g + lane;
+  if (i0 + tid < i1) rn = rect[i0 + tid];
+  for (int64_t g = i0; g < i1; g += kItemThreads) {
+    const int64_t i = g + tid;
     const ushort4 r = rn;
     rn = make_ushort4(0, 0, 0, 0);  // the next group's rects are in flight meanwhile
-    if (g + (int64_t)nw * 32 + lane < i1) rn = rect[g + (int64_t)nw * 32 + lane];
+    if (i + kItemThreads < i1) rn = rect[i + kItemThreads];
     const uint32_t w = r.z > r.x ? (uint32_t)(r.z - r.x) : 0u;
     const uint32_t area = r.w > r.y ? w * (uint32_t)(r.w - r.y) : 0u;
-    uint32_t incl = area;
+    uint32_t work = 0;
+    if (area) {  // (rects past i1 are empty)
+      const float4 r0 = proj[2 * i], r1 = proj[2 * i + 1];
+      S.e0[tid] = r0;
+      S.e1[tid] = make_float4(r1.x, __frcp_rn(r0.z), __frcp_rn(r1.x), r1.w);
+      S.tz[tid] = r1.z;
+      S.xy[tid] = (uint32_t)r.x | ((uint32_t)r.y << 16);
+      S.w[tid] = w;
+      S.area[tid] = area;
+      work = stage(tid, i, area);
+    }
+    uint32_t incl = work;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
       const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
       if (lane >= o) incl += y;
     }
-    const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
-    if (total == 0) continue;
-    Ell E{0.f, 0.f, 1.f, 0.f, 1.f, 1.f, 1.f, 0.f, 0.f};
-    if (area) E = ell_of(proj[2 * i], proj[2 * i + 1]);
-    const uint32_t excl = incl - area;
-    const uint32_t xy = (uint32_t)r.x | ((uint32_t)r.y << 16);
-    for (uint32_t j0 = 0; j0 < total; j0 += 32) {
-      const uint32_t j = j0 + (uint32_t)lane;
-      int k = 0;  // the first lane whose running count exceeds j
+    if (lane == 31) S.wsum[warp] = incl;
+    __syncthreads();
+    uint32_t off = 0, total = 0;
 #pragma unroll
-      for (int step = 16; step > 0; step >>= 1)
-        if (__shfl_sync(0xffffffffu, incl, k + step - 1) <= j) k += step;
-      Ell F;
-      F.u = __shfl_sync(0xffffffffu, E.u, k);
-      F.v = __shfl_sync(0xffffffffu, E.v, k);
-      F.a = __shfl_sync(0xffffffffu, E.a, k);
-      F.b = __shfl_sync(0xffffffffu, E.b, k);
-      F.c = __shfl_sync(0xffffffffu, E.c, k);
-      F.ia = __shfl_sync(0xffffffffu, E.ia, k);
-      F.ic = __shfl_sync(0xffffffffu, E.ic, k);
-      F.cut = __shfl_sync(0xffffffffu, E.cut, k);
-      F.tz = __shfl_sync(0xffffffffu, E.tz, k);
-      const uint32_t kxy = __shfl_sync(0xffffffffu, xy, k);
-      const uint32_t kw = __shfl_sync(0xffffffffu, w, k);
-      const uint32_t local = j - __shfl_sync(0xffffffffu, excl, k);
-      if (j < total) {
-        const uint32_t ty = (kxy >> 16) + local / kw, tx = (kxy & 0xffffu) + local % kw;
-        if (tile_hit(F, tx, ty)) fn(g + k, ty * (uint32_t)tiles_x + tx, F);
-      }
+    for (int q = 0; q < kItemThreads / 32; q++) {
+      const uint32_t v = S.wsum[q];
+      off += q < warp ? v : 0u;
+      total += v;
     }
+    S.incl[tid] = incl + off;
+    __syncthreads();
+    for (uint32_t j0 = 0; j0 < total; j0 += kItemThreads) {
+      const uint32_t j = j0 + (uint32_t)tid;
+      const bool active = j < total;
+      int k = 0;
+      uint32_t p = 0;
+      if (active) {  // the first item whose running count exceeds j
+#pragma unroll
+        for (int step = kItemThreads / 2; step > 0; step >>= 1)
+          if (S.incl[k + step - 1] <= j) k += step;
+        p = j - (k ? S.incl[k - 1] : 0u);
+      }
+      pair(k, p, active, g + k);
+    }
+    __syncthreads();  // the group's tables are read; the next group may restage them
+    if (i < i1) done(tid, i);
   }
 }
 
@@ -165,42 +236,71 @@ __device__ __forceinline__ void cam_chunk(uint32_t n, uint32_t c, int64_t& i0, i
   i1 = (int64_t)c * n + (a + per < (int64_t)n ? a + per : (int64_t)n);
 }
 
-// 1. per-tile instance counts and K.
-__global__ void __launch_bounds__(256)
+// 1. per-tile instance counts, K, and the hit masks of the small rects.
+__global__ void __launch_bounds__(kItemThreads)
 tile_count_kernel(const float4* __restrict__ proj, const ushort4* __restrict__ rect, int64_t m,
-                  uint32_t n, int tiles_x, uint32_t tiles, uint32_t n_tiles_all,
+                  uint32_t n, int tiles_x, uint32_t tiles, bool local,
                   uint32_t* __restrict__ counts, uint32_t* __restrict__ block_counts,
-                  unsigned long long* __restrict__ total) {
-  extern __shared__ uint32_t s_cnt[];  // n_tiles_all entries when they fit
-  const bool local = n_tiles_all <= (uint32_t)kSmemTiles;
-  if (local) {
-    for (uint32_t t = threadIdx.x; t < n_tiles_all; t += blockDim.x) s_cnt[t] = 0;
-    __syncthreads();
-  }
+                  uint32_t* __restrict__ masks, unsigned long long* __restrict__ total) {
+  __shared__ GroupSmem S;
+  extern __shared__ uint32_t s_cnt[];  // this camera's tiles, when they fit
+  const int lane = threadIdx.x & 31;
   unsigned long long k = 0;
   const uint32_t n_cams = (uint32_t)(m / n);
   for (uint32_t c = 0; c < n_cams; c++) {
+    if (local) {
+      for (uint32_t t = threadIdx.x; t < tiles; t += blockDim.x) s_cnt[t] = 0;
+      __syncthreads();
+    }
     int64_t i0, i1;
     cam_chunk(n, c, i0, i1);
     const uint32_t base = c * tiles;
-    for_each_hit(proj, rect, i0, i1, tiles_x, [&](int64_t, uint32_t tt, const Ell&) {
-      const uint32_t t = base + tt;
-      if (local) atomicAdd(&s_cnt[t], 1u);
-      else atomicAdd(&counts[t], 1u);
-      k++;
-    });
+    expand_items(
+        proj, rect, i0, i1, S,
+        [&](int slot, int64_t, uint32_t area) {
+          S.mask[slot] = 0;
+          return area;
+        },
+        [&](int slot, uint32_t p, bool active, int64_t) {
+          bool hit = false;
+          uint32_t area = 0;
+          if (active) {
+            area = S.area[slot];
+            uint32_t qy, qx;
+            tile_of(p, S.w[slot], area, qy, qx);
+            const uint32_t xy = S.xy[slot];
+            const uint32_t tx = (xy & 0xffffu) + qx, ty = (xy >> 16) + qy;
+            hit = tile_hit(staged_ell(S, slot), tx, ty);
+            if (hit) {
+              const uint32_t tt = ty * (uint32_t)tiles_x + tx;
+              if (local) atomicAdd(&s_cnt[tt], 1u);
+              else atomicAdd(&counts[base + tt], 1u);
+              k++;
+            }
+          }
+          // the lanes holding a small rect's pairs are consecutive: the first
+          // of them ORs the run's hit bits into the rect's mask
+          const uint32_t bal = __ballot_sync(0xffffffffu, hit);
+          if (active && area <= (uint32_t)kMaskTiles && (p == 0 || lane == 0)) {
+            const uint32_t run = min(32u - (uint32_t)lane, area - p);
+            const uint32_t bits = (bal >> lane) & (run == 32 ? 0xffffffffu : (1u << run) - 1u);
+            if (bits) atomicOr(&S.mask[slot], bits << p);
+          }
+        },
+        [&](int slot, int64_t i) { masks[i] = S.mask[slot]; });
+    if (local) {  // this block's column of the [tile][block] counts, and the totals
+      __syncthreads();
+      for (uint32_t t = threadIdx.x; t < tiles; t += blockDim.x) {
+        const uint32_t v = s_cnt[t];
+        block_counts[(size_t)(base + t) * gridDim.x + blockIdx.x] = v;
+        if (v) atomicAdd(&counts[base + t], v);
+      }
+      __syncthreads();
+    }
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) k += __shfl_xor_sync(0xffffffffu, k, o);
-  if ((threadIdx.x & 31) == 0 && k) atomicAdd(total, k);
-  if (local) {  // this block's column of the [tile][block] counts, and the totals
-    __syncthreads();
-    for (uint32_t t = threadIdx.x; t < n_tiles_all; t += blockDim.x) {
-      const uint32_t c = s_cnt[t];
-      block_counts[(size_t)t * gridDim.x + blockIdx.x] = c;
-      if (c) atomicAdd(&counts[t], c);
-    }
-  }
+  if (lane == 0 && k) atomicAdd(total, k);
 }
 
 // 2. exclusive scan of the counts (one block): ranges, cursors, K.
@@ -284,34 +384,57 @@ block_base_kernel(const uint32_t* __restrict__ block_counts, int nblocks, uint32
   }
 }
 
-// 3. append (depth bits, Gaussian index) to every covered tile's segment.
-// With the tile tables in shared memory a block starts from its own bases
-// (block_base row) and places its instances with shared-memory atomics;
-// otherwise every instance reserves its slot with a global atomic.
-__global__ void __launch_bounds__(256)
+// 3. append (depth bits, Gaussian index) to every covered tile's segment:
+// the small rects walk the set bits of their hit masks, the others repeat
+// the tile test.  With the tile tables in shared memory a block starts from
+// its own bases (block_base row) and places its instances with shared-
+// memory atomics; otherwise every instance reserves its slot with a global
+// atomic.
+__global__ void __launch_bounds__(kItemThreads)
 tile_emit_kernel(const float4* __restrict__ proj, const ushort4* __restrict__ rect, int64_t m,
-                 uint32_t n, int tiles_x, uint32_t tiles, uint32_t n_tiles_all,
+                 uint32_t n, int tiles_x, uint32_t tiles, bool local,
                  const int64_t* __restrict__ sort_n, const uint32_t* __restrict__ block_base,
-                 uint32_t* __restrict__ cursor, unsigned long long* __restrict__ seg) {
-  extern __shared__ uint32_t s_cur[];  // [n_tiles_all] next slot of this block
+                 const uint32_t* __restrict__ masks, uint32_t* __restrict__ cursor,
+                 unsigned long long* __restrict__ seg) {
+  __shared__ GroupSmem S;
+  extern __shared__ uint32_t s_cur[];  // [tiles] next slot of this block in this camera
   if (*sort_n == 0) return;  // nothing fits (or nothing visible)
-  const bool local = n_tiles_all <= (uint32_t)kSmemTiles;
-  if (local) {
-    for (uint32_t t = threadIdx.x; t < n_tiles_all; t += blockDim.x)
-      s_cur[t] = block_base[(size_t)t * gridDim.x + blockIdx.x];
-    __syncthreads();
-  }
   const uint32_t n_cams = (uint32_t)(m / n);
   for (uint32_t c = 0; c < n_cams; c++) {
+    const uint32_t base = c * tiles;
+    if (local) {
+      for (uint32_t t = threadIdx.x; t < tiles; t += blockDim.x)
+        s_cur[t] = block_base[(size_t)(base + t) * gridDim.x + blockIdx.x];
+      __syncthreads();
+    }
     int64_t i0, i1;
     cam_chunk(n, c, i0, i1);
-    const uint32_t base = c * tiles;
     const int64_t item0 = (int64_t)c * n;
-    for_each_hit(proj, rect, i0, i1, tiles_x, [&](int64_t i, uint32_t tt, const Ell& E) {
-      const uint32_t t = base + tt;
-      const uint32_t pos = local ? atomicAdd(&s_cur[t], 1u) : atomicAdd(&cursor[t], 1u);
-      seg[pos] = ((unsigned long long)__float_as_uint(E.tz) << 32) | (uint32_t)(i - item0);
-    });
+    expand_items(
+        proj, rect, i0, i1, S,
+        [&](int slot, int64_t i, uint32_t area) {
+          if (area > (uint32_t)kMaskTiles) return area;
+          const uint32_t mk = masks[i];
+          S.mask[slot] = mk;
+          return (uint32_t)__popc(mk);
+        },
+        [&](int slot, uint32_t p, bool active, int64_t i) {
+          if (!active) return;
+          const uint32_t area = S.area[slot];
+          const bool small = area <= (uint32_t)kMaskTiles;
+          uint32_t qy, qx;
+          tile_of(small ? nth_set_bit(S.mask[slot], p) : p, S.w[slot], area, qy, qx);
+          const uint32_t xy = S.xy[slot];
+          const uint32_t tx = (xy & 0xffffu) + qx, ty = (xy >> 16) + qy;
+          const Ell E = staged_ell(S, slot);
+          if (small || tile_hit(E, tx, ty)) {
+            const uint32_t t = base + ty * (uint32_t)tiles_x + tx;
+            const uint32_t pos = local ? atomicAdd(&s_cur[t - base], 1u) : atomicAdd(&cursor[t], 1u);
+            seg[pos] = ((unsigned long long)__float_as_uint(E.tz) << 32) | (uint32_t)(i - item0);
+          }
+        },
+        [](int, int64_t) {});
+    if (local) __syncthreads();  // the cursors are reloaded for the next camera
   }
 }
 
@@ -706,11 +829,18 @@ tile_sort_large_kernel(const uint2* __restrict__ ranges, const uint32_t* __restr
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 struct BinLayout {
-  size_t counts, cursor, total, n_long, sort_n, zero_end, block_counts, block_base, long_tiles,
-      seg, scratch, size;
+  size_t counts, cursor, total, n_long, sort_n, zero_end, block_counts, block_base, masks,
+      long_tiles, seg, scratch, size;
+  bool local;  // per-block tile tables in shared memory
 };
 
-BinLayout bin_layout(uint64_t n_tiles_all, int64_t capacity) {
+// The per-block tables cover one camera's tiles at a time in shared memory;
+// their [tile][block] copies in the workspace are kept below 64 M entries.
+bool block_tables(uint64_t tiles, uint64_t n_tiles_all) {
+  return tiles <= (uint64_t)kSmemTiles && n_tiles_all * kItemBlocks <= (1ull << 26);
+}
+
+BinLayout bin_layout(uint64_t m, uint64_t tiles, uint64_t n_tiles_all, int64_t capacity) {
   BinLayout L;
   size_t o = 0;
   auto take = [&](size_t b) { size_t at = o; o += align256(b > 0 ? b : 1); return at; };
@@ -720,9 +850,10 @@ BinLayout bin_layout(uint64_t n_tiles_all, int64_t capacity) {
   L.zero_end = o;  // counts, total and the long-tile count start at zero
   L.sort_n = take(8);
   L.cursor = take(4 * n_tiles_all);
-  const bool local = n_tiles_all <= (uint64_t)kSmemTiles;
-  L.block_counts = take(local ? 4 * (size_t)kItemBlocks * n_tiles_all : 0);
-  L.block_base = take(local ? 4 * (size_t)kItemBlocks * n_tiles_all : 0);
+  L.local = block_tables(tiles, n_tiles_all);
+  L.block_counts = take(L.local ? 4 * (size_t)kItemBlocks * n_tiles_all : 0);
+  L.block_base = take(L.local ? 4 * (size_t)kItemBlocks * n_tiles_all : 0);
+  L.masks = take(4 * m);
   L.long_tiles = take(4 * n_tiles_all);
   L.seg = take(8 * (size_t)capacity);
   L.scratch = take(8 * (size_t)capacity);
@@ -730,8 +861,11 @@ BinLayout bin_layout(uint64_t n_tiles_all, int64_t capacity) {
   return L;
 }
 
-int grid_items(int64_t m) {
-  return (int)std::max<int64_t>(1, std::min<int64_t>((m + 1023) / 1024, kItemBlocks));
+// Blocks of the count and emit passes: every block takes a chunk of each
+// camera's n items.
+int grid_items(int64_t n) {
+  return (int)std::max<int64_t>(
+      1, std::min<int64_t>((n + kItemThreads - 1) / kItemThreads, kItemBlocks));
 }
 
 }  // namespace
@@ -750,7 +884,8 @@ using namespace lgs;
 extern "C" size_t gs_bin_sort_workspace(int64_t n, int n_cams, int tiles_x, int tiles_y,
                                         int64_t capacity) {
   if (n < 0 || n_cams < 1 || capacity < 0 || tiles_x < 1 || tiles_y < 1) return 0;
-  return bin_layout((uint64_t)n_cams * tiles_x * tiles_y, capacity).size;
+  const uint64_t tiles = (uint64_t)tiles_x * (uint64_t)tiles_y;
+  return bin_layout((uint64_t)n_cams * (uint64_t)n, tiles, (uint64_t)n_cams * tiles, capacity).size;
 }
 
 extern "C" lgs_status gs_bin_sort(const float* proj, const uint16_t* rect, int64_t n, int n_cams,
@@ -773,7 +908,7 @@ extern "C" lgs_status gs_bin_sort(const float* proj, const uint16_t* rect, int64
   const uint32_t tiles = (uint32_t)tiles_x * (uint32_t)tiles_y;
   LGS_CHECK_ARG((uint64_t)tiles * (uint64_t)n_cams <= (1ull << 24), "too many tiles");
   const uint32_t n_tiles_all = (uint32_t)n_cams * tiles;
-  const BinLayout L = bin_layout(n_tiles_all, capacity);
+  const BinLayout L = bin_layout((uint64_t)m, tiles, n_tiles_all, capacity);
   LGS_CHECK_ARG(workspace_bytes >= L.size, "workspace too small");
   cudaStream_t s = as_stream(stream);
   char* ws = (char*)workspace;
@@ -788,16 +923,17 @@ extern "C" lgs_status gs_bin_sort(const float* proj, const uint16_t* rect, int64
   unsigned long long* total = (unsigned long long*)(ws + L.total);
   int64_t* sort_n = (int64_t*)(ws + L.sort_n);
   unsigned long long* seg = (unsigned long long*)(ws + L.seg);
-  const bool local = n_tiles_all <= (uint32_t)kSmemTiles;
-  const size_t cnt_smem = local ? 4 * (size_t)n_tiles_all : 0;
+  const bool local = L.local;
+  const size_t cnt_smem = local ? 4 * (size_t)tiles : 0;
   LGS_CHECK_CUDA(set_smem_limit(reinterpret_cast<const void*>(tile_count_kernel), 4 * kSmemTiles));
   LGS_CHECK_CUDA(set_smem_limit(reinterpret_cast<const void*>(tile_emit_kernel), 4 * kSmemTiles));
   uint32_t* block_counts = (uint32_t*)(ws + L.block_counts);
   uint32_t* block_base = (uint32_t*)(ws + L.block_base);
-  const int nblk = grid_items(m);
-  tile_count_kernel<<<nblk, 256, cnt_smem, s>>>((const float4*)proj, (const ushort4*)rect, m,
-                                                (uint32_t)n, tiles_x, tiles, n_tiles_all, counts,
-                                                block_counts, total);
+  uint32_t* masks = (uint32_t*)(ws + L.masks);
+  const int nblk = grid_items(n);
+  tile_count_kernel<<<nblk, kItemThreads, cnt_smem, s>>>((const float4*)proj, (const ushort4*)rect,
+                                                         m, (uint32_t)n, tiles_x, tiles, local,
+                                                         counts, block_counts, masks, total);
   uint32_t* long_tiles = (uint32_t*)(ws + L.long_tiles);
   uint32_t* n_long = (uint32_t*)(ws + L.n_long);
   tile_scan_kernel<<<1, kScanThreads, 0, s>>>(counts, n_tiles_all, total, capacity,
@@ -810,9 +946,9 @@ extern "C" lgs_status gs_bin_sort(const float* proj, const uint16_t* rect, int64
   if (local)
     block_base_kernel<<<(n_tiles_all + 7) / 8, 256, 0, s>>>(block_counts, nblk, n_tiles_all,
                                                           cursor, sort_n, block_base);
-  tile_emit_kernel<<<nblk, 256, cnt_smem, s>>>((const float4*)proj, (const ushort4*)rect, m,
-                                               (uint32_t)n, tiles_x, tiles, n_tiles_all, sort_n,
-                                               block_base, cursor, seg);
+  tile_emit_kernel<<<nblk, kItemThreads, cnt_smem, s>>>((const float4*)proj, (const ushort4*)rect,
+                                                        m, (uint32_t)n, tiles_x, tiles, local,
+                                                        sort_n, block_base, masks, cursor, seg);
   using SmallSmem = SegSmem<kSegThreads, kSegMax / kSegThreads>;
   using LargeSmem = SegSmem<kLargeThreads, kLargeItems>;
   LGS_CHECK_CUDA(set_smem_limit(reinterpret_cast<const void*>(tile_sort_kernel),

@@ -64,11 +64,11 @@ def test_project_matches_oracle(lgs, oracle_lib):
 
 # ---------------------------------------------------------------- binning
 
-def _bin_inputs(n, ncams, tx, ty, seed, tie_frac=0.1, empty=False):
+def _bin_inputs(n, ncams, tx, ty, seed, tie_frac=0.1, empty=False, max_extent=6):
     """Seeded rects and depths with projected records whose ellipses reach
     part of each rect (the tile test decides which tiles are binned)."""
     rng = np.random.default_rng(seed)
-    rect, depth = synth.synthetic_projected(rng, n, ncams, tx, ty, max_extent=6,
+    rect, depth = synth.synthetic_projected(rng, n, ncams, tx, ty, max_extent=max_extent,
                                             tie_frac=tie_frac)
     if empty:
         rect[:, 2] = rect[:, 0]
@@ -76,11 +76,15 @@ def _bin_inputs(n, ncams, tx, ty, seed, tie_frac=0.1, empty=False):
     return rect, depth, proj
 
 
-@pytest.mark.parametrize("n,ncams,tx,ty,seed", [(1, 1, 1, 1, 0), (1000, 1, 8, 6, 1),
-                                                (5000, 3, 13, 7, 2), (20000, 8, 40, 30, 3),
-                                                (70000, 2, 75, 43, 4), (3, 16, 2, 2, 5)])
-def test_bin_sort_bit_exact(lgs, oracle_lib, n, ncams, tx, ty, seed):
-    rect, depth, proj = _bin_inputs(n, ncams, tx, ty, seed)
+@pytest.mark.parametrize("n,ncams,tx,ty,seed,ext", [
+    (1, 1, 1, 1, 0, 6), (1000, 1, 8, 6, 1, 6), (5000, 3, 13, 7, 2, 6), (20000, 8, 40, 30, 3, 6),
+    (70000, 2, 75, 43, 4, 6), (3, 16, 2, 2, 5, 6),
+    # rects up to 40 x 40 tiles: one splat's pairs span several rounds of a block
+    (4000, 2, 60, 40, 7, 40),
+    # 34,000 tiles per camera: no per-block shared-memory tables, global atomics
+    (3000, 1, 200, 170, 6, 12)])
+def test_bin_sort_bit_exact(lgs, oracle_lib, n, ncams, tx, ty, seed, ext):
+    rect, depth, proj = _bin_inputs(n, ncams, tx, ty, seed, max_extent=ext)
     ref = oracle_lib.bin_sort(rect, depth, n, ncams, tx, ty, proj=proj)
     k = len(ref["ids"])
     if n > 100:  # the tile test drops part of the rects' tiles

@@ -144,7 +144,8 @@ __device__ __forceinline__ void put_row(uint8_t* tile, int r, int col, int kw, c
 __device__ unsigned g_fused_error;
 
 constexpr int kEpiWarps = 16;
-constexpr int kFusedThreads = (kEpiWarps + 3) * 32;   // + MMA warp + two producer warps
+constexpr int kProducers = 2;                          // warps streaming the weight units
+constexpr int kFusedThreads = (kEpiWarps + 1 + kProducers) * 32;  // + the MMA warp
 // barriers: full[kStages], empty[kStages], accH, accT, opH, opT, ybar[2],
 // dyfree, drain, the slice barriers sh2[2], sh3[4], sd2[2], sd3[4], then the
 // TMEM slot
@@ -233,8 +234,12 @@ decode_fused_kernel(const __grid_constant__ FusedArgs a) {
 
   if (warp >= kEpiWarps + 1) {
     // ---------------------------------------------------------------- producers
-    // A bulk copy holds its issuing thread for ~200 cycles, so two warps
-    // share the stream: producer pp copies the units with u % 2 == pp.
+    // The bulk copies one warp issues one after another do not overlap (a
+    // ring fed by one warp moves about 25 B/cycle per SM on GB300, two warps
+    // about 30, four about 55), so kProducers warps share the stream:
+    // producer pp copies the units with u % kProducers == pp.  Two, because
+    // the stream runs ahead of the MMA warp here, and four warps (21 in all)
+    // would cap the epilogue at 80 registers a thread, which costs more.
     const uint32_t pp = (uint32_t)(warp - kEpiWarps - 1);
     if (lane == 0) {
       uint32_t u = 0;
@@ -243,7 +248,7 @@ decode_fused_kernel(const __grid_constant__ FusedArgs a) {
         const bool first = t == blockIdx.x, next = t + gridDim.x < ntiles;
         const int n = stream_count(first, next);
         for (int j = 0; j < n; j++, u++) {
-          if ((u & 1) != pp) continue;
+          if (u % kProducers != pp) continue;
           const int i = stream_unit(first, next, j);
           const uint32_t s = u % kStages, round = u / kStages;
           if (round > 0 && !tc::mbar_wait(&empty[s], (round - 1) & 1, kLimit)) {
@@ -258,9 +263,9 @@ decode_fused_kernel(const __grid_constant__ FusedArgs a) {
       // before the CTA leaves, this producer's last copies have landed: the
       // stages of the last kStages units are its own (kStages is even), and
       // the MMA warp has waited for them already unless it gave up
-      static_assert(kStages % 2 == 0, "a ring stage must belong to one producer");
+      static_assert(kStages % kProducers == 0, "a ring stage must belong to one producer");
       for (uint32_t v = u > kStages ? u - kStages : 0; v < u; v++)
-        if ((v & 1) == pp) tc::mbar_wait(&full[v % kStages], (v / kStages) & 1, kLimit);
+        if (v % kProducers == pp) tc::mbar_wait(&full[v % kStages], (v / kStages) & 1, kLimit);
     }
   } else if (warp == kEpiWarps) {
     // ---------------------------------------------------------------- MMA issuer

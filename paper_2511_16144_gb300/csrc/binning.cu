@@ -370,17 +370,25 @@ block_base_kernel(const uint32_t* __restrict__ block_counts, int nblocks, uint32
   const uint32_t* col = block_counts + (size_t)t * nblocks;
   uint32_t* out = block_base + (size_t)t * nblocks;
   uint32_t run = cursor[t];
-  for (int b0 = 0; b0 < nblocks; b0 += 32) {
-    const int b = b0 + lane;
-    const uint32_t c = b < nblocks ? col[b] : 0u;
-    uint32_t x = c;
+  for (int b0 = 0; b0 < nblocks; b0 += 256) {  // eight loads in flight, then eight scans
+    uint32_t c[8];
 #pragma unroll
-    for (int q = 1; q < 32; q <<= 1) {
-      const uint32_t y = __shfl_up_sync(0xffffffffu, x, q);
-      if (lane >= q) x += y;
+    for (int k = 0; k < 8; k++) {
+      const int b = b0 + 32 * k + lane;
+      c[k] = b < nblocks ? col[b] : 0u;
     }
-    if (b < nblocks) out[b] = run + x - c;
-    run += __shfl_sync(0xffffffffu, x, 31);
+#pragma unroll
+    for (int k = 0; k < 8; k++) {
+      const int b = b0 + 32 * k + lane;
+      uint32_t x = c[k];
+#pragma unroll
+      for (int q = 1; q < 32; q <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, x, q);
+        if (lane >= q) x += y;
+      }
+      if (b < nblocks) out[b] = run + x - c[k];
+      run += __shfl_sync(0xffffffffu, x, 31);
+    }
   }
 }
 

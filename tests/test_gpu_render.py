@@ -136,6 +136,37 @@ def test_bin_sort_long_segments_bit_exact(lgs, oracle_lib, tie_frac):
         np.testing.assert_array_equal(_np(bufs.ranges).view(np.uint32), ref["ranges"])
 
 
+def test_bin_sort_huge_rects_bit_exact(lgs, oracle_lib):
+    """Rects of over 2^20 tiles (one camera of 1100 x 1000 tiles): their pairs
+    span thousands of rounds of a block and their tile coordinates come from
+    the exact integer division; next to a rect just under 2^20 tiles (the
+    reciprocal path), one of exactly 32 tiles (the largest with a hit mask),
+    one of 33, and a one-tile rect."""
+    ncams, tx, ty = 1, 1100, 1000
+    rect = np.array([[0, 0, 1100, 1000], [100, 50, 1100, 1000], [10, 10, 18, 14],
+                     [20, 20, 31, 23], [5, 5, 6, 6]], dtype=np.int32)
+    n = rect.shape[0]
+    depth = np.array([3.0, 2.0, 1.0, 1.5, 0.5], np.float32)
+    rng = np.random.default_rng(77)
+    proj = synth.synthetic_records(rng, rect, depth)
+    # wide isotropic ellipses for the two big rects: they reach most of their tiles
+    for i, (u, v, s) in enumerate([(8800.0, 8000.0, 4000.0), (9000.0, 8300.0, 2500.0)]):
+        o = 0.9
+        proj[i, 0:6] = [u, v, 1.0 / s ** 2, 0.0, 1.0 / s ** 2, o]
+        proj[i, 7] = 2.0 * np.log(255.0 * o) * 1.001 + 0.01
+    ref = oracle_lib.bin_sort(rect, depth, n, ncams, tx, ty, proj=proj)
+    k = len(ref["ids"])
+    assert k > (1 << 20)
+    bufs = lgs.BinBuffers(n, ncams, tx, ty, k, "cuda", want_keys=True)
+    lgs.gs_bin_sort(torch.from_numpy(proj).cuda(), torch.from_numpy(rect.astype(np.int16)).cuda(),
+                    bufs)
+    torch.cuda.synchronize()
+    assert int(bufs.k_dev.item()) == k
+    np.testing.assert_array_equal(_np(bufs.ids)[:k].view(np.uint32), ref["ids"])
+    np.testing.assert_array_equal(_np(bufs.keys)[:k].view(np.uint64), ref["keys"])
+    np.testing.assert_array_equal(_np(bufs.ranges).view(np.uint32), ref["ranges"])
+
+
 def test_bin_sort_empty_and_overflow(lgs, oracle_lib):
     n, ncams, tx, ty = 4000, 2, 20, 10
     rect, depth, proj = _bin_inputs(n, ncams, tx, ty, 11, empty=True)

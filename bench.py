@@ -608,7 +608,7 @@ TRAFFIC_SOURCES = {
 }
 TRAFFIC = {  # call group -> (bytes per launch, source digest)
     "gs_project": (13216256, "b0870be7d414"),
-    "gs_bin_sort": (37544704, "84aa75cc6a90"),
+    "gs_bin_sort": (37595904, "0728bb9a435e"),
     "gs_render_fwd": (5515520, "ae3ca3e45e19"),
     "l1_losses": (9849088, "792f0809c2a4"),
     "ae_decode": (349857280, "71cd7b966ad4"),

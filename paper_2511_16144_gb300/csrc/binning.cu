@@ -22,9 +22,11 @@
 //   evenly over the block's threads.
 //   4. one block per tile sorts its segment's 64-bit (depth bits, index)
 //      keys with a stable LSD radix sort in shared memory and writes the
-//      Gaussian indices: 256-thread blocks take the segments of up to 4,096
-//      keys, 1024-thread blocks the longer ones (listed by step 2) up to
-//      12,288 keys, and chunk by chunk from global memory beyond.
+//      Gaussian indices: 256-thread blocks with eight keys a thread take the
+//      segments of up to 2,048 keys (48 registers, five blocks per SM), with
+//      sixteen keys a thread those of up to 4,096, 1024-thread blocks the
+//      longer ones (listed by step 2) up to 12,288 keys, and chunk by chunk
+//      from global memory beyond.
 // Depths are positive floats, so their bit patterns order like the values.
 #include <algorithm>
 
@@ -39,6 +41,7 @@ __device__ unsigned long long g_capacity_k;
 
 namespace {
 
+constexpr int kSegSmall = 2048;        // keys a 256-thread block sorts with 8 keys a thread
 constexpr int kSegMax = 4096;          // keys a 256-thread block sorts in shared memory
 constexpr int kSegThreads = 256;
 constexpr int kLargeThreads = 1024;    // blocks for the longer segments
@@ -471,9 +474,9 @@ __device__ __forceinline__ uint32_t digit_peers(uint32_t d) {
 // each warp holds R consecutive runs of 32 keys, ranks them per digit with
 // per-bit ballots in position order, and a per-digit scan over the warps
 // places them.  Segments of up to kSegMax keys are sorted by 256-thread
-// blocks, one per tile; longer ones by 1024-thread blocks that take them from
-// a list (kLargeMax keys in shared memory), and the rare segment beyond that
-// the same way from global memory.
+// blocks, one per tile (eight or sixteen keys a thread); longer ones by
+// 1024-thread blocks that take them from a list (up to 12,288 keys in shared
+// memory), and the rare segment beyond that the same way from global memory.
 template <int T, int I>
 struct SegSmem {
   static constexpr int W = T / 32;
@@ -792,24 +795,40 @@ __device__ void smem_segment_sort(const unsigned long long* __restrict__ seg, ui
   }
 }
 
-// 4a. tiles of at most kSegMax instances, one 256-thread block each (longer
-// ones are left to tile_sort_large_kernel).
-__global__ void __launch_bounds__(kSegThreads, 3)
+// 4a. tiles of at most kSegSmall instances, one 256-thread block each with
+// eight keys a thread (most tiles; few registers, so many blocks per SM).
+__global__ void __launch_bounds__(kSegThreads, 5)
 tile_sort_kernel(const uint2* __restrict__ ranges, const unsigned long long* __restrict__ seg,
                  uint32_t* __restrict__ ids, uint64_t* __restrict__ keys_opt) {
+  using SS = SegSmem<kSegThreads, kSegSmall / kSegThreads>;
+  extern __shared__ __align__(16) unsigned char seg_smem[];
+  SS& S = *reinterpret_cast<SS*>(seg_smem);
+  const uint32_t tile = blockIdx.x;
+  const uint2 rg = ranges[tile];
+  const uint32_t cnt = rg.y - rg.x;
+  if (cnt == 0 || cnt > (uint32_t)kSegSmall) return;
+  smem_segment_sort<kSegThreads, kSegSmall / kSegThreads>(seg + rg.x, cnt, tile, ids + rg.x,
+                                                           keys_opt ? keys_opt + rg.x : nullptr, S);
+}
+
+// 4b. the tiles of kSegSmall + 1 to kSegMax instances: 256-thread blocks with
+// sixteen keys a thread, one per tile.
+__global__ void __launch_bounds__(kSegThreads, 3)
+tile_sort_mid_kernel(const uint2* __restrict__ ranges, const unsigned long long* __restrict__ seg,
+                     uint32_t* __restrict__ ids, uint64_t* __restrict__ keys_opt) {
   using SS = SegSmem<kSegThreads, kSegMax / kSegThreads>;
   extern __shared__ __align__(16) unsigned char seg_smem[];
   SS& S = *reinterpret_cast<SS*>(seg_smem);
   const uint32_t tile = blockIdx.x;
   const uint2 rg = ranges[tile];
   const uint32_t cnt = rg.y - rg.x;
-  if (cnt == 0 || cnt > (uint32_t)kSegMax) return;
+  if (cnt <= (uint32_t)kSegSmall || cnt > (uint32_t)kSegMax) return;
   smem_segment_sort<kSegThreads, kSegMax / kSegThreads>(seg + rg.x, cnt, tile, ids + rg.x,
                                                          keys_opt ? keys_opt + rg.x : nullptr, S);
 }
 
-// 4b. the tiles with more than kSegMax instances, from the list tile_scan
-// made: up to kLargeMax keys in shared memory, beyond that from global memory.
+// 4c. the tiles with more than kSegMax instances, from the list tile_scan
+// made: up to 12,288 keys in shared memory, beyond that from global memory.
 __global__ void __launch_bounds__(kLargeThreads, 1)
 tile_sort_large_kernel(const uint2* __restrict__ ranges, const uint32_t* __restrict__ long_tiles,
                        const uint32_t* __restrict__ n_long, unsigned long long* __restrict__ seg,
@@ -957,14 +976,19 @@ extern "C" lgs_status gs_bin_sort(const float* proj, const uint16_t* rect, int64
   tile_emit_kernel<<<nblk, kItemThreads, cnt_smem, s>>>((const float4*)proj, (const ushort4*)rect,
                                                         m, (uint32_t)n, tiles_x, tiles, local,
                                                         sort_n, block_base, masks, cursor, seg);
-  using SmallSmem = SegSmem<kSegThreads, kSegMax / kSegThreads>;
+  using SmallSmem = SegSmem<kSegThreads, kSegSmall / kSegThreads>;
+  using MidSmem = SegSmem<kSegThreads, kSegMax / kSegThreads>;
   using LargeSmem = SegSmem<kLargeThreads, kLargeItems>;
   LGS_CHECK_CUDA(set_smem_limit(reinterpret_cast<const void*>(tile_sort_kernel),
                                 (int)sizeof(SmallSmem)));
   LGS_CHECK_CUDA(set_smem_limit(reinterpret_cast<const void*>(tile_sort_large_kernel),
                                 (int)sizeof(LargeSmem)));
+  LGS_CHECK_CUDA(set_smem_limit(reinterpret_cast<const void*>(tile_sort_mid_kernel),
+                                (int)sizeof(MidSmem)));
   tile_sort_kernel<<<n_tiles_all, kSegThreads, sizeof(SmallSmem), s>>>((const uint2*)ranges, seg,
                                                                        ids, keys_opt);
+  tile_sort_mid_kernel<<<n_tiles_all, kSegThreads, sizeof(MidSmem), s>>>((const uint2*)ranges,
+                                                                         seg, ids, keys_opt);
   tile_sort_large_kernel<<<std::min<uint32_t>(n_tiles_all, kLargeBlocks), kLargeThreads,
                            sizeof(LargeSmem), s>>>((const uint2*)ranges, long_tiles, n_long, seg,
                                                    (unsigned long long*)(ws + L.scratch), ids,

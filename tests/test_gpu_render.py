@@ -103,16 +103,18 @@ def test_bin_sort_bit_exact(lgs, oracle_lib, n, ncams, tx, ty, seed, ext):
 
 @pytest.mark.parametrize("tie_frac", [0.0, 0.1])
 def test_bin_sort_long_segments_bit_exact(lgs, oracle_lib, tie_frac):
-    """Tiles with more instances than a 256-thread block sorts in shared
-    memory: 5,000 and exactly 12,288 (the 1024-thread blocks' shared-memory
+    """Tiles at every size tier of the per-tile sort: exactly 2,048 (the last
+    of the eight-keys-a-thread blocks), 2,049 and 3,000 (sixteen keys a
+    thread), 5,000 and exactly 12,288 (the 1024-thread blocks' shared-memory
     limit), 12,289 and 30,000 (chunk by chunk from global memory), all in
     the third camera, next to two cameras of ordinary tiles; with and without
     equal depths."""
     rng = np.random.default_rng(31)
-    ncams, tx, ty, n = 3, 9, 7, 60000
+    ncams, tx, ty, n = 3, 9, 7, 70000
     rect, depth = synth.synthetic_projected(rng, n, ncams, tx, ty, max_extent=3,
                                             tie_frac=tie_frac)
-    sizes = [(0, 5000), (3, 12288), (10, 12289), (40, 30000)]  # (tile, instances)
+    sizes = [(0, 5000), (3, 12288), (10, 12289), (40, 30000), (20, 3000), (25, 2048),
+             (30, 2049)]  # (tile, instances)
     rect[2 * n:] = 0  # camera 2: only the long tiles
     proj = synth.synthetic_records(rng, rect, depth)
     i0 = 2 * n

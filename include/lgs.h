@@ -368,6 +368,20 @@ lgs_status ae_decode(const lgs_ae_weights* w, const float* z, int64_t P, const u
                      float weight, float* loss_dev, float* dz, float* y_opt, void* workspace,
                      size_t workspace_bytes, void* stream);
 
+/* ae_decode with a target splits into two calls, so that the weight packing
+ * can run on another stream beside earlier work: ae_decode_pack writes the
+ * decoder weights (layers 4-7) in the layout the fused distillation streams
+ * into the first bytes of an ae_decode workspace (any P; workspace_bytes at
+ * least ae_workspace_bytes(0, LGS_AE_DECODE)); ae_decode_packed then computes
+ * exactly what ae_decode computes with that target and no y_opt, reading the
+ * packed weights from the same workspace.  The weights must not change
+ * between the two calls (the caller orders them, e.g. by an event). */
+lgs_status ae_decode_pack(const lgs_ae_weights* w, void* workspace, size_t workspace_bytes,
+                          void* stream);
+lgs_status ae_decode_packed(const lgs_ae_weights* w, const float* z, int64_t P,
+                            const uint16_t* target, float weight, float* loss_dev, float* dz,
+                            void* workspace, size_t workspace_bytes, void* stream);
+
 /* One Adam step (lr; beta 0.9, 0.999; eps 1e-8) on a batch x bf16 [P,512].
  * mode LGS_AE_RECON trains both networks on the reconstruction loss;
  * LGS_AE_ENC_ADAPT trains layers 0-3 on Eq. 3 against target = F_render

@@ -982,10 +982,12 @@ struct DecodeBufs {
   __nv_bfloat16* a[3];
   void* pack;
 };
+// The packed weight units first, at offset 0 whatever P (ae_decode_pack
+// writes them there), then the layer-by-layer activations.
 static void carve_decode(Carver& c, int64_t P, DecodeBufs& B) {
+  B.pack = c.bf(1, (int)(decode_pack_bytes() / 2));
   const int w[3] = {64, 128, 256};
   for (int i = 0; i < 3; i++) B.a[i] = c.bf(P, w[i]);
-  B.pack = c.bf(1, (int)(decode_pack_bytes() / 2));
 }
 
 struct TrainBufs {
@@ -1092,7 +1094,39 @@ extern "C" lgs_status ae_decode(const lgs_ae_weights* w, const float* z, int64_t
   if (!target) return LGS_OK;
   // Eq. 2: decoder forward, L1 against F_gt and the gradient back to
   // F_render in one persistent kernel (nothing but dz leaves the chip)
-  return launch_decode_fused(w, z, P, target, weight, loss_dev, dz, B.pack, s);
+  return launch_decode_fused(w, z, P, target, weight, loss_dev, dz, B.pack, false, s);
+}
+
+extern "C" lgs_status ae_decode_pack(const lgs_ae_weights* w, void* workspace,
+                                     size_t workspace_bytes, void* stream) {
+  clear_error();
+  lgs_status st = check_weights(w, 4, 7);
+  if (st != LGS_OK) return st;
+  LGS_CHECK_ARG(workspace != nullptr, "null pointer");
+  LGS_CHECK_ARG(aligned(workspace, 256), "misaligned pointer");
+  LGS_CHECK_ARG(workspace_bytes >= decode_pack_bytes(), "workspace too small");
+  return launch_decode_pack(w, workspace, as_stream(stream));
+}
+
+extern "C" lgs_status ae_decode_packed(const lgs_ae_weights* w, const float* z, int64_t P,
+                                       const uint16_t* target, float weight, float* loss_dev,
+                                       float* dz, void* workspace, size_t workspace_bytes,
+                                       void* stream) {
+  clear_error();
+  LGS_CHECK_ARG(P >= 0, "P < 0");
+  lgs_status st = check_weights(w, 4, 7);
+  if (st != LGS_OK) return st;
+  if (P == 0) return LGS_OK;
+  LGS_CHECK_ARG(z && workspace && target && loss_dev && dz, "null pointer");
+  LGS_CHECK_ARG(aligned(z, 16) && aligned(workspace, 256) && aligned(target, 16) &&
+                    aligned(dz, 16),
+                "misaligned pointer");
+  LGS_CHECK_ARG(workspace_bytes >= ae_workspace_bytes(P, LGS_AE_DECODE), "workspace too small");
+  Carver c(workspace);
+  DecodeBufs B;
+  carve_decode(c, P, B);
+  return launch_decode_fused(w, z, P, target, weight, loss_dev, dz, B.pack, true,
+                             as_stream(stream));
 }
 
 extern "C" lgs_status ae_pack(lgs_ae_state* st_, int first, int last, void* stream) {

@@ -726,9 +726,7 @@ const Plan& plan() {
 
 size_t decode_pack_bytes() { return (plan().total + 255) & ~(size_t)255; }
 
-lgs_status launch_decode_fused(const lgs_ae_weights* w, const float* z, int64_t P,
-                               const uint16_t* target, float weight, float* loss, float* dz,
-                               void* pack, cudaStream_t s) {
+lgs_status launch_decode_pack(const lgs_ae_weights* w, void* pack, cudaStream_t s) {
   const Plan& pl = plan();
   if ((int)pl.units.size() != kUnits) {
     set_error("decoder schedule size mismatch");
@@ -749,6 +747,17 @@ lgs_status launch_decode_fused(const lgs_ae_weights* w, const float* z, int64_t 
   pa.pack = static_cast<uint8_t*>(pack);
   pack_units_kernel<<<(pl.piece0[kUnits] + 255) / 256, 256, 0, s>>>(pa);
   LGS_CHECK_LAUNCH();
+  return LGS_OK;
+}
+
+lgs_status launch_decode_fused(const lgs_ae_weights* w, const float* z, int64_t P,
+                               const uint16_t* target, float weight, float* loss, float* dz,
+                               void* pack, bool packed, cudaStream_t s) {
+  const Plan& pl = plan();
+  if (!packed) {
+    const lgs_status st = launch_decode_pack(w, pack, s);
+    if (st != LGS_OK) return st;
+  }
   FusedArgs fa;
   fa.pack = static_cast<const uint8_t*>(pack);
   for (int i = 0; i < kUnits; i++) {

@@ -18,11 +18,13 @@ lgs_status launch_project_bwd(const float* means, const float* quats, const floa
                               float* d_log_scales, float* d_logits, cudaStream_t s);
 
 // Fused Eq. 2 distillation (decoder forward, L1 against F_gt, gradient to
-// z); `pack` is decode_pack_bytes() of scratch for the packed weights.
+// z); `pack` is decode_pack_bytes() of scratch for the packed weights, which
+// launch_decode_pack fills (and launch_decode_fused first, unless `packed`).
 size_t decode_pack_bytes();
+lgs_status launch_decode_pack(const lgs_ae_weights* w, void* pack, cudaStream_t s);
 lgs_status launch_decode_fused(const lgs_ae_weights* w, const float* z, int64_t P,
                                const uint16_t* target, float weight, float* loss, float* dz,
-                               void* pack, cudaStream_t s);
+                               void* pack, bool packed, cudaStream_t s);
 // Reads (and with clear, clears) the fused decoder's timeout word.
 unsigned fused_error_word(bool clear = true);
 // Fused encoder z = E(x) (x bf16 [P,512] -> z f32 [P,16]); `pack` is

@@ -88,6 +88,8 @@ def load():
         "ae_workspace_bytes": ([I64, I32], SZ),
         "ae_encode": ([P, P, I64, P, P, SZ, P], I32),
         "ae_decode": ([P, P, I64, P, F, P, P, P, P, SZ, P], I32),
+        "ae_decode_pack": ([P, P, SZ, P], I32),
+        "ae_decode_packed": ([P, P, I64, P, F, P, P, P, SZ, P], I32),
         "ae_train_step": ([P, P, P, I64, I32, F, P, P, SZ, P], I32),
         "ae_pack": ([P, I32, I32, P], I32),
         "lgs_device_error": ([P], I32),
@@ -124,7 +126,8 @@ def exported_symbols():
     """Names of the C entry points this binding declares."""
     return ["lgs_version", "lgs_last_error", "gs_project", "gs_bin_sort_workspace", "gs_bin_sort",
             "gs_render_fwd", "gs_render_bwd", "lgs_l1_loss", "ae_workspace_bytes", "ae_encode",
-            "ae_decode", "ae_train_step", "ae_pack", "lgs_device_error", "lgs_sync_status",
+            "ae_decode", "ae_decode_pack", "ae_decode_packed", "ae_train_step", "ae_pack",
+            "lgs_device_error", "lgs_sync_status",
             "lgs_set_sort_wait_limit", "lgs_graph_kernel_nodes", "lgs_zero",
             "gs_render_bwd_static_capacity", "gs_render_bwd_static", "gs_prune_workspace",
             "gs_prune", "gs_compact_workspace", "gs_compact_index", "gs_gather_rows",
@@ -336,6 +339,21 @@ def ae_decode(weights: AeWeights, z, target=None, weight=1.0, loss=None, dz=None
     _check(load().ae_decode(ctypes.byref(weights), _p(z), P, _p(target), float(weight), _p(loss),
                             _p(dz), _p(y), _p(ws), nb, _stream()), "ae_decode")
     return ws
+
+
+def ae_decode_pack(weights: AeWeights, ws):
+    """Packs the decoder weights into the workspace `ws` of a later
+    ae_decode_packed call (the first half of ae_decode with a target)."""
+    _check(load().ae_decode_pack(ctypes.byref(weights), _p(ws), ws.numel(), _stream()),
+           "ae_decode_pack")
+
+
+def ae_decode_packed(weights: AeWeights, z, target, weight, loss, dz, ws):
+    """Eq. 2 as ae_decode with a target, from weights ae_decode_pack wrote
+    into `ws`."""
+    _check(load().ae_decode_packed(ctypes.byref(weights), _p(z), z.shape[0], _p(target),
+                                   float(weight), _p(loss), _p(dz), _p(ws), ws.numel(),
+                                   _stream()), "ae_decode_packed")
 
 
 def ae_train_step(state: AeState, x, target, mode, lr, loss, ws=None):

@@ -130,3 +130,27 @@ def test_status_codes_without_a_device(lib_path):
     for name, v in (("LGS_OK", 0), ("LGS_ERR_INVALID", 1), ("LGS_ERR_CAPACITY", 2),
                     ("LGS_ERR_NONFINITE", 3), ("LGS_ERR_TIMEOUT", 4), ("LGS_ERR_CUDA", 5)):
         assert re.search(rf"{name}\s*=\s*{v}\b", text), name
+
+
+def test_decode_pack_argument_checks(lib_path):
+    """The split distillation calls check their arguments on the host."""
+    from paper_2511_16144_gb300 import lgs
+    lib = lgs.load()
+    w = lgs.AeWeights()
+    for l in range(lgs.AE_LAYERS):
+        w.W[l] = w.Wt[l] = w.b[l] = 0x1000
+    fake = ctypes.c_void_p(0x1000)
+    small = lib.ae_workspace_bytes(0, lgs.AE_DECODE)
+    assert small > 0 and lib.ae_workspace_bytes(1000, lgs.AE_DECODE) > small
+    assert lib.ae_decode_pack(ctypes.byref(w), fake, small // 2, None) == 1
+    assert b"workspace" in lib.lgs_last_error()
+    assert lib.ae_decode_pack(ctypes.byref(w), ctypes.c_void_p(0x1010), small, None) == 1
+    # a target is required, and the workspace must hold P pixels' buffers
+    assert lib.ae_decode_packed(ctypes.byref(w), fake, 1000, None, ctypes.c_float(1.0), fake, fake,
+                                fake, lib.ae_workspace_bytes(1000, lgs.AE_DECODE), None) == 1
+    assert lib.ae_decode_packed(ctypes.byref(w), fake, 1000, fake, ctypes.c_float(1.0), fake, fake,
+                                fake, small, None) == 1
+    assert b"workspace" in lib.lgs_last_error()
+    # nothing to do for P = 0
+    assert lib.ae_decode_packed(ctypes.byref(w), None, 0, None, ctypes.c_float(1.0), None, None,
+                                None, 0, None) == 0

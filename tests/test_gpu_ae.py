@@ -134,6 +134,44 @@ def test_fused_distillation_many_tiles(lgs):
     assert lgs.lgs_device_error() == 0
 
 
+def test_split_decode_matches_ae_decode(lgs):
+    """ae_decode_pack on another stream (ordered by an event), then
+    ae_decode_packed: bit for bit the dz of ae_decode with the same target,
+    the same loss; the packed weights fit a workspace sized for P = 0."""
+    from paper_2511_16144_gb300.ae import AutoEncoder
+    enc, dec = synth.ae_init(seed=3008)
+    model = AutoEncoder(enc, dec)
+    rng = np.random.default_rng(9)
+    P = 152 * 128 + 901
+    z = torch.from_numpy(rng.standard_normal((P, 16)).astype(np.float32)).cuda()
+    t = torch.from_numpy(synth.unit_rows(rng.standard_normal((P, 512))).astype(np.float32))
+    t = t.cuda().bfloat16()
+    nb = lgs.ae_workspace_bytes(P, lgs.AE_DECODE)
+    ws = torch.empty(nb, dtype=torch.uint8, device="cuda")
+    loss1, dz1 = torch.zeros(1, device="cuda"), torch.empty((P, 16), device="cuda")
+    lgs.ae_decode(model.weights, z, t, 0.5, loss1, dz1, ws=ws)
+    ws2 = torch.full((nb,), 0x5A, dtype=torch.uint8, device="cuda")
+    side, packed = torch.cuda.Stream(), torch.cuda.Event()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        lgs.ae_decode_pack(model.weights, ws2)
+        packed.record(side)
+    torch.cuda.current_stream().wait_event(packed)
+    loss2, dz2 = torch.zeros(1, device="cuda"), torch.empty((P, 16), device="cuda")
+    lgs.ae_decode_packed(model.weights, z, t, 0.5, loss2, dz2, ws2)
+    torch.cuda.synchronize()
+    assert torch.equal(dz1, dz2)
+    assert abs(loss2.item() - loss1.item()) <= 1e-5 * loss1.item()
+    # (the size query adds 256 bytes of slack past the packed weights)
+    small = torch.full((lgs.ae_workspace_bytes(0, lgs.AE_DECODE),), 0x5A, dtype=torch.uint8,
+                       device="cuda")
+    lgs.ae_decode_pack(model.weights, small)
+    torch.cuda.synchronize()
+    n = small.numel() - 256
+    assert torch.equal(small[:n], ws2[:n])
+    assert lgs.lgs_sync_status() == (lgs.OK, 0)
+
+
 @pytest.mark.parametrize("mode", ["recon", "enc_adapt"])
 def test_train_step_gradients_and_update(lgs, mode):
     from oracle import ae

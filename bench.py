@@ -607,12 +607,12 @@ TRAFFIC_SOURCES = {
     "gs_render_bwd": ("render.cu", "project.cu", "common.cuh", "kernels.cuh"),
 }
 TRAFFIC = {  # call group -> (bytes per launch, source digest)
-    "gs_project": (13216256, "b0870be7d414"),
-    "gs_bin_sort": (37595904, "0728bb9a435e"),
-    "gs_render_fwd": (5515520, "ae3ca3e45e19"),
-    "l1_losses": (9849088, "792f0809c2a4"),
-    "ae_decode": (349857280, "71cd7b966ad4"),
-    "gs_render_bwd": (41208064, "83aa7b383d4a"),
+    "gs_project": (13217024, "11cb2be17fcb"),
+    "gs_bin_sort": (37627648, "18d76b8a2256"),
+    "gs_render_fwd": (5515264, "011d53f72718"),
+    "l1_losses": (9845504, "792f0809c2a4"),
+    "ae_decode": (350212096, "786b927cd231"),
+    "gs_render_bwd": (41203456, "5fcc646473a8"),
 }
 
 

@@ -6,9 +6,11 @@
 // layers.  Per tile the CTA runs, on the tensor cores (BF16 operands, FP32
 // accumulators in tensor memory):
 //   F1..F3  forward hidden layers, activations kept in shared memory (BF16);
-//   F4/B1   the 512-wide output in four 128-column chunks: each chunk's
+//   F4/B1   the 512-wide output in eight 64-column chunks: each chunk's
 //           epilogue forms dy = w sign(y - F_gt) / (P 512) and immediately
 //           feeds dh3 += dy_chunk W7_chunk, so y and dy never reach memory;
+//           B1 reads the chunk's W7 units that F4 used, still in the ring, as
+//           an MN-major operand (W7 is streamed once per tile, W7^T never);
 //   R3..R1  the pre-activations are recomputed instead of stored (this keeps
 //           the working set in shared memory);
 //   B2..B4  dh2 = (dh3 * gelu'(pre3)) W6, dh1 = (dh2 * gelu'(pre2)) W5,
@@ -22,8 +24,8 @@
 // Warps 0-15 are the epilogue (TMEM -> registers -> shared memory; warps w,
 // w + 4, w + 8, w + 12 share TMEM lane quadrant w % 4 and split the columns in
 // quarters), warp 16 issues the MMAs, warps 17 and 18 stream the weights as
-// 51 pre-packed units (<= 16 KB each, already in the tensor-core's canonical
-// layout) through a 4-stage ring with bulk TMA copies.  Every wait is bounded.
+// 35 pre-packed units (<= 16 KB each, already in the tensor-core's canonical
+// layout) through a 5-stage ring with bulk TMA copies.  Every wait is bounded.
 #include <mutex>
 #include <type_traits>
 #include <vector>
@@ -36,8 +38,8 @@ namespace lgs {
 
 namespace {
 
-constexpr int kUnits = 51;
-constexpr int kStages = 4;
+constexpr int kUnits = 35;
+constexpr int kStages = 5;
 constexpr uint32_t kStageBytes = 16384;
 constexpr uint32_t kLimit = 1u << 22;
 
@@ -46,9 +48,9 @@ constexpr uint32_t SM_Z = 0;         // 2 x (128 x 16 bf16): z of this tile and 
 constexpr uint32_t SM_H1 = 8192;     // 128 x 64   (h1)
 constexpr uint32_t SM_H2 = 24576;    // 128 x 128  (h2, later d2)
 constexpr uint32_t SM_H3 = 57344;    // 128 x 256  (h3, later d3)
-constexpr uint32_t SM_DY = 122880;   // 128 x 128  (one dy chunk, later d1)
-constexpr uint32_t SM_FGX = 155648;  // F_gt transpose buffers of epilogue warps 8-15
-constexpr uint32_t SM_ST = 159744;   // kStages x 16 KB weight ring
+constexpr uint32_t SM_DY = 122880;   // 128 x 64   (one dy chunk, later d1)
+constexpr uint32_t SM_FGX = 139264;  // F_gt transpose buffers of epilogue warps 8-15
+constexpr uint32_t SM_ST = 143360;   // kStages x 16 KB weight ring
 constexpr uint32_t SM_BAR = SM_ST + kStages * kStageBytes;
 
 // weight matrices of the decoder: forward W (out x in) and transposed Wt
@@ -59,24 +61,18 @@ struct Unit {
   int mat, row0, rows, col0, kc;
 };
 
-// The 51 weight units of one tile, in the order the MMAs consume them.
+// The 35 weight units of one tile, in the order the MMAs consume them.
 std::vector<Unit> schedule() {
   std::vector<Unit> U;
   auto add = [&](int m, int r0, int rows, int c0, int kc) { U.push_back({m, r0, rows, c0, kc}); };
   add(W4, 0, 64, 0, 16);                                                   // F1
   add(W5, 0, 128, 0, 64);                                                  // F2
   for (int k = 0; k < 4; k++) add(W6, 0, 256, 32 * k, 32);                // F3 (N = 256)
-  for (int k = 0; k < 4; k++) add(W7, 0, 128, 64 * k, 64);                // F4 chunk 0
-  for (int k = 0; k < 4; k++) add(W7, 128, 128, 64 * k, 64);             // F4 chunk 1
-  auto b1 = [&](int c) {  // N = 256
-    for (int k = 0; k < 4; k++) add(T7, 0, 256, 128 * c + 32 * k, 32);
-  };
-  b1(0);
-  for (int k = 0; k < 4; k++) add(W7, 256, 128, 64 * k, 64);             // F4 chunk 2
-  b1(1);
-  for (int k = 0; k < 4; k++) add(W7, 384, 128, 64 * k, 64);             // F4 chunk 3
-  b1(2);
-  b1(3);
+  // F4: eight 64-column output chunks of two K-halves each (64 x 128); the
+  // backward product B1 of a chunk reads the same two units again, as an
+  // MN-major operand, so W7 is streamed once and W7^T not at all
+  for (int c = 0; c < 8; c++)
+    for (int u = 0; u < 2; u++) add(W7, 64 * c, 64, 128 * u, 128);
   for (int k = 0; k < 4; k++) add(W6, 0, 256, 32 * k, 32);                // R3 (N = 256)
   for (int k = 0; k < 4; k++) add(T6, 0, 128, 64 * k, 64);               // B2
   add(W5, 0, 128, 0, 64);                                                  // R2
@@ -150,35 +146,35 @@ constexpr int kFusedThreads = (kEpiWarps + 1 + kProducers) * 32;  // + the MMA w
 // dyfree, drain, the slice barriers sh2[2], sh3[4], sd2[2], sd3[4], then the
 // TMEM slot
 constexpr uint32_t kBarBytes = (2 * kStages + 20) * 8 + 4;
-constexpr uint32_t SM_BIAS = SM_BAR + 240;             // b4 | b5 | b6 | b7 (960 floats)
+constexpr uint32_t SM_BIAS = SM_BAR + 256;             // b4 | b5 | b6 | b7 (960 floats)
 constexpr uint32_t SM_ALL = SM_BIAS + 960 * 4;
 static_assert(kBarBytes <= SM_BIAS - SM_BAR, "barrier block overlaps the biases");
 static_assert(SM_ALL <= 232448, "shared-memory map exceeds 227 KB");
 static_assert(SM_FGX + 8 * 512 <= SM_ST && SM_Z + 2 * 4096 <= SM_H1, "transpose buffers overlap");
 
 // Weight units per tile in stream order.  Units 0-5 are the forward hidden
-// layers (F1, F2, F3), 6-37 the output layer and its backward (F4/B1), 38-41
-// R3, 42-46 B2 and R2, 47-49 B3 and R1, 50 B4.  The first tile of a CTA
-// starts with 0-5; every tile then streams 6-46, 47-49, 50, with the next
-// tile's F1 (0), F2 (1) and F3 (2-5) slotted in after 46, 49 and 50.
+// layers (F1, F2, F3), 6-21 the output layer (F4, its units read again by
+// B1), 22-25 R3, 26-30 B2 and R2, 31-33 B3 and R1, 34 B4.  The first tile of a
+// CTA starts with 0-5; every tile then streams 6-30, 31-33, 34, with the next
+// tile's F1 (0), F2 (1) and F3 (2-5) slotted in after 30, 33 and 34.
 __device__ __forceinline__ int stream_count(bool first, bool next) {
-  return (first ? 6 : 0) + 45 + (next ? 6 : 0);
+  return (first ? 6 : 0) + 29 + (next ? 6 : 0);
 }
 __device__ __forceinline__ int stream_unit(bool first, bool next, int j) {
   if (first) {
     if (j < 6) return j;
     j -= 6;
   }
-  if (j < 41) return 6 + j;                 // 6..46
-  j -= 41;
+  if (j < 25) return 6 + j;                 // 6..30
+  j -= 25;
   if (next) {
     if (j == 0) return 0;                   // F1 of the next tile
-    if (j <= 3) return 46 + j;              // 47..49
+    if (j <= 3) return 30 + j;              // 31..33
     if (j == 4) return 1;                   // F2 of the next tile
-    if (j == 5) return 50;
+    if (j == 5) return 34;
     return j - 4;                           // 2..5: F3 of the next tile
   }
-  return j < 3 ? 47 + j : 50;
+  return j < 3 ? 31 + j : 34;
 }
 
 __global__ void __launch_bounds__(kFusedThreads, 1)
@@ -260,10 +256,9 @@ decode_fused_kernel(const __grid_constant__ FusedArgs a) {
         }
       }
       if (!ok) atomicOr(&g_fused_error, 1u);
-      // before the CTA leaves, this producer's last copies have landed: the
-      // stages of the last kStages units are its own (kStages is even), and
-      // the MMA warp has waited for them already unless it gave up
-      static_assert(kStages % kProducers == 0, "a ring stage must belong to one producer");
+      // before the CTA leaves, this producer's copies among the last kStages
+      // units have landed (no stage was refilled after them; the MMA warp has
+      // waited for them already unless it gave up)
       for (uint32_t v = u > kStages ? u - kStages : 0; v < u; v++)
         if (v % kProducers == pp) tc::mbar_wait(&full[v % kStages], (v / kStages) & 1, kLimit);
     }
@@ -290,12 +285,15 @@ decode_fused_kernel(const __grid_constant__ FusedArgs a) {
       tc::fence_after();
     };
     // one weight unit: B = ring stage, A = activation tile at a_off (width
-    // a_kw) from column k0, D = TMEM column dcol, N = n, K = kc
-    auto unit = [&](uint32_t a_off, int a_kw, int k0, int kc, int n, uint32_t dcol, bool fresh) {
-      if (!ok) return;
+    // a_kw) from column k0, D = TMEM column dcol, N = n, K = kc; the stage is
+    // released after its MMAs unless `hold` (an output unit, read again by
+    // its chunk's B1); returns the stage
+    auto unit = [&](uint32_t a_off, int a_kw, int k0, int kc, int n, uint32_t dcol, bool fresh,
+                    bool hold = false) -> uint32_t {
       const uint32_t s = u % kStages, round = u / kStages;
+      if (!ok) return s;
       ok = __all_sync(0xffffffffu, tc::mbar_wait(&full[s], round & 1, kLimit));
-      if (!ok) return;
+      if (!ok) return s;
       tc::fence_after();
       const uint64_t ad = dbase + tc::sdesc_off(a_off + (uint32_t)k0 * 16, (uint32_t)a_kw * 16);
       const uint64_t bd = dbase + tc::sdesc_off(SM_ST + s * kStageBytes, (uint32_t)kc * 16);
@@ -303,10 +301,11 @@ decode_fused_kernel(const __grid_constant__ FusedArgs a) {
       if (tc::elect_one()) {
         for (int j = 0; j < kc / 16; j++)
           tc::mma_bf16(tmem + dcol, ad + 16 * j, bd + 16 * j, idesc, (fresh && j == 0) ? 0u : 1u);
-        tc::commit(&empty[s]);
+        if (!hold) tc::commit(&empty[s]);
       }
       __syncwarp();
       u++;
+      return s;
     };
     // forward hidden layers into TMEM columns 256-511 (z in buffer zb)
     auto f1 = [&](uint32_t zb) { unit(zb, 16, 0, 16, 64, 256, true); commit(accH); };
@@ -331,26 +330,48 @@ decode_fused_kernel(const __grid_constant__ FusedArgs a) {
       const uint32_t zc = SM_Z + (uint32_t)(k & 1) * 4096, zn = SM_Z + (uint32_t)((k + 1) & 1) * 4096;
       const uint32_t par = (uint32_t)(k & 1);
       if (k > 0) wait_on(opT, nopT);                                 // dz of the last tile read
-      // output chunk c -> TMEM buffer c & 1, announced on ybar[c & 1]; each
-      // dy chunk's product is announced on dyfree (its buffer is free again).
-      // The first chunk's K-slices start as the slices of h3 land; it writes
-      // TMEM columns 256-383, which hold F3's columns 0-127 until E3 has read
-      // its slices 0 and 1, so its first MMA waits for slice 1
+      // output chunk c (64 columns) -> TMEM buffer c & 1 (columns 256 + 64 (c &
+      // 1)), announced on ybar[c & 1]; its two units stay in their stages
+      // (held[c & 1]) until B1 c has read them.  Chunk 0's K-halves start as
+      // the slices of h3 land; its buffer holds F3's columns 0-63 until E3
+      // has read slice 0, which slice 1's arrival implies
+      uint32_t held[2][2];
       auto f4 = [&](int c) {
-        for (int kk = 0; kk < 4; kk++) {
-          if (c == 0 && kk != 1) wait_slice(&sh3[kk == 0 ? 1 : kk], par);  // h3 slices staged
-          unit(SM_H3, 256, 64 * kk, 64, 128, 256 + 128 * (c & 1), kk == 0);
+        for (int h = 0; h < 2; h++) {
+          if (c == 0) wait_slice(&sh3[2 * h + 1], par);             // h3 slices staged
+          held[c & 1][h] = unit(SM_H3, 256, 128 * h, 128, 64, 256 + 64 * (c & 1), h == 0, true);
         }
         commit(&ybar[c & 1]);
       };
+      // B1 c: dh3[:, 128 h ..] += dy_c W7[64 c .., 128 h ..]^T, B = the held
+      // unit h as an MN-major operand (K = the chunk's 64 outputs, core
+      // matrices 2 KB apart; N = 128 of h3's columns, 128 B apart); then both
+      // stages are released and dyfree announces the dy buffer free
+      const uint32_t idesc_b1 = tc::idesc_bf16(128, 128) | (1u << 16);
+      auto b1 = [&](int c) {
+        if (!ok) return;
+        if (tc::elect_one()) {
+          for (int h = 0; h < 2; h++) {
+            const uint32_t st = sbase + SM_ST + held[c & 1][h] * kStageBytes;
+            for (int j = 0; j < 4; j++)
+              tc::mma_bf16(tmem + 128 * h,
+                           dbase + tc::sdesc_off(SM_DY + (uint32_t)j * 256, 64 * 16),
+                           tc::sdesc(st + (uint32_t)j * 4096, 2048, 128), idesc_b1,
+                           (c == 0 && j == 0) ? 0u : 1u);
+          }
+          tc::commit(&empty[held[c & 1][0]]);
+          tc::commit(&empty[held[c & 1][1]]);
+          tc::commit(dyfree);
+        }
+        __syncwarp();
+      };
       f4(0);
       f4(1);
-      for (int c = 0; c < 4; c++) {
+#pragma unroll
+      for (int c = 0; c < 8; c++) {
         wait_on(opT, nopT);                                          // dy chunk c written
-        for (int kk = 0; kk < 4; kk++)
-          unit(SM_DY, 128, 32 * kk, 32, 256, 0, c == 0 && kk == 0);                       // B1 c
-        commit(dyfree);
-        if (c < 2) f4(c + 2);
+        b1(c);
+        if (c < 6) f4(c + 2);
       }
       for (int kk = 0; kk < 4; kk++) unit(SM_H2, 128, 32 * kk, 32, 256, 256, kk == 0);  // R3
       commit(accT);
@@ -491,15 +512,15 @@ decode_fused_kernel(const __grid_constant__ FusedArgs a) {
       gelu_slices(std::integral_constant<int, 4>(), 16 * qq, sb6, sm + SM_H3, 256, sh3);
     };
     // F_gt of output chunk c of tile t, loaded coalesced: slot i holds row
-    // 8 i + lane / 4 of this warp's 32 rows, 16-byte piece lane % 4 of its
-    // 32 columns (each load covers 8 rows x 64 contiguous bytes)
-    uint4 ld[4];
+    // 16 i + lane / 2 of this warp's 32 rows, 16-byte piece lane % 2 of its
+    // 16 columns (each load covers 16 rows x 32 contiguous bytes)
+    uint4 ld[2];
     auto load_fgt = [&](int64_t t, int c) {
-      const int n0 = 128 * c + 32 * qq;
+      const int n0 = 64 * c + 16 * qq;
 #pragma unroll
-      for (int i = 0; i < 4; i++) {
-        const int64_t pr = t * 128 + 32 * q + 8 * i + (lane >> 2);
-        ld[i] = pr < a.P ? *reinterpret_cast<const uint4*>(a.target + pr * 512 + n0 + 8 * (lane & 3))
+      for (int i = 0; i < 2; i++) {
+        const int64_t pr = t * 128 + 32 * q + 16 * i + (lane >> 1);
+        ld[i] = pr < a.P ? *reinterpret_cast<const uint4*>(a.target + pr * 512 + n0 + 8 * (lane & 1))
                          : make_uint4(0u, 0u, 0u, 0u);
       }
     };
@@ -523,74 +544,66 @@ decode_fused_kernel(const __grid_constant__ FusedArgs a) {
                                    : SM_FGX + (warp - 8) * 512);
       // E4: output chunks, L1 against F_gt, dy into the chunk buffer
 #pragma unroll 1
-      for (int c = 0; c < 4; c++) {
-        // round j: the 8 lanes holding piece j store it for all 32 rows, then
+      for (int c = 0; c < 8; c++) {
+        // round j: the 16 lanes holding piece j store it for all 32 rows, then
         // every lane reads piece j of its own row
-        uint4 tg[4];
+        uint4 tg[2];
 #pragma unroll
-        for (int j = 0; j < 4; j++) {
+        for (int j = 0; j < 2; j++) {
           __syncwarp();
-          if ((lane & 3) == j) {
+          if ((lane & 1) == j) {
 #pragma unroll
-            for (int i = 0; i < 4; i++)
-              *reinterpret_cast<uint4*>(fg + (8 * i + (lane >> 2)) * 16) = ld[i];
+            for (int i = 0; i < 2; i++)
+              *reinterpret_cast<uint4*>(fg + (16 * i + (lane >> 1)) * 16) = ld[i];
           }
           __syncwarp();
           tg[j] = *reinterpret_cast<const uint4*>(fg + lane * 16);
         }
-        if (c < 3) load_fgt(t, c + 1);
-        const int n0 = 128 * c + 32 * qq;
+        if (c < 7) load_fgt(t, c + 1);
+        const int n0 = 64 * c + 16 * qq;
         ok = ok && tc::mbar_wait(&ybar[c & 1], (c >> 1) & 1, kLimit);
         tc::fence_after();
-        // two halves of 16 columns (the second's TMEM load in flight while the
-        // first is computed); dy = +-scale or 0, packed to BF16 at once
-        uint4 dy[4];
-        uint32_t ya[16], yb[16];
+        // 16 columns; dy = +-scale or 0, packed to BF16 at once
+        uint4 dy[2];
+        uint32_t ya[16];
         float lc = 0.f;  // this chunk's sum of |d|
-        const uint32_t ty = tb + 256 + 128 * (c & 1) + 32 * qq;
-        tc::tmem_ld16_issue(ty, ya);
+        tc::tmem_ld16_issue(tb + 256 + 64 * (c & 1) + 16 * qq, ya);
         tc::tmem_wait16(ya);
-        tc::tmem_ld16_issue(ty + 16, yb);
 #pragma unroll
-        for (int h = 0; h < 2; h++) {
-          if (h == 1) tc::tmem_wait16(yb);
-          const uint32_t* yv = h ? yb : ya;
+        for (int kk = 0; kk < 2; kk++) {
+          const __nv_bfloat162* h2 = reinterpret_cast<const __nv_bfloat162*>(&tg[kk]);
+          __nv_bfloat162* o2 = reinterpret_cast<__nv_bfloat162*>(&dy[kk]);
 #pragma unroll
-          for (int kk = 0; kk < 2; kk++) {
-            const __nv_bfloat162* h2 = reinterpret_cast<const __nv_bfloat162*>(&tg[2 * h + kk]);
-            __nv_bfloat162* o2 = reinterpret_cast<__nv_bfloat162*>(&dy[2 * h + kk]);
-#pragma unroll
-            for (int e = 0; e < 4; e++) {
-              const float2 tt = __bfloat1622float2(h2[e]);
-              const int i = 8 * kk + 2 * e;
-              const float2 dd = __fadd2_rn(
-                  __fadd2_rn(f2(__uint_as_float(yv[i]), __uint_as_float(yv[i + 1])),
-                             *reinterpret_cast<const float2*>(sb7 + n0 + 16 * h + i)),
-                  f2(-tt.x, -tt.y));
-              lc += fabsf(dd.x) + fabsf(dd.y);
-              // BF16 pair of sign(d) * scale: d's sign bits applied to the
-              // BF16 pattern of scale, a zero half where d is exactly 0
-              uint32_t w = (__byte_perm(__float_as_uint(dd.x), __float_as_uint(dd.y), 0x7632) &
-                            0x80008000u) ^ s2bf;
-              if (dd.x == 0.f) w &= 0xffff0000u;
-              if (dd.y == 0.f) w &= 0x0000ffffu;
-              reinterpret_cast<uint32_t*>(o2)[e] = w;
-            }
+          for (int e = 0; e < 4; e++) {
+            const float2 tt = __bfloat1622float2(h2[e]);
+            const int i = 8 * kk + 2 * e;
+            const float2 dd = __fadd2_rn(
+                __fadd2_rn(f2(__uint_as_float(ya[i]), __uint_as_float(ya[i + 1])),
+                           *reinterpret_cast<const float2*>(sb7 + n0 + i)),
+                f2(-tt.x, -tt.y));
+            lc += fabsf(dd.x) + fabsf(dd.y);
+            // BF16 pair of sign(d) * scale: d's sign bits applied to the
+            // BF16 pattern of scale, a zero half where d is exactly 0
+            uint32_t w = (__byte_perm(__float_as_uint(dd.x), __float_as_uint(dd.y), 0x7632) &
+                          0x80008000u) ^ s2bf;
+            if (dd.x == 0.f) w &= 0xffff0000u;
+            if (dd.y == 0.f) w &= 0x0000ffffu;
+            reinterpret_cast<uint32_t*>(o2)[e] = w;
           }
         }
         if (valid) {
           lsum += lc;
         } else {  // rows past the end carry no loss and no gradient
-#pragma unroll
-          for (int kk = 0; kk < 4; kk++) dy[kk] = make_uint4(0u, 0u, 0u, 0u);
+          dy[0] = make_uint4(0u, 0u, 0u, 0u);
+          dy[1] = make_uint4(0u, 0u, 0u, 0u);
         }
         if (c > 0) {  // the previous chunk's product has read the dy buffer
           ok = ok && tc::mbar_wait(dyfree, (c - 1) & 1, kLimit);
           tc::fence_after();
         }
 #pragma unroll
-        for (int kk = 0; kk < 4; kk++)
-          *reinterpret_cast<uint4*>(sm + SM_DY + tc::core_offset(r, 4 * qq + kk, 128)) = dy[kk];
+        for (int kk = 0; kk < 2; kk++)
+          *reinterpret_cast<uint4*>(sm + SM_DY + tc::core_offset(r, 2 * qq + kk, 64)) = dy[kk];
         arrive(opT);
       }
       ok = ok && tc::mbar_wait(dyfree, 1, kLimit);  // the last chunk's phase

@@ -361,7 +361,8 @@ lgs_status ae_encode(const lgs_ae_weights* w, const uint16_t* x, int64_t P, floa
                      void* workspace, size_t workspace_bytes, void* stream);
 
 /* Decoder D_theta on z [P,16] fp32 (the rendered F_render).  With target
- * (F_gt, bf16 [P,512]): loss_dev += weight * mean|D(z) - F_gt| (Eq. 2) and
+ * (F_gt, bf16 [P,512], 32-byte aligned; the other pointers 16-byte aligned,
+ * the workspace 256-byte): loss_dev += weight * mean|D(z) - F_gt| (Eq. 2) and
  * dz [P,16] fp32 = its gradient w.r.t. z (overwritten; the decoder is
  * frozen).  With y_opt: y_opt [P,512] fp32 = D(z).  Either or both. */
 lgs_status ae_decode(const lgs_ae_weights* w, const float* z, int64_t P, const uint16_t* target,

@@ -1072,7 +1072,7 @@ extern "C" lgs_status ae_decode(const lgs_ae_weights* w, const float* z, int64_t
   LGS_CHECK_ARG(z && workspace, "null pointer");
   LGS_CHECK_ARG(target || y_opt, "nothing to compute: give a target or y_opt");
   LGS_CHECK_ARG(!target || (loss_dev && dz), "a target needs loss_dev and dz");
-  LGS_CHECK_ARG(aligned(z, 16) && aligned(workspace, 256) && aligned(target, 16) &&
+  LGS_CHECK_ARG(aligned(z, 16) && aligned(workspace, 256) && aligned(target, 32) &&
                     aligned(dz, 16) && aligned(y_opt, 16),
                 "misaligned pointer");
   LGS_CHECK_ARG(workspace_bytes >= ae_workspace_bytes(P, LGS_AE_DECODE), "workspace too small");
@@ -1118,7 +1118,7 @@ extern "C" lgs_status ae_decode_packed(const lgs_ae_weights* w, const float* z, 
   if (st != LGS_OK) return st;
   if (P == 0) return LGS_OK;
   LGS_CHECK_ARG(z && workspace && target && loss_dev && dz, "null pointer");
-  LGS_CHECK_ARG(aligned(z, 16) && aligned(workspace, 256) && aligned(target, 16) &&
+  LGS_CHECK_ARG(aligned(z, 16) && aligned(workspace, 256) && aligned(target, 32) &&
                     aligned(dz, 16),
                 "misaligned pointer");
   LGS_CHECK_ARG(workspace_bytes >= ae_workspace_bytes(P, LGS_AE_DECODE), "workspace too small");

@@ -19,8 +19,8 @@
 // (R3, B2..B4, accumulators in TMEM columns 0-255) interleave with the
 // forward hidden layers of tile t+1 (F1..F3, columns 256-511), so the tensor
 // core works on one tile while the epilogue warps work on the other.  z is
-// double-buffered for this; the shared buffer of the z not in use doubles as
-// the F_gt transpose buffer of the output epilogue.
+// double-buffered for this.  The output epilogue reads F_gt with one 32-byte
+// load per lane (its row's 16 columns of the chunk, one sector) a chunk ahead.
 // Warps 0-15 are the epilogue (TMEM -> registers -> shared memory; warps w,
 // w + 4, w + 8, w + 12 share TMEM lane quadrant w % 4 and split the columns in
 // quarters), warp 16 issues the MMAs, warps 17 and 18 stream the weights as
@@ -49,8 +49,7 @@ constexpr uint32_t SM_H1 = 8192;     // 128 x 64   (h1)
 constexpr uint32_t SM_H2 = 24576;    // 128 x 128  (h2, later d2)
 constexpr uint32_t SM_H3 = 57344;    // 128 x 256  (h3, later d3)
 constexpr uint32_t SM_DY = 122880;   // 128 x 64   (one dy chunk, later d1)
-constexpr uint32_t SM_FGX = 139264;  // F_gt transpose buffers of epilogue warps 8-15
-constexpr uint32_t SM_ST = 143360;   // kStages x 16 KB weight ring
+constexpr uint32_t SM_ST = 139264;   // kStages x 16 KB weight ring
 constexpr uint32_t SM_BAR = SM_ST + kStages * kStageBytes;
 
 // weight matrices of the decoder: forward W (out x in) and transposed Wt
@@ -150,7 +149,7 @@ constexpr uint32_t SM_BIAS = SM_BAR + 256;             // b4 | b5 | b6 | b7 (960
 constexpr uint32_t SM_ALL = SM_BIAS + 960 * 4;
 static_assert(kBarBytes <= SM_BIAS - SM_BAR, "barrier block overlaps the biases");
 static_assert(SM_ALL <= 232448, "shared-memory map exceeds 227 KB");
-static_assert(SM_FGX + 8 * 512 <= SM_ST && SM_Z + 2 * 4096 <= SM_H1, "transpose buffers overlap");
+static_assert(SM_DY + 128 * 64 * 2 <= SM_ST, "dy buffer overlaps the ring");
 
 // Weight units per tile in stream order.  Units 0-5 are the forward hidden
 // layers (F1, F2, F3), 6-21 the output layer (F4, its units read again by
@@ -511,17 +510,22 @@ decode_fused_kernel(const __grid_constant__ FusedArgs a) {
       wait_acc(accH, nH);
       gelu_slices(std::integral_constant<int, 4>(), 16 * qq, sb6, sm + SM_H3, 256, sh3);
     };
-    // F_gt of output chunk c of tile t, loaded coalesced: slot i holds row
-    // 16 i + lane / 2 of this warp's 32 rows, 16-byte piece lane % 2 of its
-    // 16 columns (each load covers 16 rows x 32 contiguous bytes)
+    // F_gt of output chunk c of tile t: this lane's row, this warp's 16
+    // columns, one 32-byte load (a whole sector; F_gt is 32-byte aligned, so
+    // the warp's load touches 32 sectors and uses every byte of them).  (The
+    // same bytes as two 16-byte loads per lane cost twice the sector requests
+    // and were slower; 16 rows x 32 bytes per instruction then a transpose
+    // through shared memory, 0.302 ms against 0.297.)
     uint4 ld[2];
     auto load_fgt = [&](int64_t t, int c) {
-      const int n0 = 64 * c + 16 * qq;
-#pragma unroll
-      for (int i = 0; i < 2; i++) {
-        const int64_t pr = t * 128 + 32 * q + 16 * i + (lane >> 1);
-        ld[i] = pr < a.P ? *reinterpret_cast<const uint4*>(a.target + pr * 512 + n0 + 8 * (lane & 1))
-                         : make_uint4(0u, 0u, 0u, 0u);
+      const int64_t pr = t * 128 + r;
+      ld[0] = ld[1] = make_uint4(0u, 0u, 0u, 0u);
+      if (pr < a.P) {
+        const __nv_bfloat16* ptr = a.target + pr * 512 + 64 * c + 16 * qq;
+        asm volatile("ld.global.nc.v8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                     : "=r"(ld[0].x), "=r"(ld[0].y), "=r"(ld[0].z), "=r"(ld[0].w), "=r"(ld[1].x),
+                       "=r"(ld[1].y), "=r"(ld[1].z), "=r"(ld[1].w)
+                     : "l"(ptr));
       }
     };
     if (blockIdx.x < ntiles) {
@@ -537,28 +541,10 @@ decode_fused_kernel(const __grid_constant__ FusedArgs a) {
       const bool next = t + gridDim.x < ntiles;
       const int64_t p = t * 128 + r;
       const bool valid = p < a.P;
-      // this warp's transpose buffer: the z buffer of the next tile (not
-      // written before E5 of this tile) for warps 0-7, a buffer of its own
-      // for warps 8-15
-      uint8_t* fg = sm + (warp < 8 ? SM_Z + (uint32_t)((k + 1) & 1) * 4096 + warp * 512
-                                   : SM_FGX + (warp - 8) * 512);
       // E4: output chunks, L1 against F_gt, dy into the chunk buffer
 #pragma unroll 1
       for (int c = 0; c < 8; c++) {
-        // round j: the 16 lanes holding piece j store it for all 32 rows, then
-        // every lane reads piece j of its own row
-        uint4 tg[2];
-#pragma unroll
-        for (int j = 0; j < 2; j++) {
-          __syncwarp();
-          if ((lane & 1) == j) {
-#pragma unroll
-            for (int i = 0; i < 2; i++)
-              *reinterpret_cast<uint4*>(fg + (16 * i + (lane >> 1)) * 16) = ld[i];
-          }
-          __syncwarp();
-          tg[j] = *reinterpret_cast<const uint4*>(fg + lane * 16);
-        }
+        const uint4 tg[2] = {ld[0], ld[1]};  // F_gt of this row's 16 columns
         if (c < 7) load_fgt(t, c + 1);
         const int n0 = 64 * c + 16 * qq;
         ok = ok && tc::mbar_wait(&ybar[c & 1], (c >> 1) & 1, kLimit);

@@ -154,3 +154,11 @@ def test_decode_pack_argument_checks(lib_path):
     # nothing to do for P = 0
     assert lib.ae_decode_packed(ctypes.byref(w), None, 0, None, ctypes.c_float(1.0), None, None,
                                 None, 0, None) == 0
+    # F_gt is read 32 bytes a lane: a target on a 16-byte (not 32-byte) boundary is refused
+    big = lib.ae_workspace_bytes(1000, lgs.AE_DECODE)
+    odd = ctypes.c_void_p(0x1010)
+    assert lib.ae_decode(ctypes.byref(w), fake, 1000, odd, ctypes.c_float(1.0), fake, fake, None,
+                         fake, big, None) == 1
+    assert b"misaligned" in lib.lgs_last_error()
+    assert lib.ae_decode_packed(ctypes.byref(w), fake, 1000, odd, ctypes.c_float(1.0), fake, fake,
+                                fake, big, None) == 1

@@ -52,6 +52,9 @@ def parse():
     ap.add_argument("--profile-ae", action="store_true",
                     help="run warmup + steps eager ae_train_step calls (RECON, 65,536 "
                          "unit-norm 512-d pixels) and exit (for ncu)")
+    ap.add_argument("--profile-prune", action="store_true",
+                    help="run warmup + steps eager gs_prune calls on the indoor map with its "
+                         "encoder-prior features and exit (for ncu)")
     return ap.parse_args()
 
 
@@ -236,6 +239,14 @@ def run_gpu(args, rank, world):
     def timed(step, k, warm, clocks=None):
         return timed_graph_steps(step.run, k, warm, flush, world, clocks)
 
+    if args.profile_prune:
+        params = lgs.prune_params(synth.ROOM_LO, synth.ROOM_HI, **PRUNE_PARAMS)
+        for _ in range(args.warmup + args.steps):
+            mask, cnt = lgs.gs_prune(s16_bf.means, s16_bf.opacity_logits, s16_bf.log_scales,
+                                     s16_bf.feats, params)
+        torch.cuda.synchronize()
+        print(f"profile-prune: {args.warmup + args.steps} eager calls, {int(cnt.item())} pruned")
+        return
     step16 = MappingStep(s16_bf, cams, rgb_t, dep_t, f_gt, model=model)
     if args.profile:
         for _ in range(args.warmup + args.steps):

@@ -8,8 +8,11 @@
 // tau_dist can satisfy the rule, so the neighbour search runs on a uniform
 // grid of cells just wider than tau_dist: the Gaussians are radix-sorted by
 // cell, and every query scans the 3 x 3 rows of three consecutive cells
-// around its own (each row one contiguous run of the sorted order, found by
-// binary search).  A query keeps the 16 nearest candidates in registers
+// around its own (each row one contiguous run of the sorted order).  Where
+// the grid has at most 8 cells per Gaussian a table holds each cell's first
+// sorted position, filled from the sorted keys, and a row's run is two loads;
+// a cell the table leaves open (one inside a gap of more than kFillRun empty
+// cells, or every cell of a larger grid) is found by binary search.  A query keeps the 16 nearest candidates in registers
 // (ranked by squared distance, then index), then tests its first K for
 // similarity and marks those it outranks (higher opacity logit, or equal
 // logit and lower index).
@@ -31,6 +34,9 @@ namespace {
 
 constexpr int kKnnMax = 16;
 constexpr int kPruneMaxDim = 64;
+constexpr int kCellsPerGaussian = 8;  // the largest grid the start table covers
+constexpr int kFillRun = 16;          // the longest run of cells one thread fills
+constexpr uint32_t kOpen = 0xffffffffu;
 
 struct Grid {
   float lo[3];
@@ -110,17 +116,91 @@ __device__ __forceinline__ int64_t lower_bound(const uint32_t* __restrict__ keys
   return lo;
 }
 
+// start[c] = the first sorted position with key >= c, for c in [0, cells]:
+// position t (t = n stands for the end) fills the cells after its
+// predecessor's key up to its own.  A run longer than kFillRun stays open
+// (kOpen, set beforehand), as does anything after keys out of order or out of
+// range (only a sort that gave up leaves those).
+__global__ void cell_start_kernel(const uint32_t* __restrict__ skey, int64_t n, uint32_t cells,
+                                  uint32_t* __restrict__ start) {
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t <= n;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t prev = t > 0 ? (int64_t)skey[t - 1] : -1;
+    const int64_t key = t < n ? (int64_t)skey[t] : (int64_t)cells;
+    const int64_t cur = key < (int64_t)cells ? key : (int64_t)cells;
+    if (cur - prev > kFillRun) continue;
+    for (int64_t c = prev + 1; c <= cur; c++) start[c] = (uint32_t)t;
+  }
+}
+
+__device__ __forceinline__ int64_t run_start(const uint32_t* __restrict__ start,
+                                             const uint32_t* __restrict__ keys, int64_t n,
+                                             uint32_t c) {
+  const uint32_t v = start ? start[c] : kOpen;
+  return v != kOpen ? (int64_t)v : lower_bound(keys, n, c);
+}
+
 __device__ __forceinline__ bool closer(float d2, uint32_t j, float e2, uint32_t ej) {
   return d2 < e2 || (d2 == e2 && j < ej);
 }
 
+// sequential sum over k of f_ik f_jk, whole rows fetched as 16-byte vectors
+// when every row starts on a 16-byte boundary (vec), else one element at a time
 template <typename T>
+__device__ __forceinline__ float row_dot(const T* __restrict__ f, uint32_t i, uint32_t j, int d,
+                                         bool vec);
+template <>
+__device__ __forceinline__ float row_dot<float>(const float* __restrict__ f, uint32_t i,
+                                                uint32_t j, int d, bool vec) {
+  float dot = 0.f;
+  if (vec) {
+    const float4* a = (const float4*)(f + (int64_t)d * i);
+    const float4* b = (const float4*)(f + (int64_t)d * j);
+    for (int c = 0; c < d / 4; c++) {
+      const float4 x = a[c], y = b[c];
+      dot = __fadd_rn(dot, __fmul_rn(x.x, y.x));
+      dot = __fadd_rn(dot, __fmul_rn(x.y, y.y));
+      dot = __fadd_rn(dot, __fmul_rn(x.z, y.z));
+      dot = __fadd_rn(dot, __fmul_rn(x.w, y.w));
+    }
+    return dot;
+  }
+  for (int k = 0; k < d; k++)
+    dot = __fadd_rn(dot, __fmul_rn(feat_at(f, i, d, k), feat_at(f, j, d, k)));
+  return dot;
+}
+template <>
+__device__ __forceinline__ float row_dot<__nv_bfloat16>(const __nv_bfloat16* __restrict__ f,
+                                                        uint32_t i, uint32_t j, int d, bool vec) {
+  float dot = 0.f;
+  if (vec) {
+    const uint4* a = (const uint4*)(f + (int64_t)d * i);
+    const uint4* b = (const uint4*)(f + (int64_t)d * j);
+    for (int c = 0; c < d / 8; c++) {
+      const uint4 x = a[c], y = b[c];
+      const uint32_t xs[4] = {x.x, x.y, x.z, x.w}, ys[4] = {y.x, y.y, y.z, y.w};
+#pragma unroll
+      for (int w = 0; w < 4; w++) {  // element 2w in the low half, 2w + 1 in the high half
+        dot = __fadd_rn(dot, __fmul_rn(__uint_as_float(xs[w] << 16), __uint_as_float(ys[w] << 16)));
+        dot = __fadd_rn(dot, __fmul_rn(__uint_as_float(xs[w] & 0xffff0000u),
+                                       __uint_as_float(ys[w] & 0xffff0000u)));
+      }
+    }
+    return dot;
+  }
+  for (int k = 0; k < d; k++)
+    dot = __fadd_rn(dot, __fmul_rn(feat_at(f, i, d, k), feat_at(f, j, d, k)));
+  return dot;
+}
+
+// KM: the length of the nearest-candidate list, at least K
+template <typename T, int KM>
 __global__ void __launch_bounds__(128)
     prune_knn_kernel(const uint32_t* __restrict__ skey, const uint32_t* __restrict__ sidx,
                      const float4* __restrict__ sp, int64_t n, Grid grid, int K, float tau,
-                     float tau_sim, const T* __restrict__ feats, int d,
+                     float tau_sim, const T* __restrict__ feats, int d, bool vec,
                      const float* __restrict__ norms, const float* __restrict__ logits,
-                     uint8_t* __restrict__ redundant) {
+                     const uint32_t* __restrict__ start, uint8_t* __restrict__ redundant) {
   for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n;
        t += (int64_t)gridDim.x * blockDim.x) {
     const uint32_t i = sidx[t];
@@ -130,10 +210,10 @@ __global__ void __launch_bounds__(128)
     const uint32_t cx = key % grid.g[0];
     const uint32_t cy = (key / grid.g[0]) % grid.g[1];
     const uint32_t cz = key / (grid.g[0] * grid.g[1]);
-    float bd[kKnnMax];
-    uint32_t bj[kKnnMax];
+    float bd[KM];
+    uint32_t bj[KM];
 #pragma unroll
-    for (int s = 0; s < kKnnMax; s++) {
+    for (int s = 0; s < KM; s++) {
       bd[s] = INFINITY;
       bj[s] = 0xffffffffu;
     }
@@ -145,8 +225,8 @@ __global__ void __launch_bounds__(128)
         const int64_t yy = (int64_t)cy + dy;
         if (yy < 0 || yy >= grid.g[1]) continue;
         const uint32_t row = ((uint32_t)zz * grid.g[1] + (uint32_t)yy) * grid.g[0];
-        const int64_t a = lower_bound(skey, n, row + x0);
-        const int64_t b = lower_bound(skey, n, row + x1 + 1);
+        const int64_t a = run_start(start, skey, n, row + x0);
+        const int64_t b = run_start(start, skey, n, row + x1 + 1);
         for (int64_t u = a; u < b; u++) {
           if (u == t) continue;
           const float4 pj = sp[u];
@@ -156,10 +236,10 @@ __global__ void __launch_bounds__(128)
               __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy2, dy2)), __fmul_rn(dz2, dz2));
           if (!(__fsqrt_rn(d2) < tau)) continue;
           const uint32_t j = sidx[u];
-          if (j >= n || !closer(d2, j, bd[kKnnMax - 1], bj[kKnnMax - 1])) continue;
+          if (j >= n || !closer(d2, j, bd[KM - 1], bj[KM - 1])) continue;
           // insert into the sorted list: e[s-1] <= new < e[s]
 #pragma unroll
-          for (int s = kKnnMax - 1; s > 0; s--) {
+          for (int s = KM - 1; s > 0; s--) {
             const bool up = closer(d2, j, bd[s - 1], bj[s - 1]);
             const bool here = !up && closer(d2, j, bd[s], bj[s]);
             const float nd = up ? bd[s - 1] : (here ? d2 : bd[s]);
@@ -177,14 +257,12 @@ __global__ void __launch_bounds__(128)
     const float ni = norms[i];
     const float li = pi.w;
 #pragma unroll
-    for (int s = 0; s < kKnnMax; s++) {
+    for (int s = 0; s < KM; s++) {
       if (s >= K || bj[s] == 0xffffffffu) break;
       const uint32_t j = bj[s];
       const float lj = logits[j];
       if (!(li > lj || (li == lj && i < j))) continue;  // G_i is not the one to keep
-      float dot = 0.f;
-      for (int k = 0; k < d; k++)
-        dot = __fadd_rn(dot, __fmul_rn(feat_at(feats, i, d, k), feat_at(feats, j, d, k)));
+      const float dot = row_dot(feats, i, j, d, vec);
       const float nn = __fmul_rn(ni, norms[j]);
       const float sim = nn > 0.f ? __fdiv_rn(dot, nn) : 0.f;
       if (sim > tau_sim) redundant[j] = 1;  // every writer stores the same byte
@@ -315,7 +393,7 @@ __global__ void gather_rows_kernel(const W* __restrict__ src, int64_t n, int wor
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 struct PruneLayout {
-  size_t k0, k1, v0, v1, sp, norms, red, sort, total;
+  size_t k0, k1, v0, v1, sp, norms, red, start, sort, total;
 };
 
 PruneLayout prune_layout(int64_t n) {
@@ -324,6 +402,7 @@ PruneLayout prune_layout(int64_t n) {
   auto take = [&](size_t b) { size_t at = o; o += align256(b > 0 ? b : 1); return at; };
   L.k0 = take(4 * n); L.k1 = take(4 * n); L.v0 = take(4 * n); L.v1 = take(4 * n);
   L.sp = take(16 * n); L.norms = take(4 * n); L.red = take(n);
+  L.start = take(4 * (kCellsPerGaussian * (size_t)n + 1));
   L.sort = take(sort_pairs_scratch(n));
   L.total = o;
   return L;
@@ -336,7 +415,7 @@ int grid_for(int64_t n, int threads) {
 template <typename T>
 void launch_prune(const float* means, const float* logits, const float* log_scales,
                   const void* feats, int d, int64_t n, const lgs_prune_params& P, const Grid& g,
-                  int nbits, float thr_logit, float thr_logscale, uint8_t* mask,
+                  uint64_t cells, int nbits, float thr_logit, float thr_logscale, uint8_t* mask,
                   int64_t* n_pruned, char* ws, const PruneLayout& L, cudaStream_t s) {
   uint32_t *k0 = (uint32_t*)(ws + L.k0), *k1 = (uint32_t*)(ws + L.k1);
   uint32_t *v0 = (uint32_t*)(ws + L.v0), *v1 = (uint32_t*)(ws + L.v1);
@@ -353,8 +432,21 @@ void launch_prune(const float* means, const float* logits, const float* log_scal
   }
   prune_gather_kernel<<<grid_for(n, 256), 256, 0, s>>>(means, logits, v0, n, sp);
   cudaMemsetAsync(red, 0, (size_t)n, s);
-  prune_knn_kernel<T><<<(unsigned)std::max<int64_t>(1, (n + 127) / 128), 128, 0, s>>>(
-      k0, v0, sp, n, g, P.k, P.tau_dist, P.tau_sim, f, d, norms, logits, red);
+  uint32_t* start = nullptr;
+  if (cells <= (uint64_t)kCellsPerGaussian * (uint64_t)n) {
+    start = (uint32_t*)(ws + L.start);
+    cudaMemsetAsync(start, 0xff, 4 * (size_t)(cells + 1), s);
+    cell_start_kernel<<<grid_for(n + 1, 256), 256, 0, s>>>(k0, n, (uint32_t)cells, start);
+  }
+  const bool vec = d % (int)(16 / sizeof(T)) == 0 && ((uintptr_t)feats & 15) == 0;
+  const unsigned blocks = (unsigned)std::max<int64_t>(1, (n + 127) / 128);
+  if (P.k <= 8)
+    prune_knn_kernel<T, 8><<<blocks, 128, 0, s>>>(k0, v0, sp, n, g, P.k, P.tau_dist, P.tau_sim,
+                                                   f, d, vec, norms, logits, start, red);
+  else
+    prune_knn_kernel<T, kKnnMax><<<blocks, 128, 0, s>>>(k0, v0, sp, n, g, P.k, P.tau_dist,
+                                                         P.tau_sim, f, d, vec, norms, logits,
+                                                         start, red);
   prune_final_kernel<<<grid_for(n, 256), 256, 0, s>>>(red, n, mask,
                                                       (unsigned long long*)n_pruned);
 }
@@ -424,11 +516,12 @@ extern "C" lgs_status gs_prune(const float* means, const float* opacity_logits,
   LGS_CHECK_CUDA(cudaMemsetAsync(n_pruned_dev, 0, sizeof(int64_t), s));
   if (n == 0) return LGS_OK;
   if (feat_dtype == LGS_F32)
-    launch_prune<float>(means, opacity_logits, log_scales, feats, feat_dim, n, P, g, nbits,
-                        thr_logit, thr_logscale, mask, n_pruned_dev, (char*)workspace, L, s);
+    launch_prune<float>(means, opacity_logits, log_scales, feats, feat_dim, n, P, g, total,
+                        nbits, thr_logit, thr_logscale, mask, n_pruned_dev, (char*)workspace, L,
+                        s);
   else
     launch_prune<__nv_bfloat16>(means, opacity_logits, log_scales, feats, feat_dim, n, P, g,
-                                nbits, thr_logit, thr_logscale, mask, n_pruned_dev,
+                                total, nbits, thr_logit, thr_logscale, mask, n_pruned_dev,
                                 (char*)workspace, L, s);
   LGS_CHECK_LAUNCH();
   return LGS_OK;

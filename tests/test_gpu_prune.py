@@ -63,6 +63,28 @@ def test_prune_matches_oracle(lgs, oracle_lib, dtype, kw):
     assert (ref & 2).sum() > 100  # the rule fires
 
 
+@pytest.mark.parametrize("dtype,d,k,tau", [(torch.bfloat16, 12, 8, 0.03),
+                                            (torch.float32, 12, 5, 0.035),
+                                            (torch.float32, 13, 12, 0.035),
+                                            (torch.bfloat16, 64, 16, 0.03)])
+def test_prune_feature_widths(lgs, oracle_lib, dtype, d, k, tau):
+    """Feature rows read element by element (BF16 widths that are not a
+    multiple of 8, FP32 widths not a multiple of 4) or as 16-byte vectors,
+    with candidate lists of 8 and 16 entries, on grids of more (0.03) and
+    fewer (0.035) than 8 cells per Gaussian."""
+    p, lg, ls, f = _clustered(5000, 13)
+    rng = np.random.default_rng(14)
+    f = np.ascontiguousarray(f[:, rng.integers(0, 16, d)]
+                             + 0.05 * rng.standard_normal((5000, d)).astype(np.float32))
+    kw = dict(k=k, tau_dist=tau, tau_sim=0.8)
+    m, cnt = _run(lgs, p, lg, ls, f, dtype, **kw)
+    fo = bf16_round(f) if dtype == torch.bfloat16 else f
+    ref = oracle_lib.prune(p, lg, ls, fo, **kw)
+    np.testing.assert_array_equal(m, ref)
+    assert cnt == int((ref != 0).sum())
+    assert (ref & 2).sum() > 100
+
+
 def test_prune_points_outside_the_bounds(lgs, oracle_lib):
     """Bounds that cover only part of the scene: the border cells absorb the
     rest and the result is unchanged."""

@@ -8,7 +8,9 @@
 //   F1..F3  forward hidden layers, activations kept in shared memory (BF16);
 //   F4/B1   the 512-wide output in eight 64-column chunks: each chunk's
 //           epilogue forms dy = w sign(y - F_gt) / (P 512) and immediately
-//           feeds dh3 += dy_chunk W7_chunk, so y and dy never reach memory;
+//           feeds dh3 += dy_chunk W7_chunk, so y and dy never reach memory
+//           (dy goes back into tensor memory, double-buffered, as the A
+//           operand of that product);
 //           B1 reads the chunk's W7 units that F4 used, still in the ring, as
 //           an MN-major operand (W7 is streamed once per tile, W7^T never);
 //   R3..R1  the pre-activations are recomputed instead of stored (this keeps
@@ -21,11 +23,12 @@
 // core works on one tile while the epilogue warps work on the other.  z is
 // double-buffered for this.  The output epilogue reads F_gt with one 32-byte
 // load per lane (its row's 16 columns of the chunk, one sector) a chunk ahead.
-// Warps 0-15 are the epilogue (TMEM -> registers -> shared memory; warps w,
-// w + 4, w + 8, w + 12 share TMEM lane quadrant w % 4 and split the columns in
-// quarters), warp 16 issues the MMAs, warps 17 and 18 stream the weights as
-// 35 pre-packed units (<= 16 KB each, already in the tensor-core's canonical
-// layout) through a 5-stage ring with bulk TMA copies.  Every wait is bounded.
+// Warps 0-15 are the epilogue (TMEM -> registers -> shared memory, or back to
+// TMEM for dy and d1; warps w, w + 4, w + 8, w + 12 share TMEM lane quadrant
+// w % 4 and split the columns in quarters), warp 16 issues the MMAs, warps 17
+// and 18 stream the weights as 35 pre-packed units (<= 16 KB each, already in
+// the tensor-core's canonical layout) through a 6-stage ring with bulk TMA
+// copies.  Every wait is bounded.
 #include <mutex>
 #include <type_traits>
 #include <vector>
@@ -39,7 +42,7 @@ namespace lgs {
 namespace {
 
 constexpr int kUnits = 35;
-constexpr int kStages = 5;
+constexpr int kStages = 6;
 constexpr uint32_t kStageBytes = 16384;
 constexpr uint32_t kLimit = 1u << 22;
 
@@ -48,9 +51,14 @@ constexpr uint32_t SM_Z = 0;         // 2 x (128 x 16 bf16): z of this tile and 
 constexpr uint32_t SM_H1 = 8192;     // 128 x 64   (h1)
 constexpr uint32_t SM_H2 = 24576;    // 128 x 128  (h2, later d2)
 constexpr uint32_t SM_H3 = 57344;    // 128 x 256  (h3, later d3)
-constexpr uint32_t SM_DY = 122880;   // 128 x 64   (one dy chunk, later d1)
-constexpr uint32_t SM_ST = 139264;   // kStages x 16 KB weight ring
+constexpr uint32_t SM_ST = 122880;   // kStages x 16 KB weight ring
 constexpr uint32_t SM_BAR = SM_ST + kStages * kStageBytes;
+
+// tensor-memory columns of the BF16 A operands the epilogue stores there:
+// the two dy chunk buffers (free during the output phase, whose forward
+// chunks use 256-383 and B1 0-255) and d1 (pre2's columns, read by E6 before)
+constexpr uint32_t TM_DY = 384;      // 2 x 32 columns (128 x 64 BF16 each)
+constexpr uint32_t TM_D1 = 128;      // 32 columns
 
 // weight matrices of the decoder: forward W (out x in) and transposed Wt
 enum Mat { W4 = 0, W5, W6, W7, T4, T5, T6, T7 };
@@ -142,14 +150,13 @@ constexpr int kEpiWarps = 16;
 constexpr int kProducers = 2;                          // warps streaming the weight units
 constexpr int kFusedThreads = (kEpiWarps + 1 + kProducers) * 32;  // + the MMA warp
 // barriers: full[kStages], empty[kStages], accH, accT, opH, opT, ybar[2],
-// dyfree, drain, the slice barriers sh2[2], sh3[4], sd2[2], sd3[4], then the
-// TMEM slot
-constexpr uint32_t kBarBytes = (2 * kStages + 20) * 8 + 4;
+// drain, the slice barriers sh2[2], sh3[4], sd2[2], sd3[4], then the TMEM slot
+constexpr uint32_t kBarBytes = (2 * kStages + 19) * 8 + 4;
 constexpr uint32_t SM_BIAS = SM_BAR + 256;             // b4 | b5 | b6 | b7 (960 floats)
 constexpr uint32_t SM_ALL = SM_BIAS + 960 * 4;
 static_assert(kBarBytes <= SM_BIAS - SM_BAR, "barrier block overlaps the biases");
 static_assert(SM_ALL <= 232448, "shared-memory map exceeds 227 KB");
-static_assert(SM_DY + 128 * 64 * 2 <= SM_ST, "dy buffer overlaps the ring");
+static_assert(SM_H3 + 128 * 256 * 2 <= SM_ST, "h3 overlaps the ring");
 
 // Weight units per tile in stream order.  Units 0-5 are the forward hidden
 // layers (F1, F2, F3), 6-21 the output layer (F4, its units read again by
@@ -186,8 +193,7 @@ decode_fused_kernel(const __grid_constant__ FusedArgs a) {
   uint64_t* opH = accT + 1;             // epilogue -> MMA: z / h1 / h2 / h3 staged
   uint64_t* opT = opH + 1;              // epilogue -> MMA: a dy chunk / d3 / d2 / d1 / dz done
   uint64_t* ybar = opT + 1;             // [2] output chunk ready in TMEM buffer c & 1
-  uint64_t* dyfree = ybar + 2;          // the backward product of the last dy chunk is done
-  uint64_t* drain = dyfree + 1;         // a give-up waits here for the MMAs already issued
+  uint64_t* drain = ybar + 2;           // a give-up waits here for the MMAs already issued
   // epilogue -> MMA, one phase per tile: 64-column slice s of h2 / h3 / d2 / d3
   // written (the next GEMM's K-slices start as soon as theirs are in)
   uint64_t* sh2 = drain + 1;            // [2]
@@ -216,7 +222,6 @@ decode_fused_kernel(const __grid_constant__ FusedArgs a) {
     tc::mbar_init(opT, kEpiWarps);
     tc::mbar_init(&ybar[0], 1);
     tc::mbar_init(&ybar[1], 1);
-    tc::mbar_init(dyfree, 1);
     tc::mbar_init(drain, 1);
     for (int i = 0; i < 12; i++) tc::mbar_init(&sh2[i], kEpiWarps);  // sh2 .. sd3
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -286,9 +291,10 @@ decode_fused_kernel(const __grid_constant__ FusedArgs a) {
     // one weight unit: B = ring stage, A = activation tile at a_off (width
     // a_kw) from column k0, D = TMEM column dcol, N = n, K = kc; the stage is
     // released after its MMAs unless `hold` (an output unit, read again by
-    // its chunk's B1); returns the stage
+    // its chunk's B1); returns the stage.  With a_tcol >= 0, A is in TMEM from
+    // that column instead
     auto unit = [&](uint32_t a_off, int a_kw, int k0, int kc, int n, uint32_t dcol, bool fresh,
-                    bool hold = false) -> uint32_t {
+                    bool hold = false, int a_tcol = -1) -> uint32_t {
       const uint32_t s = u % kStages, round = u / kStages;
       if (!ok) return s;
       ok = __all_sync(0xffffffffu, tc::mbar_wait(&full[s], round & 1, kLimit));
@@ -298,8 +304,14 @@ decode_fused_kernel(const __grid_constant__ FusedArgs a) {
       const uint64_t bd = dbase + tc::sdesc_off(SM_ST + s * kStageBytes, (uint32_t)kc * 16);
       const uint32_t idesc = tc::idesc_bf16(128, n);
       if (tc::elect_one()) {
-        for (int j = 0; j < kc / 16; j++)
-          tc::mma_bf16(tmem + dcol, ad + 16 * j, bd + 16 * j, idesc, (fresh && j == 0) ? 0u : 1u);
+        for (int j = 0; j < kc / 16; j++) {
+          if (a_tcol >= 0)
+            tc::mma_bf16_ts(tmem + dcol, tmem + (uint32_t)a_tcol + 8 * j, bd + 16 * j, idesc,
+                            (fresh && j == 0) ? 0u : 1u);
+          else
+            tc::mma_bf16(tmem + dcol, ad + 16 * j, bd + 16 * j, idesc,
+                         (fresh && j == 0) ? 0u : 1u);
+        }
         if (!hold) tc::commit(&empty[s]);
       }
       __syncwarp();
@@ -342,10 +354,12 @@ decode_fused_kernel(const __grid_constant__ FusedArgs a) {
         }
         commit(&ybar[c & 1]);
       };
-      // B1 c: dh3[:, 128 h ..] += dy_c W7[64 c .., 128 h ..]^T, B = the held
-      // unit h as an MN-major operand (K = the chunk's 64 outputs, core
-      // matrices 2 KB apart; N = 128 of h3's columns, 128 B apart); then both
-      // stages are released and dyfree announces the dy buffer free
+      // B1 c: dh3[:, 128 h ..] += dy_c W7[64 c .., 128 h ..]^T, A = dy_c in
+      // TMEM buffer c & 1, B = the held unit h as an MN-major operand (K = the
+      // chunk's 64 outputs, core matrices 2 KB apart; N = 128 of h3's columns,
+      // 128 B apart); then both stages are released.  The epilogue refills
+      // buffer c & 1 with chunk c + 2 only after ybar announces F4 c + 2,
+      // which this thread issues after B1 c, so the commit covers B1 c too
       const uint32_t idesc_b1 = tc::idesc_bf16(128, 128) | (1u << 16);
       auto b1 = [&](int c) {
         if (!ok) return;
@@ -353,14 +367,12 @@ decode_fused_kernel(const __grid_constant__ FusedArgs a) {
           for (int h = 0; h < 2; h++) {
             const uint32_t st = sbase + SM_ST + held[c & 1][h] * kStageBytes;
             for (int j = 0; j < 4; j++)
-              tc::mma_bf16(tmem + 128 * h,
-                           dbase + tc::sdesc_off(SM_DY + (uint32_t)j * 256, 64 * 16),
-                           tc::sdesc(st + (uint32_t)j * 4096, 2048, 128), idesc_b1,
-                           (c == 0 && j == 0) ? 0u : 1u);
+              tc::mma_bf16_ts(tmem + 128 * h, tmem + TM_DY + 32 * (c & 1) + 8 * j,
+                              tc::sdesc(st + (uint32_t)j * 4096, 2048, 128), idesc_b1,
+                              (c == 0 && j == 0) ? 0u : 1u);
           }
           tc::commit(&empty[held[c & 1][0]]);
           tc::commit(&empty[held[c & 1][1]]);
-          tc::commit(dyfree);
         }
         __syncwarp();
       };
@@ -400,7 +412,7 @@ decode_fused_kernel(const __grid_constant__ FusedArgs a) {
         f2();
       }
       wait_on(opT, nopT);                                            // d1 written
-      unit(SM_DY, 64, 0, 64, 16, 0, true);                           // B4
+      unit(0, 64, 0, 64, 16, 0, true, false, (int)TM_D1);            // B4 (A = d1 in TMEM)
       commit(accT);
       if (next) f3(par ^ 1u);
     }
@@ -583,17 +595,12 @@ decode_fused_kernel(const __grid_constant__ FusedArgs a) {
           dy[0] = make_uint4(0u, 0u, 0u, 0u);
           dy[1] = make_uint4(0u, 0u, 0u, 0u);
         }
-        if (c > 0) {  // the previous chunk's product has read the dy buffer
-          ok = ok && tc::mbar_wait(dyfree, (c - 1) & 1, kLimit);
-          tc::fence_after();
-        }
-#pragma unroll
-        for (int kk = 0; kk < 2; kk++)
-          *reinterpret_cast<uint4*>(sm + SM_DY + tc::core_offset(r, 2 * qq + kk, 64)) = dy[kk];
+        // dy into TMEM buffer c & 1 (this warp's 16 columns = 8 TMEM columns),
+        // whose last reader B1 c - 2 finished before ybar announced chunk c
+        tc::tmem_st8(tb + TM_DY + 32 * (c & 1) + 8 * qq, reinterpret_cast<const uint32_t*>(dy));
+        tc::tmem_wait_st();
         arrive(opT);
       }
-      ok = ok && tc::mbar_wait(dyfree, 1, kLimit);  // the last chunk's phase
-      tc::fence_after();
       // E5: d3 = dh3 * gelu'(pre3), 64-column slice s by all 16 warps in step
       // s (this warp: columns 16 qq + 64 s ..), each slice announced on sd3[s]
       wait_acc(accT, nT);
@@ -651,7 +658,8 @@ decode_fused_kernel(const __grid_constant__ FusedArgs a) {
         }
       }
       if (next) e1();
-      // E7: d1 = dh1 * gelu'(pre1), into the dy buffer (free once R3 is done)
+      // E7: d1 = dh1 * gelu'(pre1), into TMEM columns TM_D1.. (pre2's: every
+      // warp has read them in E6, which R1's commit implies)
       wait_acc(accT, nT);
       {
         const int c0 = 16 * qq;
@@ -664,7 +672,15 @@ decode_fused_kernel(const __grid_constant__ FusedArgs a) {
           v[i] = d.x;
           v[i + 1] = d.y;
         }
-        put_row<16>(sm + SM_DY, r, c0, 64, v);
+        // BF16 pairs into TMEM columns TM_D1 + 8 qq .. (B4's A operand)
+        uint32_t pk[8];
+#pragma unroll
+        for (int i = 0; i < 8; i++) {
+          const __nv_bfloat162 h = __floats2bfloat162_rn(v[2 * i], v[2 * i + 1]);
+          pk[i] = *reinterpret_cast<const uint32_t*>(&h);
+        }
+        tc::tmem_st8(tb + TM_D1 + 8 * qq, pk);
+        tc::tmem_wait_st();
       }
       arrive(opT);
       if (next) e2();

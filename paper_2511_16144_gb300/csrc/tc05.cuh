@@ -94,6 +94,18 @@ __device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t a, uint64_t b
       "l"(a), "l"(b), "r"(idesc), "r"(accumulate));
 }
 
+// D += A B with A in tensor memory: row m of A in TMEM lane m, its K BF16
+// values packed in pairs along consecutive columns from tmem_a (element 2i in
+// the low half of column i), B from shared memory as in mma_bf16.
+__device__ __forceinline__ void mma_bf16_ts(uint32_t tmem_d, uint32_t tmem_a, uint64_t b,
+                                            uint32_t idesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n\t}\n" ::"r"(tmem_d),
+      "r"(tmem_a), "l"(b), "r"(idesc), "r"(accumulate));
+}
+
 // Arrives on `bar` once every tcgen05 op issued so far by this thread is done.
 __device__ __forceinline__ void commit(uint64_t* bar) {
   asm volatile(
@@ -184,6 +196,20 @@ __device__ __forceinline__ void tmem_ld16x2(uint32_t ta, float* va, uint32_t tb,
     va[i] = __uint_as_float(r[i]);
     vb[i] = __uint_as_float(r[16 + i]);
   }
+}
+
+// 32 lanes x 8 consecutive 32-bit columns stored from registers, and the wait
+// that makes them visible to the issuing thread's later tcgen05 operations
+// (after it, fence_before + a barrier hands them to the MMA issuer).
+__device__ __forceinline__ void tmem_st8(uint32_t taddr, const uint32_t* r) {
+  asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"r"(
+                   taddr),
+               "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]),
+               "r"(r[7])
+               : "memory");
+}
+__device__ __forceinline__ void tmem_wait_st() {
+  asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
 }
 
 // One 32 x 16 load without the wait (see tmem_wait16).

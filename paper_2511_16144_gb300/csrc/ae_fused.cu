@@ -447,6 +447,12 @@ decode_fused_kernel(const __grid_constant__ FusedArgs a) {
       __syncwarp();
       if (lane == 0) tc::mbar_arrive(bar);
     };
+    // the same after TMEM accesses only (no shared-memory writes to publish)
+    auto arrive_tmem = [&](uint64_t* bar) {
+      tc::fence_before();
+      __syncwarp();
+      if (lane == 0) tc::mbar_arrive(bar);
+    };
     // E0: z (f32) of tile t -> bf16 A operand in buffer zb, columns [8 qq, 8 qq + 8)
     auto stage_z = [&](int64_t t, uint32_t zb) {
       if (qq < 2) {
@@ -599,7 +605,7 @@ decode_fused_kernel(const __grid_constant__ FusedArgs a) {
         // whose last reader B1 c - 2 finished before ybar announced chunk c
         tc::tmem_st8(tb + TM_DY + 32 * (c & 1) + 8 * qq, reinterpret_cast<const uint32_t*>(dy));
         tc::tmem_wait_st();
-        arrive(opT);
+        arrive_tmem(opT);
       }
       // E5: d3 = dh3 * gelu'(pre3), 64-column slice s by all 16 warps in step
       // s (this warp: columns 16 qq + 64 s ..), each slice announced on sd3[s]
@@ -682,7 +688,7 @@ decode_fused_kernel(const __grid_constant__ FusedArgs a) {
         tc::tmem_st8(tb + TM_D1 + 8 * qq, pk);
         tc::tmem_wait_st();
       }
-      arrive(opT);
+      arrive_tmem(opT);
       if (next) e2();
       // E8: dz
       wait_acc(accT, nT);
@@ -695,7 +701,7 @@ decode_fused_kernel(const __grid_constant__ FusedArgs a) {
             dst[kk] = make_float4(v[4 * kk], v[4 * kk + 1], v[4 * kk + 2], v[4 * kk + 3]);
         }
       }
-      arrive(opT);
+      arrive_tmem(opT);
       if (next) {
         load_fgt(t + gridDim.x, 0);
         e3();

@@ -149,10 +149,10 @@ __device__ unsigned g_fused_error;
 constexpr int kEpiWarps = 16;
 constexpr int kProducers = 2;                          // warps streaming the weight units
 constexpr int kFusedThreads = (kEpiWarps + 1 + kProducers) * 32;  // + the MMA warp
-// barriers: full[kStages], empty[kStages], accH, accT, opH, opT, ybar[2],
+// barriers: full[kStages], empty[kStages], accH, accT, opH, opT, ybar[2], dyrdy[2],
 // drain, the slice barriers sh2[2], sh3[4], sd2[2], sd3[4], then the TMEM slot
-constexpr uint32_t kBarBytes = (2 * kStages + 19) * 8 + 4;
-constexpr uint32_t SM_BIAS = SM_BAR + 256;             // b4 | b5 | b6 | b7 (960 floats)
+constexpr uint32_t kBarBytes = (2 * kStages + 21) * 8 + 4;
+constexpr uint32_t SM_BIAS = SM_BAR + 512;             // b4 | b5 | b6 | b7 (960 floats)
 constexpr uint32_t SM_ALL = SM_BIAS + 960 * 4;
 static_assert(kBarBytes <= SM_BIAS - SM_BAR, "barrier block overlaps the biases");
 static_assert(SM_ALL <= 232448, "shared-memory map exceeds 227 KB");
@@ -191,9 +191,16 @@ decode_fused_kernel(const __grid_constant__ FusedArgs a) {
   uint64_t* accH = full + 2 * kStages;  // MMA -> epilogue: a forward hidden layer is done
   uint64_t* accT = accH + 1;            // MMA -> epilogue: a backward group is done
   uint64_t* opH = accT + 1;             // epilogue -> MMA: z / h1 / h2 / h3 staged
-  uint64_t* opT = opH + 1;              // epilogue -> MMA: a dy chunk / d3 / d2 / d1 / dz done
+  uint64_t* opT = opH + 1;              // epilogue -> MMA: d1 written / dz read
   uint64_t* ybar = opT + 1;             // [2] output chunk ready in TMEM buffer c & 1
-  uint64_t* drain = ybar + 2;           // a give-up waits here for the MMAs already issued
+  // [2] epilogue -> MMA: dy chunk c written, on dyrdy[c & 1].  Two barriers,
+  // because a warp may finish chunk c + 1 before a slower one has finished
+  // chunk c (nothing else holds it back: the dy buffers alternate), and on
+  // one barrier its second arrival would complete chunk c's phase early.  It
+  // cannot reach chunk c + 2, whose output F4 c + 2 issues only after every
+  // warp's chunk c, so each barrier sees one arrival per warp and phase.
+  uint64_t* dyrdy = ybar + 2;
+  uint64_t* drain = dyrdy + 2;          // a give-up waits here for the MMAs already issued
   // epilogue -> MMA, one phase per tile: 64-column slice s of h2 / h3 / d2 / d3
   // written (the next GEMM's K-slices start as soon as theirs are in)
   uint64_t* sh2 = drain + 1;            // [2]
@@ -222,6 +229,8 @@ decode_fused_kernel(const __grid_constant__ FusedArgs a) {
     tc::mbar_init(opT, kEpiWarps);
     tc::mbar_init(&ybar[0], 1);
     tc::mbar_init(&ybar[1], 1);
+    tc::mbar_init(&dyrdy[0], kEpiWarps);
+    tc::mbar_init(&dyrdy[1], kEpiWarps);
     tc::mbar_init(drain, 1);
     for (int i = 0; i < 12; i++) tc::mbar_init(&sh2[i], kEpiWarps);  // sh2 .. sd3
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -380,7 +389,7 @@ decode_fused_kernel(const __grid_constant__ FusedArgs a) {
       f4(1);
 #pragma unroll
       for (int c = 0; c < 8; c++) {
-        wait_on(opT, nopT);                                          // dy chunk c written
+        wait_slice(&dyrdy[c & 1], (uint32_t)(c >> 1) & 1u);          // dy chunk c written
         b1(c);
         if (c < 6) f4(c + 2);
       }
@@ -605,7 +614,7 @@ decode_fused_kernel(const __grid_constant__ FusedArgs a) {
         // whose last reader B1 c - 2 finished before ybar announced chunk c
         tc::tmem_st8(tb + TM_DY + 32 * (c & 1) + 8 * qq, reinterpret_cast<const uint32_t*>(dy));
         tc::tmem_wait_st();
-        arrive_tmem(opT);
+        arrive_tmem(&dyrdy[c & 1]);
       }
       // E5: d3 = dh3 * gelu'(pre3), 64-column slice s by all 16 warps in step
       // s (this warp: columns 16 qq + 64 s ..), each slice announced on sd3[s]

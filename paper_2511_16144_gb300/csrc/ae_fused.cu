@@ -580,8 +580,13 @@ decode_fused_kernel(const __grid_constant__ FusedArgs a) {
         uint4 dy[2];
         uint32_t ya[16];
         float lc = 0.f;  // this chunk's sum of |d|
-        tc::tmem_ld16_issue(tb + 256 + 64 * (c & 1) + 16 * qq, ya);
+        bool anyz = false;
+        const uint32_t ycol = tb + 256 + 64 * (c & 1) + 16 * qq;
+        tc::tmem_ld16_issue(ycol, ya);
         tc::tmem_wait16(ya);
+        // the BF16 pair of sign(d) * scale: d's sign bits applied to the BF16
+        // pattern of scale; a d that is exactly 0 (its gradient is 0) only
+        // raises anyz here and is handled below
 #pragma unroll
         for (int kk = 0; kk < 2; kk++) {
           const __nv_bfloat162* h2 = reinterpret_cast<const __nv_bfloat162*>(&tg[kk]);
@@ -595,13 +600,32 @@ decode_fused_kernel(const __grid_constant__ FusedArgs a) {
                            *reinterpret_cast<const float2*>(sb7 + n0 + i)),
                 f2(-tt.x, -tt.y));
             lc += fabsf(dd.x) + fabsf(dd.y);
-            // BF16 pair of sign(d) * scale: d's sign bits applied to the
-            // BF16 pattern of scale, a zero half where d is exactly 0
-            uint32_t w = (__byte_perm(__float_as_uint(dd.x), __float_as_uint(dd.y), 0x7632) &
-                          0x80008000u) ^ s2bf;
-            if (dd.x == 0.f) w &= 0xffff0000u;
-            if (dd.y == 0.f) w &= 0x0000ffffu;
-            reinterpret_cast<uint32_t*>(o2)[e] = w;
+            anyz |= (dd.x == 0.f) | (dd.y == 0.f);
+            reinterpret_cast<uint32_t*>(o2)[e] =
+                (__byte_perm(__float_as_uint(dd.x), __float_as_uint(dd.y), 0x7632) & 0x80008000u) ^
+                s2bf;
+          }
+        }
+        if (__any_sync(0xffffffffu, anyz)) {
+          // rare: some d of the warp is exactly 0; the warp reloads the chunk
+          // (the TMEM load is warp-collective) and zeroes those halves
+          tc::tmem_ld16_issue(ycol, ya);
+          tc::tmem_wait16(ya);
+#pragma unroll
+          for (int kk = 0; kk < 2; kk++) {
+            const __nv_bfloat162* h2 = reinterpret_cast<const __nv_bfloat162*>(&tg[kk]);
+            uint32_t* o = reinterpret_cast<uint32_t*>(&dy[kk]);
+#pragma unroll
+            for (int e = 0; e < 4; e++) {
+              const float2 tt = __bfloat1622float2(h2[e]);
+              const int i = 8 * kk + 2 * e;
+              const float2 dd = __fadd2_rn(
+                  __fadd2_rn(f2(__uint_as_float(ya[i]), __uint_as_float(ya[i + 1])),
+                             *reinterpret_cast<const float2*>(sb7 + n0 + i)),
+                  f2(-tt.x, -tt.y));
+              if (dd.x == 0.f) o[e] &= 0xffff0000u;
+              if (dd.y == 0.f) o[e] &= 0x0000ffffu;
+            }
           }
         }
         if (valid) {

@@ -622,7 +622,7 @@ TRAFFIC = {  # call group -> (bytes per launch, source digest)
     "gs_bin_sort": (37627648, "18d76b8a2256"),
     "gs_render_fwd": (5515264, "011d53f72718"),
     "l1_losses": (9845504, "792f0809c2a4"),
-    "ae_decode": (349359360, "237406040412"),
+    "ae_decode": (349692160, "ec4aea27d248"),
     "gs_render_bwd": (41203456, "5fcc646473a8"),
 }
 

@@ -146,6 +146,14 @@ __device__ __forceinline__ void put_row(uint8_t* tile, int r, int col, int kw, c
 
 __device__ unsigned g_fused_error;
 
+// -x and -y of a BF16 pair (x in the low half) as floats: the BF16 bits moved
+// to the top of the FP32 word with the sign flipped (exact, as is -t itself)
+__device__ __forceinline__ float2 neg_bf16x2(__nv_bfloat162 h) {
+  const uint32_t w = *reinterpret_cast<const uint32_t*>(&h);
+  return f2(__uint_as_float((w << 16) ^ 0x80000000u),
+            __uint_as_float((w & 0xffff0000u) ^ 0x80000000u));
+}
+
 constexpr int kEpiWarps = 16;
 constexpr int kProducers = 2;                          // warps streaming the weight units
 constexpr int kFusedThreads = (kEpiWarps + 1 + kProducers) * 32;  // + the MMA warp
@@ -593,12 +601,12 @@ decode_fused_kernel(const __grid_constant__ FusedArgs a) {
           __nv_bfloat162* o2 = reinterpret_cast<__nv_bfloat162*>(&dy[kk]);
 #pragma unroll
           for (int e = 0; e < 4; e++) {
-            const float2 tt = __bfloat1622float2(h2[e]);
+            const float2 nt = neg_bf16x2(h2[e]);
             const int i = 8 * kk + 2 * e;
             const float2 dd = __fadd2_rn(
                 __fadd2_rn(f2(__uint_as_float(ya[i]), __uint_as_float(ya[i + 1])),
                            *reinterpret_cast<const float2*>(sb7 + n0 + i)),
-                f2(-tt.x, -tt.y));
+                nt);
             lc += fabsf(dd.x) + fabsf(dd.y);
             anyz |= (dd.x == 0.f) | (dd.y == 0.f);
             reinterpret_cast<uint32_t*>(o2)[e] =
@@ -617,12 +625,12 @@ decode_fused_kernel(const __grid_constant__ FusedArgs a) {
             uint32_t* o = reinterpret_cast<uint32_t*>(&dy[kk]);
 #pragma unroll
             for (int e = 0; e < 4; e++) {
-              const float2 tt = __bfloat1622float2(h2[e]);
+              const float2 nt = neg_bf16x2(h2[e]);
               const int i = 8 * kk + 2 * e;
               const float2 dd = __fadd2_rn(
                   __fadd2_rn(f2(__uint_as_float(ya[i]), __uint_as_float(ya[i + 1])),
                              *reinterpret_cast<const float2*>(sb7 + n0 + i)),
-                  f2(-tt.x, -tt.y));
+                  nt);
               if (dd.x == 0.f) o[e] &= 0xffff0000u;
               if (dd.y == 0.f) o[e] &= 0x0000ffffu;
             }
